@@ -1,0 +1,467 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: every check is a printed value
+(tests/golden), a brute-force 2^n x 2^n matrix product built without einsum,
+a closed form, a group/unitarity identity or an independent gradient rule.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import qsim_oracle as O
+from paper_2506_04891_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+RNG = np.random.default_rng(1234)
+
+
+def _read_blocks(name):
+    blocks, cur = {}, None
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line:
+                continue
+            if line.startswith("#"):
+                tag = line[1:].strip()
+                if tag and " " not in tag:
+                    cur = tag
+                    blocks[cur] = []
+                continue
+            blocks[cur].append(line.split())
+    return blocks
+
+
+# ---------------------------------------------------------------------------
+# printed values
+# ---------------------------------------------------------------------------
+
+def test_k_rz_printed_example_n3():
+    b = _read_blocks("k_rz_n3.txt")
+    J = np.array([[int(v) for v in r] for r in b["J"]])
+    K = np.array([[int(v) for v in r] for r in b["K_Rz"]])
+    assert np.array_equal(O.binary_counting_matrix(3), J)
+    assert np.array_equal(O.k_rz(3), K)
+
+
+def test_cnot_matrix_and_sigma_printed():
+    b = _read_blocks("cnot_perm.txt")
+    C = np.array([[int(v) for v in r] for r in b["CNOT"]])
+    sigma = np.array([int(v) for v in b["sigma"][0]]) - 1
+    assert np.array_equal(O.CNOT.real, C) and not O.CNOT.imag.any()
+    phi = RNG.normal(size=4) + 1j * RNG.normal(size=4)
+    out = O.apply_local(phi.reshape(2, 2), O.CNOT, (0, 1)).reshape(-1)
+    assert np.array_equal(out, phi[sigma])
+
+
+def test_printed_gate_entries():
+    rows = {}
+    with open(os.path.join(GOLD, "printed_gates.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            tag, *vals = line.split()
+            rows[tag] = np.array([complex(float(v.split(",")[0]), float(v.split(",")[1])) for v in vals])
+    assert np.allclose(O.ECR[0] * np.sqrt(2), rows["ECR_ROW0"], atol=1e-15)
+    assert np.allclose(O.ECR[1] * np.sqrt(2), rows["ECR_ROW1"], atol=1e-15)
+    assert np.allclose(O.SX[0] * 2, rows["SX_ROW0"], atol=1e-15)
+    assert np.allclose(O.SX[1] * 2, rows["SX_ROW1"], atol=1e-15)
+
+
+def test_ms_matches_printed_except_corrected_entry():
+    p0, p1, th = 0.13, 0.71, 0.37
+    m = O.ms(p0, p1, th)
+    c, s = np.cos(np.pi * th), np.sin(np.pi * th)
+    assert np.allclose(np.diag(m), c)
+    assert np.isclose(m[0, 3], -1j * np.exp(-2j * np.pi * (p0 + p1)) * s)
+    assert np.isclose(m[1, 2], -1j * np.exp(-2j * np.pi * (p1 - p0)) * s)
+    assert np.isclose(m[2, 1], -1j * np.exp(-2j * np.pi * (p0 - p1)) * s)
+    # printed (3,0) equals printed (0,3): that matrix is not unitary ...
+    printed = m.copy()
+    printed[3, 0] = printed[0, 3]
+    assert not np.allclose(printed.conj().T @ printed, np.eye(4))
+    # ... the conjugated entry is
+    assert np.allclose(m.conj().T @ m, np.eye(4), atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# algebraic identities of single gates
+# ---------------------------------------------------------------------------
+
+def _all_gate_mats():
+    t = RNG.uniform(0, 2 * np.pi, size=3)
+    return {
+        "RX": O.rx(t[0]), "RY": O.ry(t[0]), "RZ": O.rz(t[0]), "ZZ": O.isingzz(t[1]),
+        "GPI": O.gpi(t[2]), "GPI2": O.gpi2(t[2]), "MS": O.ms(*t), "SX": O.SX,
+        "ECR": O.ECR, "X": O.X, "CNOT": O.CNOT, "H": O.H,
+    }
+
+
+@pytest.mark.parametrize("name", list(_all_gate_mats().keys()))
+def test_gate_unitary(name):
+    m = _all_gate_mats()[name]
+    assert np.allclose(m.conj().T @ m, np.eye(m.shape[0]), atol=1e-14)
+
+
+def test_fixed_gate_identities():
+    assert np.allclose(O.SX @ O.SX, O.X, atol=1e-15)
+    assert np.allclose(O.ECR, O.ECR.conj().T, atol=1e-15)
+    assert np.allclose(O.ECR @ O.ECR, np.eye(4), atol=1e-15)
+    assert np.allclose(O.ms(0.3, 0.4, 0.0), np.eye(4))
+    # MS = cos(pi th) I - i sin(pi th) K with K hermitian, K^2 = I
+    p0, p1, th = 0.21, 0.05, 0.33
+    K = (np.cos(np.pi * th) * np.eye(4) - O.ms(p0, p1, th)) / (1j * np.sin(np.pi * th))
+    assert np.allclose(K, K.conj().T) and np.allclose(K @ K, np.eye(4))
+
+
+def test_h_rz_expansion_identities():
+    t = 0.731
+    # Rx = H Rz H (Sec. 2.5)
+    assert np.allclose(O.rx(t), O.H @ O.rz(t) @ O.H, atol=1e-15)
+    # printed "Ry = Z H Rz H Z" is false; the identity that holds is S H Rz H S^dagger
+    assert not np.allclose(O.ry(t), O.Z @ O.H @ O.rz(t) @ O.H @ O.Z)
+    assert np.allclose(O.ry(t), O.S @ O.H @ O.rz(t) @ O.H @ O.S.conj().T, atol=1e-15)
+    # GPI2(phi) = Rz(-th) Rx(pi/2) Rz(th) with th = -2 pi phi (GPI2 is in turns)
+    phi = 0.173
+    th = -2 * np.pi * phi
+    assert np.allclose(O.gpi2(phi), O.rz(-th) @ O.rx(np.pi / 2) @ O.rz(th), atol=1e-15)
+
+
+@pytest.mark.parametrize("fn,dfn", [(O.rx, O.d_rx), (O.ry, O.d_ry), (O.rz, O.d_rz),
+                                    (O.isingzz, O.d_isingzz), (O.gpi, O.d_gpi),
+                                    (O.gpi2, O.d_gpi2)])
+def test_gate_derivatives_match_difference_quotient(fn, dfn):
+    t, h = 0.4123, 1e-6
+    num = (fn(t + h) - fn(t - h)) / (2 * h)
+    assert np.allclose(dfn(t), num, atol=1e-8)
+
+
+def test_ms_derivatives_match_difference_quotient():
+    p = np.array([0.11, 0.62, 0.29])
+    h = 1e-6
+    d = O.d_ms(*p)
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        num = (O.ms(*(p + e)) - O.ms(*(p - e))) / (2 * h)
+        assert np.allclose(d[i], num, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# layers: einsum application vs brute-force matrices (Unitary operation)
+# ---------------------------------------------------------------------------
+
+ALL_KINDS = ["RX", "RY", "RZ", "ISINGZZ_RING", "CNOT_RING", "X", "SX", "GPI", "GPI2",
+             "MS_BRICK", "ECR_BRICK"]
+
+
+def _random_layer_inputs(n, layer):
+    c = O.layer_param_count(n, layer)
+    theta = RNG.uniform(0, 2 * np.pi, size=max(c, 1))
+    x = RNG.uniform(0, np.pi, size=max(c, 1))
+    return x, theta
+
+
+@pytest.mark.parametrize("kind", ALL_KINDS)
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_layer_einsum_equals_bruteforce(kind, n):
+    for parity in (0, 1):
+        for source in ("theta", "input"):
+            layer = (kind, source, 0, parity)
+            x, theta = _random_layer_inputs(n, layer)
+            psi = RNG.normal(size=2 ** n) + 1j * RNG.normal(size=2 ** n)
+            psi /= np.linalg.norm(psi)
+            out = O.apply_local  # noqa: F841 (documentation of the path)
+            via_einsum = O.forward_sample(n, [layer], x, theta, psi0=psi)
+            via_matrix = O.layer_unitary(n, layer, x, theta) @ psi
+            assert np.allclose(via_einsum, via_matrix, atol=1e-13), (kind, n, parity, source)
+
+
+def test_single_qubit_layer_is_kronecker_product():
+    n = 4
+    th = RNG.uniform(0, 2 * np.pi, size=n)
+    M = O.layer_unitary(n, ("RY", "theta", 0, 0), None, th)
+    K = O.kron_layer_matrix(n, [O.ry(t) for t in th])
+    assert np.allclose(M, K, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [3, 4, 6])
+def test_full_circuits_match_bruteforce(n):
+    circuits = [W.hea_circuit(n, 2), W.zz_circuit(n, 2), W.ibm_circuit(n, 2), W.ionq_circuit(n, 2)]
+    for layers in circuits:
+        x, theta, _ = W.draw_inputs(n, layers, 2, seed=n)
+        for b in range(2):
+            a = O.forward_sample(n, layers, x[b], theta)
+            m = O.forward_bruteforce(n, layers, x[b], theta)
+            assert np.allclose(a, m, atol=1e-12)
+            assert np.isclose(np.linalg.norm(a), 1.0, atol=1e-13)
+
+
+def test_norm_preserved_n10():
+    n = 10
+    layers = W.ionq_circuit(n, 3) + W.ibm_circuit(n, 2)[2:]
+    x, theta, _ = W.draw_inputs(n, layers, 1, seed=3)
+    psi = O.forward_sample(n, layers, x[0], theta)
+    assert abs(np.vdot(psi, psi).real - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# permutation layers (Sec. 2.3)
+# ---------------------------------------------------------------------------
+
+def _ring_image(bits):
+    """CNOT(q -> q+1 mod n) for q = 0..n-1 on a basis state, worked out by hand:
+    b'_q = b_0 ^ ... ^ b_q for q >= 1 and b'_0 = b_1 ^ ... ^ b_{n-1}."""
+    n = len(bits)
+    out = [0] * n
+    acc = bits[0]
+    for q in range(1, n):
+        acc ^= bits[q]
+        out[q] = acc
+    p = 0
+    for q in range(1, n):
+        p ^= bits[q]
+    out[0] = p
+    return out
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 7])
+def test_cnot_ring_is_the_closed_form_permutation(n):
+    psi = RNG.normal(size=2 ** n) + 1j * RNG.normal(size=2 ** n)
+    out = O.forward_sample(n, [("CNOT_RING", "none", 0, 0)], None, None, psi0=psi)
+    expected = np.empty_like(psi)
+    for k in range(2 ** n):
+        bits = [(k >> (n - 1 - q)) & 1 for q in range(n)]
+        nb = _ring_image(bits)
+        kk = 0
+        for b in nb:
+            kk = (kk << 1) | b
+        expected[kk] = psi[k]
+    assert np.array_equal(out, expected)  # bit-exact
+
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_x_layer_reverses_the_state(n):
+    psi = RNG.normal(size=2 ** n) + 1j * RNG.normal(size=2 ** n)
+    out = O.forward_sample(n, [("X", "none", 0, 0)], None, None, psi0=psi)
+    assert np.array_equal(out, psi[::-1])
+
+
+# ---------------------------------------------------------------------------
+# diagonal layers (Sec. 2.4): EC, TP, K_Rzz, GPI mapping
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_rz_layer_ec_tp_einsum_agree(n):
+    th = RNG.uniform(0, 2 * np.pi, size=n)
+    ec = O.ec_diagonal(O.k_rz(n), th)
+    tp = O.tp_diagonal([np.diag(O.rz(t)) for t in th])
+    psi = RNG.normal(size=2 ** n) + 1j * RNG.normal(size=2 ** n)
+    es = O.forward_sample(n, [("RZ", "theta", 0, 0)], None, th, psi0=psi)
+    assert np.allclose(ec, tp, atol=1e-14)
+    assert np.allclose(es, ec * psi, atol=1e-13)
+    # multiplication count of the diagonal tensor product: 2^(n+1) - 4
+    assert sum(2 ** k for k in range(2, n + 1)) == max(2 ** (n + 1) - 4, 0)
+
+
+@pytest.mark.parametrize("n", [2, 3, 6])
+def test_isingzz_ring_ec_equals_einsum(n):
+    th = RNG.uniform(0, 2 * np.pi, size=n)
+    ec = O.ec_diagonal(O.k_rzz_ring(n), th)
+    psi = RNG.normal(size=2 ** n) + 1j * RNG.normal(size=2 ** n)
+    es = O.forward_sample(n, [("ISINGZZ_RING", "theta", 0, 0)], None, th, psi0=psi)
+    assert np.allclose(es, ec * psi, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_gpi_layer_is_phase_then_reversal(n):
+    phi = RNG.uniform(0, 1, size=n)
+    psi = RNG.normal(size=2 ** n) + 1j * RNG.normal(size=2 ** n)
+    es = O.forward_sample(n, [("GPI", "theta", 0, 0)], None, phi, psi0=psi)
+    # psi'[2^n - 1 - i] = (psi o exp(i K theta))[i] with theta = 2 pi phi
+    ph = psi * np.exp(1j * (O.k_rz(n) @ (2 * np.pi * phi)))
+    assert np.allclose(es, ph[::-1], atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# closed forms for <Z> and gradients
+# ---------------------------------------------------------------------------
+
+def test_ry_layer_on_zero_gives_cos():
+    n = 7
+    th = RNG.uniform(0, 2 * np.pi, size=n)
+    psi = O.forward_sample(n, [("RY", "theta", 0, 0)], None, th)
+    assert np.allclose(O.expect_z_sample(psi, n), np.cos(th), atol=1e-13)
+
+
+def test_rx_embedding_gives_cos():
+    n = 6
+    x = RNG.uniform(0, np.pi, size=n)
+    psi = O.forward_sample(n, [("RX", "input", 0, 0)], x, None)
+    assert np.allclose(O.expect_z_sample(psi, n), np.cos(x), atol=1e-13)
+
+
+def block_closed_form(x, th):
+    """<Z_q> after RX(x), RY(th), IsingZZ ring (any angles), CNOT ring.
+
+    RX then RY on |0> leaves qubit j with <Z_j> = cos x_j cos th_j; the ZZ ring
+    only adds phases; the CNOT ring maps b -> b' with b'_q = b_0^..^b_q (q >= 1)
+    and b'_0 = b_1^..^b_{n-1}, so <Z'_q> is a product of the input <Z_j>.
+    """
+    c = np.cos(x) * np.cos(th)
+    n = len(c)
+    out = np.empty(n)
+    out[0] = np.prod(c[1:])
+    for q in range(1, n):
+        out[q] = np.prod(c[: q + 1])
+    return out
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_one_block_closed_form(n):
+    layers = W.zz_circuit(n, 1)
+    x, theta, g = W.draw_inputs(n, layers, 3, seed=n)
+    for b in range(3):
+        psi = O.forward_sample(n, layers, x[b], theta)
+        ez = O.expect_z_sample(psi, n)
+        assert np.allclose(ez, block_closed_form(x[b], theta[:n]), atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [3, 5])
+def test_one_block_closed_form_gradient(n):
+    layers = W.zz_circuit(n, 1)
+    x, theta, _ = W.draw_inputs(n, layers, 1, seed=11)
+    g = W.draw_upstream(1, n, seed=5)
+    ez, dth, dth_s, dx = O.adjoint(n, layers, x, theta, g)
+    c = np.cos(x[0]) * np.cos(theta[:n])
+    dc_dth = -np.cos(x[0]) * np.sin(theta[:n])
+    dc_dx = -np.sin(x[0]) * np.cos(theta[:n])
+    # dL/dc_j via the product form
+    dL_dc = np.zeros(n)
+    for j in range(n):
+        for q in range(n):
+            idx = list(range(1, n)) if q == 0 else list(range(q + 1))
+            if j in idx:
+                dL_dc[j] += g[0, q] * np.prod([c[i] for i in idx if i != j])
+    assert np.allclose(dth[:n], dL_dc * dc_dth, atol=1e-12)
+    assert np.allclose(dth[n:], 0.0, atol=1e-12)  # the ZZ ring does not change <Z>
+    assert np.allclose(dx[0], dL_dc * dc_dx, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# gradients: adjoint vs parameter shift vs finite differences
+# ---------------------------------------------------------------------------
+
+def _small_circuits(n):
+    return {
+        "hea": W.hea_circuit(n, 2),
+        "zz": W.zz_circuit(n, 2),
+        "ibm": W.ibm_circuit(n, 2),
+        "ionq": W.ionq_circuit(n, 2),
+    }
+
+
+@pytest.mark.parametrize("name", ["hea", "zz", "ibm", "ionq"])
+def test_adjoint_matches_param_shift_and_finite_differences(name):
+    n = 4
+    layers = _small_circuits(n)[name]
+    x, theta, _ = W.draw_inputs(n, layers, 2, seed=7)
+    g = W.draw_upstream(2, n, seed=1)
+    ez, dth, dth_s, dx = O.adjoint(n, layers, x, theta, g)
+    for b in range(2):
+        ps = O.param_shift_sample(n, layers, x[b], theta, g[b])
+        assert len(ps) > 0
+        for (src, idx), v in ps.items():
+            ref = dth_s[b, idx] if src == "theta" else dx[b, idx]
+            assert abs(ref - v) < 1e-11, (name, src, idx, ref, v)
+        fd_th, fd_x = O.finite_diff_sample(n, layers, x[b], theta, g[b])
+        assert np.allclose(dth_s[b], fd_th, atol=2e-8)
+        assert np.allclose(dx[b], fd_x, atol=2e-8)
+    assert np.allclose(dth, dth_s.sum(axis=0))
+
+
+def test_parameter_shift_covers_every_exact_kind():
+    n = 3
+    layers = [("RX", "input", 0, 0), ("RY", "theta", 0, 0), ("RZ", "theta", 3, 0),
+              ("ISINGZZ_RING", "theta", 6, 0), ("GPI", "theta", 9, 0),
+              ("MS_BRICK", "theta", 12, 0), ("CNOT_RING", "none", 0, 0)]
+    x, theta, _ = W.draw_inputs(n, layers, 1, seed=2)
+    theta = np.random.default_rng(3).uniform(0, 1, size=15)
+    g = W.draw_upstream(1, n, seed=2)
+    _, _, dth_s, dx = O.adjoint(n, layers, x, theta, g)
+    ps = O.param_shift_sample(n, layers, x[0], theta, g[0])
+    for (src, idx), v in ps.items():
+        ref = dth_s[0, idx] if src == "theta" else dx[0, idx]
+        assert abs(ref - v) < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes must be caught by the pins above (run on the CPU only)
+# ---------------------------------------------------------------------------
+
+def _pins_pass():
+    try:
+        test_layer_einsum_equals_bruteforce.__wrapped__ if False else None
+        for kind in ALL_KINDS:
+            test_layer_einsum_equals_bruteforce(kind, 3)
+        test_cnot_ring_is_the_closed_form_permutation(4)
+        test_one_block_closed_form(3)
+        test_rz_layer_ec_tp_einsum_agree(3)
+        test_isingzz_ring_ec_equals_einsum(3)
+        test_gpi_layer_is_phase_then_reversal(3)
+        test_ry_layer_on_zero_gives_cos()
+        test_rx_embedding_gives_cos()
+        for name in ("hea", "zz", "ibm", "ionq"):
+            test_adjoint_matches_param_shift_and_finite_differences(name)
+        test_h_rz_expansion_identities()
+        test_ms_matches_printed_except_corrected_entry()
+    except AssertionError:
+        return False
+    return True
+
+
+def _transposed_apply(psi_t, U, qubits):
+    return _orig_apply(psi_t, U.T, qubits)
+
+
+_orig_apply = O.apply_local
+
+
+@pytest.mark.parametrize("mutation", [
+    "ry_sign", "rz_sign", "apply_transposed", "dry_dropped_term", "ring_reversed",
+    "expect_wrong_bit", "adjoint_no_conj", "ms_unconjugated",
+])
+def test_planted_mistakes_are_caught(monkeypatch, mutation):
+    if mutation == "ry_sign":
+        monkeypatch.setattr(O, "ry", lambda t: np.array([[np.cos(t / 2), np.sin(t / 2)],
+                                                         [-np.sin(t / 2), np.cos(t / 2)]], dtype=complex))
+    elif mutation == "rz_sign":
+        monkeypatch.setattr(O, "rz", lambda t: np.diag([np.exp(0.5j * t), np.exp(-0.5j * t)]))
+    elif mutation == "apply_transposed":
+        monkeypatch.setattr(O, "apply_local", _transposed_apply)
+    elif mutation == "dry_dropped_term":
+        monkeypatch.setattr(O, "d_ry", lambda t: 0.5 * np.array([[0, -np.cos(t / 2)], [np.cos(t / 2), 0]],
+                                                               dtype=complex))
+    elif mutation == "ring_reversed":
+        orig = O.layer_gates
+
+        def lg(n, layer, x_b, theta):
+            gates = orig(n, layer, x_b, theta)
+            return gates[::-1] if layer[0] == "CNOT_RING" else gates
+        monkeypatch.setattr(O, "layer_gates", lg)
+    elif mutation == "expect_wrong_bit":
+        orig_e = O.expect_z_sample
+        monkeypatch.setattr(O, "expect_z_sample", lambda psi, n: orig_e(psi, n)[::-1])
+    elif mutation == "adjoint_no_conj":
+        orig_vdot = np.vdot
+        monkeypatch.setattr(O.np, "vdot", lambda a, b: np.sum(a * b))
+    elif mutation == "ms_unconjugated":
+        orig_ms = O.ms
+
+        def bad(p0, p1, th):
+            m = orig_ms(p0, p1, th)
+            m[3, 0] = m[0, 3]
+            return m
+        monkeypatch.setattr(O, "ms", bad)
+    assert not _pins_pass(), mutation
