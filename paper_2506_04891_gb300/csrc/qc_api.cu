@@ -1,0 +1,1216 @@
+// C ABI (include/qlayer.h): validation, per-layer planning, workspace layout
+// and execution of the forward / <Z> / adjoint-backward kernel sequences.
+//
+// Planner (the GPU analogue of the paper's per-layer technique selection,
+// Sec. 3): every layer class maps to the kernel that needs the fewest HBM
+// passes for the qubit count at hand:
+//   ROT1 / DENSE2 -> tile passes (2^t amplitudes staged in shared memory),
+//                    ceil over the bit ranges that a tile can hold;
+//   DIAG          -> one elementwise pass with factored phase tables
+//                    (Diagonal Tensor Product, Sec. 2.4.2);
+//   XCOMP         -> one elementwise pass over mirrored chunks (X, GPI: Sec. 2.4.1);
+//   RING          -> one permutation pass with the closed-form index map (Sec. 2.3);
+//   leading single-qubit layers -> one write-only product-state pass;
+//   small n       -> the whole circuit of a sample in one CTA's shared memory.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/qlayer.h"
+#include "qc_internal.h"
+#include "qc_kernels.h"
+
+using namespace qc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// ---- launch counting and optional per-launch event timing (diagnostics) ----
+enum ProfClass {
+  PC_COEF, PC_PRODINIT, PC_TILE_F, PC_TILE_B, PC_DIAG_F, PC_DIAG_B, PC_RING_F, PC_RING_B,
+  PC_EXPECT, PC_LAMINIT, PC_REDUCE, PC_SMEM_F, PC_SMEM_B, PC_N
+};
+const char* kProfNames[PC_N] = {"coef", "prodinit", "tile_fwd", "tile_bwd", "diag_fwd", "diag_bwd",
+                                "ring_fwd", "ring_bwd", "expect", "laminit", "reduce", "smem_fwd",
+                                "smem_bwd"};
+unsigned long long g_launches = 0;
+bool g_prof = false;
+struct ProfRec {
+  int cls;
+  double bytes;
+  cudaEvent_t a, b;
+};
+std::vector<ProfRec> g_recs;
+size_t g_nrec = 0;
+
+struct ProfScope {
+  ProfRec* r = nullptr;
+  cudaStream_t st;
+  int nl;
+  ProfScope(int cls, double bytes, cudaStream_t s, int nlaunch = 1) : st(s), nl(nlaunch) {
+    g_launches += nlaunch;
+    if (!g_prof) return;
+    if (g_nrec == g_recs.size()) {
+      ProfRec x;
+      x.cls = 0;
+      x.bytes = 0;
+      cudaEventCreate(&x.a);
+      cudaEventCreate(&x.b);
+      g_recs.push_back(x);
+    }
+    r = &g_recs[g_nrec++];
+    r->cls = cls;
+    r->bytes = bytes;
+    cudaEventRecord(r->a, st);
+  }
+  ~ProfScope() {
+    if (r) cudaEventRecord(r->b, st);
+  }
+};
+
+qc_status fail(qc_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+qc_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(QC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+enum StepType { ST_PRODINIT, ST_TILE, ST_DIAG, ST_RING, ST_LAMINIT };
+enum BufId { B_NONE = -1, B_PSIOUT = 0, B_RUN0 = 1, B_RUN1 = 2, B_LAM0 = 3, B_LAM1 = 4, B_CKPT = 16 };
+
+struct Step {
+  int type = ST_TILE;
+  int ns = 1;
+  int rb = 4;
+  TilePass tp;
+  DiagPass dp;
+  RingPass rp;
+  int cb = 12;
+  int s0 = B_NONE, d0 = B_NONE, s1 = B_NONE, d1 = B_NONE;
+  long long part_off = 0;
+  int layer = -1;
+};
+
+struct OutMap {
+  int job;
+  int val;
+  int pidx;
+  double scale;
+};
+
+struct Plan {
+  int batch = 0;
+  bool smem = false;
+  std::vector<Step> fwd, bwd;
+  std::vector<CoefJob> coef_jobs;
+  ProdVecJob pv{};
+  int nlead = 0;
+  int nckpt = 0;
+  std::vector<int> ckpt_after;  // layer whose output each slot holds
+  size_t S = 0;                 // bytes of one batch of states
+  size_t coef_elems = 0;
+  size_t off_coef = 0, off_pv = 0, off_run0 = 0, off_run1 = 0, off_lam0 = 0, off_lam1 = 0,
+         off_ckpt = 0, off_part = 0, off_V = 0, ws_fwd = 0, ws_bwd = 0;
+  size_t part_doubles = 0;
+  // reductions
+  std::vector<RedJob> jobs;
+  std::vector<long long> row0;
+  std::vector<OutMap> outs;
+  long long nrows = 0;
+  bool overlap = false;
+  // whole-circuit program
+  std::vector<SmemLayer> prog;
+  int nslots = 0;
+  // device copies (lazily uploaded)
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  CoefJob* d_coef_jobs = nullptr;
+  RedJob* d_jobs = nullptr;
+  long long* d_row0 = nullptr;
+  int* d_out0 = nullptr;
+  RedOut* d_outs = nullptr;
+  SmemLayer* d_prog = nullptr;
+  std::vector<std::vector<int>> job_groups;  // finalize groups (serial when outputs overlap)
+};
+
+}  // namespace
+
+struct qc_circuit {
+  int n = 0;
+  qc_dtype dtype = QC_C64;
+  int rsize = 4;
+  qc_options opt{};
+  std::vector<LayerInfo> layers;
+  int n_theta = 0, n_in = 0;
+  std::map<int, std::unique_ptr<Plan>> plans;
+  void* exp_scratch = nullptr;
+  size_t exp_scratch_bytes = 0;
+  const void* last_ws = nullptr;
+  int last_batch = -1;
+};
+
+namespace {
+
+int tile_tmax(const qc_circuit* c, int ns) {
+  (void)ns;
+  return c->dtype == QC_C64 ? 12 : 11;
+}
+int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
+int reg_bits(const qc_circuit* c, int ns) {
+  if (c->dtype == QC_C64) return 4;
+  return ns == 2 ? 3 : 4;
+}
+
+bool cuts_pair(const LayerInfo& L, int n, int e) {
+  // boundary between bits e-1 and e cuts a brick pair (p_lo, p_hi) = (e-1, e)
+  if (L.cls != LC_DENSE2 || e <= 0 || e >= n) return false;
+  const int q = n - 1 - e;  // qubit of the pair's high bit (first qubit)
+  return q >= L.parity && ((q - L.parity) % 2 == 0) && q + 1 <= n - 1;
+}
+
+struct PassOpInfo {
+  int pidx;  // absolute parameter index of the op's first parameter (or -1)
+};
+
+// Builds the tile passes of a ROT1 or DENSE2 layer.
+std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, int ns,
+                                      std::vector<std::vector<int>>& pidx_per_slot) {
+  const int n = c->n;
+  const int tmax = tile_tmax(c, ns);
+  const int cbits = contig_bits(c);
+  std::vector<TilePass> out;
+  // later passes share the bits left after the first one evenly
+  const int rest = std::max(0, n - tmax);
+  const int later_cap = tmax - cbits;
+  const int nlater = rest > 0 ? (rest + later_cap - 2) / (later_cap - 1) : 0;  // slack for pair cuts
+  const int even_cap = nlater > 0 ? (rest + nlater - 1) / nlater : later_cap;
+  int s = 0;
+  bool first = true;
+  while (s < n) {
+    int cap = first ? tmax : std::min(later_cap, std::max(even_cap, 2));
+    int e = std::min(n, s + cap);
+    if (e < n && cuts_pair(L, n, e)) e -= 1;
+    TilePass P;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    if (first) {
+      P.c = e; P.h0 = e; P.t = e;
+    } else {
+      P.c = std::min(cbits, s); P.h0 = s; P.t = P.c + (e - s);
+    }
+    auto local = [&](int p) { return first ? p : P.c + (p - s); };
+    struct OpTmp { TileOp op; std::vector<int> pidx; };
+    std::vector<OpTmp> ops;
+    if (L.cls == LC_ROT1) {
+      for (int p = s; p < e; ++p) {
+        const int q = n - 1 - p;
+        OpTmp o;
+        memset(&o.op, 0, sizeof(o.op));
+        o.op.l = (int16_t)local(p);
+        o.op.is2q = 0;
+        o.op.real = (int8_t)L.real;
+        o.op.np = (int16_t)((ns == 2 && L.diff) ? 1 : 0);
+        o.op.coef = L.coef_off + (long long)q * kRec1q;
+        o.op.bstride = L.coef_bstride;
+        o.op.nco = ns == 2 ? kRec1q : 8;
+        if (o.op.np) o.pidx.push_back(L.offset + q);
+        ops.push_back(o);
+      }
+    } else {
+      for (int i = 0; i < L.ngates; ++i) {
+        const int q0 = L.parity + 2 * i;
+        const int plo = n - 2 - q0, phi = plo + 1;
+        if (plo < s || phi >= e) continue;
+        OpTmp o;
+        memset(&o.op, 0, sizeof(o.op));
+        o.op.l = (int16_t)local(plo);
+        o.op.is2q = 1;
+        const int np = (ns == 2 && L.diff && L.kind == QC_L_MS_BRICK) ? 3 : 0;
+        o.op.np = (int16_t)np;
+        o.op.coef = L.coef_off + (long long)i * kRec2q;
+        o.op.bstride = L.coef_bstride;
+        o.op.nco = 32 + (ns == 2 ? 32 * np : 0);
+        for (int k = 0; k < np; ++k) o.pidx.push_back(L.offset + 3 * i + k);
+        ops.push_back(o);
+      }
+    }
+    // rounds of RB register bits
+    const int RB = std::min(reg_bits(c, ns), P.t);
+    std::vector<int> assigned(ops.size(), 0);
+    int nass = 0, nr = 0;
+    std::vector<TileOp> ordered;
+    std::vector<std::vector<int>> ordered_pidx;
+    P.rop[0] = 0;
+    while (nass < (int)ops.size()) {
+      int lo = 1 << 30;
+      for (size_t k = 0; k < ops.size(); ++k)
+        if (!assigned[k]) lo = std::min(lo, (int)ops[k].op.l);
+      lo = std::min(lo, P.t - RB);
+      const int hi = lo + RB;
+      int got = 0;
+      for (size_t k = 0; k < ops.size(); ++k) {
+        if (assigned[k]) continue;
+        const int top = ops[k].op.l + (ops[k].op.is2q ? 1 : 0);
+        if (ops[k].op.l >= lo && top < hi) {
+          assigned[k] = 1;
+          ++nass;
+          ++got;
+          ordered.push_back(ops[k].op);
+          ordered_pidx.push_back(ops[k].pidx);
+        }
+      }
+      if (!got || nr >= kMaxRounds) break;  // cannot happen for valid geometry
+      P.rlo[nr] = (int8_t)lo;
+      ++nr;
+      P.rop[nr] = (int16_t)ordered.size();
+    }
+    P.nrounds = nr;
+    P.nops = (int)ordered.size();
+    int soff = 0, slot = 0;
+    for (int k = 0; k < P.nops; ++k) {
+      P.ops[k] = ordered[k];
+      P.ops[k].soff = soff;
+      soff += P.ops[k].nco;
+      P.ops[k].slot = (int16_t)slot;
+      for (int q = 0; q < P.ops[k].np; ++q) pidx_per_slot.push_back({(int)out.size(), slot + q, ordered_pidx[k][q]});
+      slot += P.ops[k].np;
+    }
+    P.ncoef = soff;
+    P.nslots = slot;
+    P.store = 1;
+    out.push_back(P);
+    s = e;
+    first = false;
+  }
+  return out;
+}
+
+int diag_zbit(const LayerInfo& L, int n, int j) {
+  if (L.kind == QC_L_ISINGZZ_RING) return ((n - 2 - j) % n + n) % n;
+  return n - 1 - j;
+}
+
+bool smem_fits(const qc_circuit* c) {
+  const int lim = c->dtype == QC_C64 ? 13 : 12;
+  return c->n <= lim;
+}
+
+void add_job(Plan& P, int kind, int source, long long part_off, long long nblk, int nvals,
+             long long bps, const std::vector<OutMap>& outs) {
+  RedJob J;
+  memset(&J, 0, sizeof(J));
+  J.part_off = part_off;
+  J.nblk = (int)nblk;
+  J.nvals = nvals;
+  J.blk_per_sample = (int)bps;
+  J.kind = kind;
+  J.nout = (int)outs.size();
+  J.source = source;
+  J.first = (int)P.outs.size();
+  const int jid = (int)P.jobs.size();
+  P.jobs.push_back(J);
+  P.row0.push_back(P.nrows);
+  P.nrows += (long long)P.batch * nvals;
+  for (auto o : outs) {
+    o.job = jid;
+    P.outs.push_back(o);
+  }
+}
+
+std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
+  auto P = std::make_unique<Plan>();
+  Plan& p = *P;
+  p.batch = batch;
+  const int n = c->n;
+  const int L = (int)c->layers.size();
+  const size_t N = (size_t)1 << n;
+  p.S = (size_t)batch * N * 2 * c->rsize;
+
+  // coefficient layout
+  size_t ce = 0;
+  for (int l = 0; l < L; ++l) {
+    const LayerInfo& Li = c->layers[l];
+    size_t sz = 0;
+    if (Li.cls == LC_ROT1) sz = (size_t)n * kRec1q;
+    else if (Li.cls == LC_DENSE2) sz = (size_t)Li.ngates * kRec2q;
+    else if ((Li.cls == LC_DIAG || Li.cls == LC_XCOMP) && Li.has_phase) sz = (size_t)kDiagTables * 2 * ((size_t)1 << Li.tb);
+    if (!sz) continue;
+    CoefJob J;
+    memset(&J, 0, sizeof(J));
+    J.cls = Li.cls; J.kind = Li.kind; J.source = Li.source; J.offset = Li.offset;
+    J.parity = Li.parity; J.ngates = Li.ngates; J.per_sample = Li.per_sample;
+    J.has_phase = Li.has_phase; J.tb = Li.tb;
+    J.coef_off = (long long)ce;
+    J.bstride = Li.per_sample ? (long long)sz : 0;
+    ce += Li.per_sample ? sz * batch : sz;
+    ce = (ce + 1) & ~(size_t)1;
+    p.coef_jobs.push_back(J);
+  }
+  p.coef_elems = ce;
+  // write back offsets into a local copy of layer infos
+  std::vector<LayerInfo> LI = c->layers;
+  {
+    size_t k = 0;
+    for (int l = 0; l < L; ++l) {
+      LayerInfo& Li = LI[l];
+      const bool has = Li.cls == LC_ROT1 || Li.cls == LC_DENSE2 ||
+                       ((Li.cls == LC_DIAG || Li.cls == LC_XCOMP) && Li.has_phase);
+      if (!has) continue;
+      Li.coef_off = p.coef_jobs[k].coef_off;
+      Li.coef_bstride = p.coef_jobs[k].bstride;
+      ++k;
+    }
+  }
+
+  bool smem = false;
+  if (c->opt.path == 1) smem = true;
+  else if (c->opt.path == 0) smem = smem_fits(c);
+  p.smem = smem;
+
+  size_t off = 0;
+  p.off_coef = off;
+  off = align256(off + ce * c->rsize);
+
+  if (smem) {
+    int slot = 0;
+    for (int l = 0; l < L; ++l) {
+      const LayerInfo& Li = LI[l];
+      SmemLayer S;
+      memset(&S, 0, sizeof(S));
+      S.cls = Li.cls; S.kind = Li.kind; S.real = Li.real; S.zmode = Li.zmode;
+      S.has_phase = Li.has_phase; S.tb = Li.tb; S.ngates = Li.ngates;
+      S.np_per_gate = Li.kind == QC_L_MS_BRICK ? 3 : 1;
+      S.parity = Li.parity;
+      S.coef = Li.coef_off; S.bstride = Li.coef_bstride;
+      S.gscale = Li.gscale;
+      S.slot = -1;
+      if (Li.diff && Li.nparams > 0) {
+        S.slot = slot;
+        std::vector<OutMap> outs;
+        for (int j = 0; j < Li.nparams; ++j) outs.push_back(OutMap{0, j, Li.offset + j, 1.0});
+        add_job(p, RK_DIRECT, Li.source, (long long)slot * batch, batch, Li.nparams, 1, outs);
+        slot += Li.nparams;
+      }
+      p.prog.push_back(S);
+    }
+    p.nslots = slot;
+    p.part_doubles = (size_t)slot * batch;
+    p.off_part = off;
+    off = align256(off + p.part_doubles * 8);
+    p.off_V = off;
+    off = align256(off + (size_t)p.nrows * 8);
+    p.ws_fwd = p.ws_bwd = std::max<size_t>(off, 256);
+  } else {
+    // ---------------- forward ----------------
+    const int ck = c->opt.ckpt_every < 0 ? (p.S >= ((size_t)1 << 30) ? 4 : 0) : c->opt.ckpt_every;
+    int lead = 0;
+    if (c->opt.fuse) {
+      while (lead < L && lead < kMaxLeading) {
+        const LayerInfo& Li = LI[lead];
+        const bool single = Li.cls == LC_ROT1 || (Li.cls == LC_DIAG && Li.kind == QC_L_RZ) ||
+                            Li.cls == LC_XCOMP;
+        if (!single) break;
+        ++lead;
+      }
+    }
+    p.nlead = lead;
+    p.pv.nl = lead;
+    for (int l = 0; l < lead; ++l) {
+      p.pv.kind[l] = LI[l].kind;
+      p.pv.source[l] = LI[l].source;
+      p.pv.offset[l] = LI[l].offset;
+    }
+    // checkpoint slots: state after layer l for (l + 1) % ck == 0, l < L-1, l >= lead-1
+    std::map<int, int> ck_slot;
+    if (ck > 0) {
+      for (int l = std::max(lead - 1, 0); l < L - 1; ++l)
+        if ((l + 1) % ck == 0) {
+          ck_slot[l] = (int)p.ckpt_after.size();
+          p.ckpt_after.push_back(l);
+        }
+    }
+    p.nckpt = (int)p.ckpt_after.size();
+    // symbolic buffers: A = 1, B = 2 (renamed at the end), CK = B_CKPT + slot
+    const int A = 1, Bb = 2;
+    auto other = [&](int x) { return x == A ? Bb : A; };
+    int cur;
+    {
+      Step s;
+      s.type = ST_PRODINIT;
+      s.cb = std::min(n, 12);
+      const int l0 = lead - 1;
+      s.d0 = (l0 >= 0 && ck_slot.count(l0)) ? B_CKPT + ck_slot[l0] : A;
+      s.layer = l0;
+      p.fwd.push_back(s);
+      cur = s.d0;
+    }
+    std::vector<std::vector<int>> dummy;
+    for (int l = lead; l < L; ++l) {
+      const LayerInfo& Li = LI[l];
+      std::vector<Step> passes;
+      if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
+        for (auto& tp : plan_tile_layer(c, Li, 1, dummy)) {
+          Step s;
+          s.type = ST_TILE; s.ns = 1; s.tp = tp; s.rb = std::min(reg_bits(c, 1), tp.t);
+          passes.push_back(s);
+        }
+      } else if (Li.cls == LC_DIAG || Li.cls == LC_XCOMP) {
+        Step s;
+        s.type = ST_DIAG; s.ns = 1;
+        memset(&s.dp, 0, sizeof(s.dp));
+        s.dp.n = n; s.dp.cb = std::min(n, 12); s.dp.zmode = Li.zmode;
+        s.dp.xcomp = Li.cls == LC_XCOMP; s.dp.has_phase = Li.has_phase; s.dp.tb = Li.tb;
+        s.dp.coef = Li.coef_off; s.dp.bstride = Li.coef_bstride; s.dp.nvals = n + 1;
+        passes.push_back(s);
+      } else if (Li.cls == LC_RING) {
+        Step s;
+        s.type = ST_RING; s.ns = 1;
+        memset(&s.rp, 0, sizeof(s.rp));
+        s.rp.n = n;
+        const size_t w = 2 * c->rsize;
+        s.rp.whole = ((size_t)1 << n) * w <= 96 * 1024;
+        s.rp.t = std::min(tile_tmax(c, 1), n - 1);
+        passes.push_back(s);
+      }
+      const bool to_ck = ck_slot.count(l) > 0;
+      for (size_t i = 0; i < passes.size(); ++i) {
+        Step& s = passes[i];
+        s.layer = l;
+        s.s0 = cur;
+        const bool last = i + 1 == passes.size();
+        const bool inplace_ok = s.type != ST_RING;
+        if (last && to_ck) s.d0 = B_CKPT + ck_slot[l];
+        else if (inplace_ok && (cur == A || cur == Bb)) s.d0 = cur;
+        else if (cur == A || cur == Bb) s.d0 = other(cur);
+        else s.d0 = A;
+        cur = s.d0;
+        p.fwd.push_back(s);
+      }
+    }
+    // rename so that the final state lands in psi_out
+    const int fin = cur;  // A or B (the last layer is never checkpointed)
+    for (auto& s : p.fwd) {
+      auto ren = [&](int& b) {
+        if (b == fin) b = B_PSIOUT;
+        else if (b == A || b == Bb) b = B_RUN0;
+      };
+      ren(s.s0);
+      ren(s.d0);
+    }
+    if (fin >= B_CKPT) {
+      // only when the circuit is the product init alone with a checkpoint: not produced
+    }
+
+    // ---------------- backward ----------------
+    // need[l]: some layer <= l has gradients
+    std::vector<int> need(L, 0);
+    for (int l = 0; l < L; ++l) need[l] = (l > 0 ? need[l - 1] : 0) || (LI[l].diff && LI[l].nparams > 0);
+    {
+      Step s;
+      s.type = ST_LAMINIT;
+      s.cb = std::min(n, 12);
+      s.s0 = B_PSIOUT;
+      s.d1 = B_LAM0;
+      p.bwd.push_back(s);
+    }
+    int cp = B_PSIOUT, cl = B_LAM0;
+    long long part_off = 0;
+    auto isrun = [](int x) { return x == B_RUN0 || x == B_RUN1; };
+    auto orun = [](int x) { return x == B_RUN0 ? B_RUN1 : B_RUN0; };
+    auto olam = [](int x) { return x == B_LAM0 ? B_LAM1 : B_LAM0; };
+    for (int l = L - 1; l >= 0; --l) {
+      if (!need[l]) break;
+      const LayerInfo& Li = LI[l];
+      const int srcp = ck_slot.count(l) ? B_CKPT + ck_slot[l] : cp;
+      std::vector<Step> passes;
+      std::vector<std::vector<int>> pslots;  // (pass index, slot, pidx)
+      if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
+        for (auto& tp : plan_tile_layer(c, Li, 2, pslots)) {
+          Step s;
+          s.type = ST_TILE; s.ns = 2; s.tp = tp; s.rb = std::min(reg_bits(c, 2), tp.t);
+          passes.push_back(s);
+        }
+      } else if (Li.cls == LC_DIAG || Li.cls == LC_XCOMP) {
+        Step s;
+        s.type = ST_DIAG; s.ns = 2;
+        memset(&s.dp, 0, sizeof(s.dp));
+        s.dp.n = n; s.dp.cb = std::min(n, 12); s.dp.zmode = Li.zmode;
+        s.dp.xcomp = Li.cls == LC_XCOMP; s.dp.has_phase = Li.has_phase; s.dp.tb = Li.tb;
+        s.dp.coef = Li.coef_off; s.dp.bstride = Li.coef_bstride; s.dp.nvals = n + 1;
+        passes.push_back(s);
+      } else if (Li.cls == LC_RING) {
+        Step s;
+        s.type = ST_RING; s.ns = 2;
+        memset(&s.rp, 0, sizeof(s.rp));
+        s.rp.n = n;
+        const size_t w = 2 * c->rsize;
+        s.rp.whole = ((size_t)1 << n) * w * 2 <= 96 * 1024;
+        s.rp.t = std::min(tile_tmax(c, 2), n - 1);
+        passes.push_back(s);
+      }
+      int sp = srcp;
+      for (size_t i = 0; i < passes.size(); ++i) {
+        Step& s = passes[i];
+        s.layer = l;
+        s.s0 = sp;
+        s.s1 = cl;
+        const bool inplace_ok = s.type != ST_RING;
+        s.d0 = (inplace_ok && isrun(sp)) ? sp : (isrun(sp) ? orun(sp) : B_RUN0);
+        s.d1 = inplace_ok ? cl : olam(cl);
+        if (l == 0 && i + 1 == passes.size() && s.type == ST_TILE) s.tp.store = 0;
+        // gradient bookkeeping
+        if (s.type == ST_TILE && s.tp.nslots > 0) {
+          const long long nblk = (long long)batch << (n - s.tp.t);
+          s.part_off = part_off;
+          std::vector<OutMap> outs;
+          for (auto& e : pslots)
+            if (e[0] == (int)i) outs.push_back(OutMap{0, e[1], e[2], 1.0});
+          add_job(p, RK_DIRECT, Li.source, part_off, nblk, s.tp.nslots, 1LL << (n - s.tp.t), outs);
+          part_off += nblk * s.tp.nslots;
+        } else if (s.type == ST_DIAG && Li.diff && Li.nparams > 0) {
+          const long long nblk = diag_grid(s.dp, batch);
+          s.part_off = part_off;
+          std::vector<OutMap> outs;
+          for (int j = 0; j < Li.nparams; ++j)
+            outs.push_back(OutMap{0, diag_zbit(Li, n, j), Li.offset + j, Li.gscale});
+          add_job(p, RK_MARGINAL, Li.source, part_off, nblk, n + 1, nblk / batch, outs);
+          part_off += nblk * (n + 1);
+        } else if (s.type == ST_DIAG) {
+          s.part_off = -1;  // no gradient: marginals go to a scratch region
+        }
+        sp = s.d0;
+        cl = s.d1;
+        p.bwd.push_back(s);
+      }
+      cp = sp;
+    }
+    // diag passes without gradients still write marginals: give them a scratch region
+    long long scratch_need = 0;
+    for (auto& s : p.bwd)
+      if (s.type == ST_DIAG && s.part_off < 0) scratch_need = std::max(scratch_need, diag_grid(s.dp, batch) * (n + 1));
+    for (auto& s : p.bwd)
+      if (s.type == ST_DIAG && s.part_off < 0) s.part_off = part_off;
+    part_off += scratch_need;
+    // <Z> partials (forward, ez requested)
+    const int cbe = std::min(n, 12);
+    const long long ez_need = ((long long)batch << (n - cbe)) * (n + 1);
+    p.part_doubles = (size_t)std::max(part_off, ez_need);
+
+    // workspace layout
+    p.off_pv = off;
+    off = align256(off + (size_t)batch * n * 4 * c->rsize);
+    p.off_part = off;
+    off = align256(off + p.part_doubles * 8);
+    p.off_V = off;
+    off = align256(off + (size_t)std::max<long long>(p.nrows, 1) * 8);
+    p.off_ckpt = off;
+    off = align256(off + (size_t)p.nckpt * p.S);
+    p.off_run0 = off;
+    off = align256(off + p.S);
+    p.ws_fwd = off;
+    p.off_run1 = off;
+    off = align256(off + p.S);
+    p.off_lam0 = off;
+    off = align256(off + p.S);
+    p.off_lam1 = off;
+    off = align256(off + p.S);
+    p.ws_bwd = off;
+  }
+
+  // finalize groups: serial when two jobs write the same output
+  {
+    std::map<std::pair<int, int>, int> seen;
+    for (auto& o : p.outs) {
+      auto key = std::make_pair(p.jobs[o.job].source, o.pidx);
+      if (seen.count(key) && seen[key] != o.job) p.overlap = true;
+      seen[key] = o.job;
+    }
+    if (!p.jobs.empty()) {
+      if (p.overlap) {
+        for (size_t j = 0; j < p.jobs.size(); ++j) p.job_groups.push_back({(int)j});
+      } else {
+        std::vector<int> all;
+        for (size_t j = 0; j < p.jobs.size(); ++j) all.push_back((int)j);
+        p.job_groups.push_back(all);
+      }
+    }
+  }
+  return P;
+}
+
+qc_status upload_plan(Plan& p) {
+  if (p.dev) return QC_OK;
+  // layout: coef jobs | jobs | row0 | out0 (per group) | outs | prog
+  std::vector<char> host;
+  auto put = [&](const void* src, size_t bytes) {
+    size_t o = align256(host.size());
+    host.resize(o + bytes);
+    if (bytes) memcpy(host.data() + o, src, bytes);
+    return o;
+  };
+  size_t o_cj = put(p.coef_jobs.data(), p.coef_jobs.size() * sizeof(CoefJob));
+  size_t o_j = put(p.jobs.data(), p.jobs.size() * sizeof(RedJob));
+  size_t o_r = put(p.row0.data(), p.row0.size() * sizeof(long long));
+  std::vector<RedOut> ro;
+  for (auto& o : p.outs) {
+    RedOut r;
+    r.val = o.val;
+    r.pidx = o.pidx;
+    r.scale = o.scale;
+    ro.push_back(r);
+  }
+  // outputs are ordered by job; k_finalize maps a flat output id to its job
+  std::vector<int> out0;
+  for (auto& J : p.jobs) out0.push_back(J.first);
+  size_t o_o0 = put(out0.data(), out0.size() * sizeof(int));
+  size_t o_ro = put(ro.data(), ro.size() * sizeof(RedOut));
+  size_t o_pr = put(p.prog.data(), p.prog.size() * sizeof(SmemLayer));
+  size_t bytes = std::max<size_t>(host.size(), 256);
+  cudaError_t e = cudaMalloc(&p.dev, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(plan tables)");
+  e = cudaMemcpy(p.dev, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(plan tables)");
+  char* d = (char*)p.dev;
+  p.d_coef_jobs = (CoefJob*)(d + o_cj);
+  p.d_jobs = (RedJob*)(d + o_j);
+  p.d_row0 = (long long*)(d + o_r);
+  p.d_out0 = (int*)(d + o_o0);
+  p.d_outs = (RedOut*)(d + o_ro);
+  p.d_prog = (SmemLayer*)(d + o_pr);
+  p.dev_bytes = bytes;
+  return QC_OK;
+}
+
+qc_status get_plan(qc_circuit* c, int batch, Plan** out) {
+  auto it = c->plans.find(batch);
+  if (it == c->plans.end()) {
+    auto P = build_plan(c, batch);
+    it = c->plans.emplace(batch, std::move(P)).first;
+  }
+  *out = it->second.get();
+  return QC_OK;
+}
+
+template <class R>
+qc_status run_coef(qc_circuit* c, Plan& p, int batch, const double* x, const double* theta,
+                   char* ws, cudaStream_t st) {
+  if (p.coef_jobs.empty()) return QC_OK;
+  ProfScope ps(PC_COEF, 0, st);
+  cudaError_t e = launch_coef<R>(p.d_coef_jobs, (int)p.coef_jobs.size(), c->n, batch, c->n_in, x,
+                                 theta, ws + p.off_coef, st);
+  if (e != cudaSuccess) return cuda_fail(e, "coef kernel");
+  return QC_OK;
+}
+
+struct Bufs {
+  void* b[32];
+};
+
+template <class R>
+qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int batch,
+                    const double* x, const double* theta, const double* gez, void* psi_out,
+                    char* ws, cudaStream_t st) {
+  Bufs B;
+  memset(&B, 0, sizeof(B));
+  B.b[B_PSIOUT] = psi_out;
+  B.b[B_RUN0] = ws + p.off_run0;
+  B.b[B_RUN1] = ws + p.off_run1;
+  B.b[B_LAM0] = ws + p.off_lam0;
+  B.b[B_LAM1] = ws + p.off_lam1;
+  auto buf = [&](int id) -> void* {
+    if (id == B_NONE) return nullptr;
+    if (id >= B_CKPT) return ws + p.off_ckpt + (size_t)(id - B_CKPT) * p.S;
+    return B.b[id];
+  };
+  const char* coef = ws + p.off_coef;
+  double* part = (double*)(ws + p.off_part);
+  const double S = (double)p.S;
+  for (const Step& s : steps) {
+    cudaError_t e = cudaSuccess;
+    // algorithmic bytes of one launch: every pass reads and writes each state once
+    const double passb = s.ns == 2 ? (s.type == ST_TILE && !s.tp.store ? 2 * S : 4 * S) : 2 * S;
+    switch (s.type) {
+      case ST_PRODINIT: {
+        ProfScope ps(PC_PRODINIT, S, st, 2);
+        e = launch_prodvec<R>(p.pv, c->n, batch, c->n_in, x, theta, ws + p.off_pv, st);
+        if (e == cudaSuccess) e = launch_prodinit<R>(c->n, s.cb, batch, ws + p.off_pv, buf(s.d0), st);
+        break;
+      }
+      case ST_TILE: {
+        ProfScope ps(s.ns == 2 ? PC_TILE_B : PC_TILE_F, passb, st);
+        e = launch_tile<R>(s.tp, s.rb, s.ns, batch, coef, buf(s.s0), buf(s.d0), buf(s.s1), buf(s.d1),
+                           part + s.part_off, st);
+        break;
+      }
+      case ST_DIAG: {
+        ProfScope ps(s.ns == 2 ? PC_DIAG_B : PC_DIAG_F, passb, st);
+        e = launch_diag<R>(s.dp, s.ns, batch, coef, buf(s.s0), buf(s.d0), buf(s.s1), buf(s.d1),
+                           part + s.part_off, st);
+        break;
+      }
+      case ST_RING: {
+        ProfScope ps(s.ns == 2 ? PC_RING_B : PC_RING_F, passb, st);
+        e = launch_ring<R>(s.rp, s.ns, batch, buf(s.s0), buf(s.d0), buf(s.s1), buf(s.d1), st);
+        break;
+      }
+      case ST_LAMINIT: {
+        ProfScope ps(PC_LAMINIT, 2 * S, st);
+        e = launch_laminit<R>(c->n, s.cb, batch, gez, buf(s.s0), buf(s.d1), st);
+        break;
+      }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "layer kernel launch");
+  }
+  return QC_OK;
+}
+
+qc_status run_reduce(qc_circuit* c, Plan& p, int batch, char* ws, double* d_theta, double* d_x,
+                     cudaStream_t st) {
+  if (p.jobs.empty()) return QC_OK;
+  const double* part = (const double*)(ws + p.off_part);
+  double* V = (double*)(ws + p.off_V);
+  for (auto& g : p.job_groups) {
+    // a group is a contiguous run of jobs
+    const int j0 = g.front(), nj = (int)g.size();
+    long long rows = 0;
+    int nout = 0;
+    for (int j : g) { rows += (long long)batch * p.jobs[j].nvals; nout += p.jobs[j].nout; }
+    ProfScope ps(PC_REDUCE, 0, st, 2);
+    cudaError_t e = launch_reduce(p.d_jobs + j0, p.d_row0 + j0, p.d_out0 + j0, nj, p.row0[j0], rows,
+                                  p.jobs[j0].first, nout, p.d_outs, batch, c->n_in, part, V,
+                                  d_theta, d_x, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce kernels");
+  }
+  return QC_OK;
+}
+
+qc_status check_common(qc_circuit* c, int batch) {
+  if (!c) return fail(QC_ERR_INVALID, "circuit handle is NULL");
+  if (batch <= 0) return fail(QC_ERR_INVALID, "batch must be positive");
+  if ((size_t)batch * ((size_t)1 << c->n) > ((size_t)1 << 40)) return fail(QC_ERR_INVALID, "batch * 2^n too large");
+  return QC_OK;
+}
+
+template <class R>
+qc_status forward_impl(qc_circuit* c, int batch, const double* x, const double* theta, void* psi_out,
+                       double* ez, void* workspace, size_t wbytes, cudaStream_t st) {
+  Plan* p;
+  qc_status s = get_plan(c, batch, &p);
+  if (s != QC_OK) return s;
+  if (wbytes < p->ws_fwd) return fail(QC_ERR_OOM, "workspace smaller than qc_workspace_bytes");
+  if ((uintptr_t)workspace % 256) return fail(QC_ERR_INVALID, "workspace must be 256-byte aligned");
+  if ((uintptr_t)psi_out % 16) return fail(QC_ERR_INVALID, "psi_out must be 16-byte aligned");
+  s = upload_plan(*p);
+  if (s != QC_OK) return s;
+  char* ws = (char*)workspace;
+  s = run_coef<R>(c, *p, batch, x, theta, ws, st);
+  if (s != QC_OK) return s;
+  if (p->smem) {
+    ProfScope ps(PC_SMEM_F, (double)p->S, st);
+    cudaError_t e = launch_smem<R>(p->d_prog, (int)p->prog.size(), c->n, batch, 0, ws + p->off_coef,
+                                   nullptr, psi_out, ez, nullptr, nullptr, p->nslots, st);
+    if (e != cudaSuccess) return cuda_fail(e, "whole-circuit forward kernel");
+  } else {
+    s = run_steps<R>(c, *p, p->fwd, batch, x, theta, nullptr, psi_out, ws, st);
+    if (s != QC_OK) return s;
+    if (ez) {
+      const int cbe = std::min(c->n, 12);
+      ProfScope ps(PC_EXPECT, (double)p->S, st, 2);
+      cudaError_t e = launch_expect<R>(c->n, cbe, batch, psi_out, (double*)(ws + p->off_part), ez, st);
+      if (e != cudaSuccess) return cuda_fail(e, "expect kernel");
+    }
+  }
+  c->last_ws = workspace;
+  c->last_batch = batch;
+  return QC_OK;
+}
+
+template <class R>
+qc_status backward_impl(qc_circuit* c, int batch, const double* x, const double* theta,
+                        const void* psi_out, const double* gez, double* d_theta, double* d_x,
+                        void* workspace, size_t wbytes, cudaStream_t st) {
+  Plan* p;
+  qc_status s = get_plan(c, batch, &p);
+  if (s != QC_OK) return s;
+  if (wbytes < p->ws_bwd) return fail(QC_ERR_OOM, "workspace smaller than qc_workspace_bytes");
+  if ((uintptr_t)workspace % 256) return fail(QC_ERR_INVALID, "workspace must be 256-byte aligned");
+  if (p->nckpt > 0 && (c->last_ws != workspace || c->last_batch != batch))
+    return fail(QC_ERR_INVALID, "checkpointed backward needs the workspace of the preceding forward");
+  s = upload_plan(*p);
+  if (s != QC_OK) return s;
+  char* ws = (char*)workspace;
+  cudaError_t e;
+  if (d_theta && c->n_theta > 0) {
+    e = cudaMemsetAsync(d_theta, 0, sizeof(double) * c->n_theta, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset d_theta");
+  }
+  if (d_x && c->n_in > 0) {
+    e = cudaMemsetAsync(d_x, 0, sizeof(double) * c->n_in * (size_t)batch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset d_x");
+  }
+  s = run_coef<R>(c, *p, batch, x, theta, ws, st);
+  if (s != QC_OK) return s;
+  if (p->smem) {
+    ProfScope ps(PC_SMEM_B, (double)p->S, st);
+    e = launch_smem<R>(p->d_prog, (int)p->prog.size(), c->n, batch, 1, ws + p->off_coef, psi_out,
+                       nullptr, nullptr, gez, (double*)(ws + p->off_part), p->nslots, st);
+    if (e != cudaSuccess) return cuda_fail(e, "whole-circuit backward kernel");
+  } else {
+    s = run_steps<R>(c, *p, p->bwd, batch, x, theta, gez, const_cast<void*>(psi_out), ws, st);
+    if (s != QC_OK) return s;
+  }
+  return run_reduce(c, *p, batch, ws, d_theta, d_x, st);
+}
+
+int layer_class(int kind) {
+  switch (kind) {
+    case QC_L_RX: case QC_L_RY: case QC_L_SX: case QC_L_GPI2: return LC_ROT1;
+    case QC_L_RZ: case QC_L_ISINGZZ_RING: return LC_DIAG;
+    case QC_L_CNOT_RING: return LC_RING;
+    case QC_L_X: case QC_L_GPI: return LC_XCOMP;
+    case QC_L_MS_BRICK: case QC_L_ECR_BRICK: return LC_DENSE2;
+  }
+  return -1;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+QC_API int qc_version(void) { return 100; }
+
+QC_API void qc_default_options(qc_options* opt) {
+  if (!opt) return;
+  opt->ckpt_every = -1;
+  opt->path = 0;
+  opt->fuse = 1;
+  opt->reserved = 0;
+}
+
+QC_API const char* qc_last_error(void) { return g_last_error.c_str(); }
+
+QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_layers,
+                           const qc_options* opt, qc_circuit** out) {
+  if (!out) return fail(QC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > kMaxQubits) return fail(QC_ERR_INVALID, "n must be in [1, 30]");
+  if (dtype != QC_C64 && dtype != QC_C128) return fail(QC_ERR_INVALID, "unknown dtype");
+  if (n_layers < 0 || (n_layers > 0 && !layers)) return fail(QC_ERR_INVALID, "bad layer list");
+  qc_options o;
+  qc_default_options(&o);
+  if (opt) o = *opt;
+  if (o.path < 0 || o.path > 2) return fail(QC_ERR_INVALID, "options.path must be 0, 1 or 2");
+  if (o.ckpt_every < -1) return fail(QC_ERR_INVALID, "options.ckpt_every must be >= -1");
+  auto c = std::make_unique<qc_circuit>();
+  c->n = n;
+  c->dtype = dtype;
+  c->rsize = dtype == QC_C64 ? 4 : 8;
+  c->opt = o;
+  if (o.path == 1 && !smem_fits(c.get()))
+    return fail(QC_ERR_UNSUPPORTED, "whole-circuit shared-memory path needs n <= 13 (c64) / 12 (c128)");
+  for (int l = 0; l < n_layers; ++l) {
+    const qc_layer& in = layers[l];
+    LayerInfo L;
+    memset(&L, 0, sizeof(L));
+    L.kind = in.kind;
+    L.source = in.source;
+    L.offset = in.offset;
+    L.parity = in.parity;
+    L.cls = layer_class(in.kind);
+    if (L.cls < 0) return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unknown kind");
+    if (in.source < QC_SRC_NONE || in.source > QC_SRC_INPUT)
+      return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unknown source");
+    if ((in.kind == QC_L_CNOT_RING || in.kind == QC_L_ISINGZZ_RING) && n < 2)
+      return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": ring layers need n >= 2");
+    if (in.kind == QC_L_MS_BRICK || in.kind == QC_L_ECR_BRICK) {
+      if (in.parity != 0 && in.parity != 1)
+        return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": brick parity must be 0 or 1");
+      L.ngates = std::max(0, (n - in.parity) / 2);
+    } else if (L.cls == LC_ROT1) {
+      L.ngates = n;
+    } else {
+      L.ngates = n;
+    }
+    switch (in.kind) {
+      case QC_L_RX: case QC_L_RY: case QC_L_RZ: case QC_L_GPI: case QC_L_GPI2: case QC_L_ISINGZZ_RING:
+        L.nparams = n; break;
+      case QC_L_MS_BRICK: L.nparams = 3 * L.ngates; break;
+      default: L.nparams = 0;
+    }
+    if (L.nparams == 0 && in.source != QC_SRC_NONE)
+      return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unparametrised kind needs source NONE");
+    if (in.source != QC_SRC_NONE && in.offset < 0)
+      return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": negative offset");
+    L.diff = (in.source == QC_SRC_THETA || in.source == QC_SRC_INPUT) && L.nparams > 0;
+    L.per_sample = in.source == QC_SRC_INPUT && L.nparams > 0;
+    L.real = in.kind == QC_L_RY;
+    L.zmode = in.kind == QC_L_ISINGZZ_RING ? Z_RINGXOR : Z_IDENT;
+    L.has_phase = (L.cls == LC_DIAG) || in.kind == QC_L_GPI;
+    L.gscale = in.kind == QC_L_GPI ? -4.0 * 3.14159265358979323846 : 1.0;
+    L.tb = (n + kDiagTables - 1) / kDiagTables;
+    if (L.tb < 1) L.tb = 1;
+    if (in.source == QC_SRC_THETA) c->n_theta = std::max(c->n_theta, in.offset + L.nparams);
+    if (in.source == QC_SRC_INPUT) c->n_in = std::max(c->n_in, in.offset + L.nparams);
+    c->layers.push_back(L);
+  }
+  *out = c.release();
+  return QC_OK;
+}
+
+QC_API qc_status qc_destroy(qc_circuit* c) {
+  if (!c) return QC_OK;
+  bool any_dev = c->exp_scratch != nullptr;
+  for (auto& kv : c->plans) any_dev = any_dev || kv.second->dev;
+  if (any_dev) cudaDeviceSynchronize();
+  for (auto& kv : c->plans)
+    if (kv.second->dev) cudaFree(kv.second->dev);
+  if (c->exp_scratch) cudaFree(c->exp_scratch);
+  delete c;
+  return QC_OK;
+}
+
+QC_API qc_status qc_num_params(const qc_circuit* c, int* n_theta, int* n_in) {
+  if (!c) return fail(QC_ERR_INVALID, "circuit handle is NULL");
+  if (n_theta) *n_theta = c->n_theta;
+  if (n_in) *n_in = c->n_in;
+  return QC_OK;
+}
+
+QC_API qc_status qc_workspace_bytes(const qc_circuit* cc, int batch, size_t* bytes) {
+  qc_circuit* c = const_cast<qc_circuit*>(cc);
+  qc_status s = check_common(c, batch);
+  if (s != QC_OK) return s;
+  if (!bytes) return fail(QC_ERR_INVALID, "bytes is NULL");
+  Plan* p;
+  s = get_plan(c, batch, &p);
+  if (s != QC_OK) return s;
+  *bytes = std::max(p->ws_fwd, p->ws_bwd);
+  return QC_OK;
+}
+
+QC_API qc_status qc_forward(qc_circuit* c, int batch, const double* x, const double* theta,
+                            void* psi_out, double* ez, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+  qc_status s = check_common(c, batch);
+  if (s != QC_OK) return s;
+  if (!psi_out) return fail(QC_ERR_INVALID, "psi_out is NULL");
+  if (!workspace) return fail(QC_ERR_INVALID, "workspace is NULL");
+  if (c->n_in > 0 && !x) return fail(QC_ERR_INVALID, "circuit reads x but x is NULL");
+  if (c->n_theta > 0 && !theta) return fail(QC_ERR_INVALID, "circuit reads theta but theta is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->dtype == QC_C64) return forward_impl<float>(c, batch, x, theta, psi_out, ez, workspace, workspace_bytes, st);
+  return forward_impl<double>(c, batch, x, theta, psi_out, ez, workspace, workspace_bytes, st);
+}
+
+QC_API qc_status qc_expect_z(qc_circuit* c, int batch, const void* psi, double* ez, void* stream) {
+  qc_status s = check_common(c, batch);
+  if (s != QC_OK) return s;
+  if (!psi || !ez) return fail(QC_ERR_INVALID, "psi and ez must be non-NULL");
+  const int n = c->n, cb = std::min(n, 12);
+  const size_t need = (size_t)(((long long)batch << (n - cb)) * (n + 1)) * sizeof(double);
+  if (need > c->exp_scratch_bytes) {
+    if (c->exp_scratch) {
+      cudaDeviceSynchronize();
+      cudaFree(c->exp_scratch);
+      c->exp_scratch = nullptr;
+      c->exp_scratch_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->exp_scratch, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(expect scratch)");
+    c->exp_scratch_bytes = need;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ProfScope ps(PC_EXPECT, (double)batch * ((size_t)1 << n) * 2 * c->rsize, st, 2);
+  cudaError_t e = c->dtype == QC_C64
+                      ? launch_expect<float>(n, cb, batch, psi, (double*)c->exp_scratch, ez, st)
+                      : launch_expect<double>(n, cb, batch, psi, (double*)c->exp_scratch, ez, st);
+  if (e != cudaSuccess) return cuda_fail(e, "expect kernel");
+  return QC_OK;
+}
+
+QC_API qc_status qc_backward(qc_circuit* c, int batch, const double* x, const double* theta,
+                             const void* psi_out, const double* g_ez, double* d_theta, double* d_x,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+  qc_status s = check_common(c, batch);
+  if (s != QC_OK) return s;
+  if (!psi_out || !g_ez) return fail(QC_ERR_INVALID, "psi_out and g_ez must be non-NULL");
+  if (!workspace) return fail(QC_ERR_INVALID, "workspace is NULL");
+  if (c->n_in > 0 && !x) return fail(QC_ERR_INVALID, "circuit reads x but x is NULL");
+  if (c->n_theta > 0 && !theta) return fail(QC_ERR_INVALID, "circuit reads theta but theta is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->dtype == QC_C64)
+    return backward_impl<float>(c, batch, x, theta, psi_out, g_ez, d_theta, d_x, workspace, workspace_bytes, st);
+  return backward_impl<double>(c, batch, x, theta, psi_out, g_ez, d_theta, d_x, workspace, workspace_bytes, st);
+}
+
+QC_API qc_status qc_staging_bytes(const qc_circuit* c, int batch, size_t* bytes) {
+  if (!c || batch <= 0 || !bytes) return fail(QC_ERR_INVALID, "bad arguments");
+  size_t b = 0;
+  b += align256((size_t)batch * std::max(c->n_in, 1) * 8);  // x
+  b += align256((size_t)std::max(c->n_theta, 1) * 8);       // theta
+  b += align256((size_t)batch * c->n * 8);                  // g
+  b += align256((size_t)batch * c->n * 8);                  // ez
+  b += align256((size_t)std::max(c->n_theta, 1) * 8);       // d_theta
+  b += align256((size_t)batch * std::max(c->n_in, 1) * 8);  // d_x
+  *bytes = b;
+  return QC_OK;
+}
+
+QC_API qc_status qc_step_host(qc_circuit* c, int batch, const double* x_h, const double* th_h,
+                              const double* g_h, double* ez_h, double* dth_h, double* dx_h,
+                              void* psi_out, void* workspace, size_t wbytes, void* staging,
+                              void* stream) {
+  qc_status s = check_common(c, batch);
+  if (s != QC_OK) return s;
+  if (!staging || !g_h) return fail(QC_ERR_INVALID, "staging and g_ez_host must be non-NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* sp = (char*)staging;
+  size_t o = 0;
+  double* x = (double*)(sp + o); o += align256((size_t)batch * std::max(c->n_in, 1) * 8);
+  double* th = (double*)(sp + o); o += align256((size_t)std::max(c->n_theta, 1) * 8);
+  double* g = (double*)(sp + o); o += align256((size_t)batch * c->n * 8);
+  double* ez = (double*)(sp + o); o += align256((size_t)batch * c->n * 8);
+  double* dth = (double*)(sp + o); o += align256((size_t)std::max(c->n_theta, 1) * 8);
+  double* dx = (double*)(sp + o);
+  cudaError_t e = cudaSuccess;
+  if (c->n_in > 0 && x_h) e = cudaMemcpyAsync(x, x_h, (size_t)batch * c->n_in * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && c->n_theta > 0 && th_h) e = cudaMemcpyAsync(th, th_h, (size_t)c->n_theta * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g, g_h, (size_t)batch * c->n * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "host->device copy");
+  s = qc_forward(c, batch, x, th, psi_out, ez, workspace, wbytes, stream);
+  if (s != QC_OK) return s;
+  s = qc_backward(c, batch, x, th, psi_out, g, dth, dx, workspace, wbytes, stream);
+  if (s != QC_OK) return s;
+  if (ez_h) e = cudaMemcpyAsync(ez_h, ez, (size_t)batch * c->n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && dth_h && c->n_theta > 0) e = cudaMemcpyAsync(dth_h, dth, (size_t)c->n_theta * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && dx_h && c->n_in > 0) e = cudaMemcpyAsync(dx_h, dx, (size_t)batch * c->n_in * 8, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "device->host copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return QC_OK;
+}
+
+QC_API qc_status qc_wait(void* stream, int timeout_ms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  e = cudaEventRecord(ev, st);
+  if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(e, "cudaEventRecord"); }
+  // host-side polling with a limit; the device never spins
+  const long long limit_us = (long long)timeout_ms * 1000;
+  long long waited = 0;
+  while (true) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(e, "cudaEventQuery"); }
+    if (waited >= limit_us) { cudaEventDestroy(ev); return fail(QC_ERR_TIMEOUT, "stream still busy after timeout"); }
+    struct timespec ts = {0, 200000};
+    nanosleep(&ts, nullptr);
+    waited += 200;
+  }
+  cudaEventDestroy(ev);
+  return QC_OK;
+}
+
+QC_API unsigned long long qc_launch_count(void) { return g_launches; }
+
+QC_API qc_status qc_profile_enable(int on) {
+  g_prof = on != 0;
+  g_nrec = 0;
+  return QC_OK;
+}
+
+QC_API qc_status qc_profile_summary(char* buf, size_t len) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  double ms[PC_N] = {0}, bytes[PC_N] = {0};
+  long long cnt[PC_N] = {0};
+  for (size_t i = 0; i < g_nrec; ++i) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, g_recs[i].a, g_recs[i].b) != cudaSuccess) continue;
+    ms[g_recs[i].cls] += t;
+    bytes[g_recs[i].cls] += g_recs[i].bytes;
+    cnt[g_recs[i].cls] += 1;
+  }
+  std::string o;
+  char line[256];
+  for (int k = 0; k < PC_N; ++k) {
+    if (!cnt[k]) continue;
+    snprintf(line, sizeof line, "%s %lld %.6f %.6e\n", kProfNames[k], cnt[k], ms[k], bytes[k]);
+    o += line;
+  }
+  if (buf && len) {
+    size_t k = std::min(len - 1, o.size());
+    memcpy(buf, o.data(), k);
+    buf[k] = 0;
+  }
+  return QC_OK;
+}
+
+// Text description of the plan for `batch` (host only; for tests and tools).
+QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, size_t len) {
+  qc_circuit* c = const_cast<qc_circuit*>(cc);
+  qc_status s = check_common(c, batch);
+  if (s != QC_OK) return s;
+  Plan* p;
+  get_plan(c, batch, &p);
+  std::string o;
+  char line[512];
+  snprintf(line, sizeof line, "path=%s nlead=%d nckpt=%d ws_fwd=%zu ws_bwd=%zu jobs=%zu outs=%zu overlap=%d\n",
+           p->smem ? "smem" : "layer", p->nlead, p->nckpt, p->ws_fwd, p->ws_bwd, p->jobs.size(),
+           p->outs.size(), (int)p->overlap);
+  o += line;
+  auto dump = [&](const char* tag, const std::vector<Step>& v) {
+    for (auto& st : v) {
+      if (st.type == ST_TILE) {
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d rounds=%d ops=%d slots=%d store=%d src=%d dst=%d",
+                 tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.tp.nrounds, st.tp.nops, st.tp.nslots,
+                 st.tp.store, st.s0, st.d0);
+        o += line;
+        for (int k = 0; k < st.tp.nops; ++k) {
+          snprintf(line, sizeof line, " [l=%d%s np=%d]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "", st.tp.ops[k].np);
+          o += line;
+        }
+        o += "\n";
+      } else if (st.type == ST_DIAG) {
+        snprintf(line, sizeof line, "%s layer=%d DIAG ns=%d xcomp=%d z=%d cb=%d src=%d dst=%d\n", tag, st.layer, st.ns,
+                 st.dp.xcomp, st.dp.zmode, st.dp.cb, st.s0, st.d0);
+        o += line;
+      } else if (st.type == ST_RING) {
+        snprintf(line, sizeof line, "%s layer=%d RING ns=%d whole=%d t=%d src=%d dst=%d\n", tag, st.layer, st.ns,
+                 st.rp.whole, st.rp.t, st.s0, st.d0);
+        o += line;
+      } else if (st.type == ST_PRODINIT) {
+        snprintf(line, sizeof line, "%s layer=%d PRODINIT dst=%d\n", tag, st.layer, st.d0);
+        o += line;
+      } else if (st.type == ST_LAMINIT) {
+        snprintf(line, sizeof line, "%s LAMINIT\n", tag);
+        o += line;
+      }
+    }
+  };
+  dump("F", p->fwd);
+  dump("B", p->bwd);
+  if (buf && len) {
+    size_t k = std::min(len - 1, o.size());
+    memcpy(buf, o.data(), k);
+    buf[k] = 0;
+  }
+  return QC_OK;
+}
+
+}  // extern "C"

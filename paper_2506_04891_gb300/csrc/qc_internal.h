@@ -1,0 +1,132 @@
+// Internal descriptors shared by the host planner (qc_api.cu) and the kernels
+// (qc_kernels.cu).  Plain structs: they are passed to kernels by value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qlayer.h"
+
+namespace qc {
+
+constexpr int kMaxQubits = 30;
+constexpr int kThreads = 256;        // block size of every pass kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxTileOps = 48;      // gate ops in one tile pass
+constexpr int kMaxRounds = 8;
+constexpr int kDiagTables = 3;       // diagonal phase = T0[z0] * T1[z1] * T2[z2]
+
+// Layer classes: how a layer is applied.
+enum LayerClass {
+  LC_ROT1 = 0,    // non-diagonal single-qubit gate on every qubit (RX, RY, SX, GPI2)
+  LC_DIAG = 1,    // diagonal phase (RZ, ISINGZZ_RING)
+  LC_RING = 2,    // CNOT ring permutation
+  LC_XCOMP = 3,   // index complement k -> ~k with an optional phase (X, GPI)
+  LC_DENSE2 = 4,  // two-qubit gates on a brick of qubit pairs (MS, ECR)
+};
+
+// z-transform of a diagonal layer: the phase is a product over the bits of z(k).
+enum ZMode { Z_IDENT = 0, Z_RINGXOR = 1 };
+
+// Coefficient records, in units of the state's real type R.
+constexpr int kRec1q = 16;    // M (2x2 complex) + A = M^dagger dM (2x2 complex)
+constexpr int kRec2q = 128;   // M (4x4 complex) + up to three A (4x4 complex)
+
+struct LayerInfo {
+  int kind, source, offset, parity;
+  int cls;
+  int nparams;          // parameters read (0 if unparametrised)
+  int ngates;           // 1q: n; dense2: pairs; diag/xcomp: n phase bits
+  int diff;             // source is THETA or INPUT
+  int per_sample;       // source is INPUT
+  int real;             // ROT1 with a real matrix (RY)
+  int zmode;            // DIAG: ZMode
+  int has_phase;        // XCOMP: GPI has a phase, X none
+  double gscale;        // DIAG/XCOMP gradient g_j = gscale * (W - 2 M_{zbit(j)})
+  // device coefficient placement (R units, relative to the coefficient base)
+  long long coef_off;
+  long long coef_bstride;   // per-sample stride (0 when shared)
+  int tb;                   // DIAG/XCOMP: bits per table (tables of 2^tb complex)
+};
+
+// One gate op inside a tile pass.
+struct TileOp {
+  int16_t l;        // local bit (1q) or lower local bit of the pair (2q)
+  int8_t is2q;
+  int8_t real;      // 1q with a real matrix
+  int16_t np;       // gradient parameters produced (0, 1 or 3)
+  int16_t slot;     // first gradient slot in the pass's partial vector
+  int32_t soff;     // offset of the op's coefficients in the staged smem block (R units)
+  int32_t nco;      // number of R to stage
+  long long coef;   // coefficient offset (R units) for sample 0
+  long long bstride;// per-sample stride (0 = shared)
+};
+
+// A tile pass: the CTA loads 2^t amplitudes whose local bit l maps to global bit
+// l (l < c) or h0 + (l - c) (l >= c), applies rounds of register-blocked gate
+// ops, and stores them back.
+struct TilePass {
+  int n, t, c, h0;
+  int nrounds;
+  int8_t rlo[kMaxRounds];            // round r: register bits [rlo[r], rlo[r] + RB)
+  int16_t rop[kMaxRounds + 1];       // ops of round r: [rop[r], rop[r+1])
+  int nops;
+  int nslots;                        // gradient slots (bwd)
+  int store;                         // 0: gradient only, no store
+  int ncoef;                         // R units of staged coefficients
+  TileOp ops[kMaxTileOps];
+};
+
+// Diagonal / complement pass (elementwise).
+struct DiagPass {
+  int n;
+  int cb;            // chunk bits (CTA handles 2^cb contiguous amplitudes)
+  int zmode;         // ZMode
+  int xcomp;         // 1: out[k] = phase(~k) * in[~k]
+  int has_phase;
+  int tb;            // bits per table
+  long long coef;    // table offset (R units)
+  long long bstride; // per-sample stride of the tables
+  int nvals;         // bwd: 1 + n marginal values
+};
+
+struct RingPass {
+  int n;
+  int t;             // CTA covers 2^t amplitudes (two halves of 2^(t-1))
+  int whole;         // 1: whole state per CTA (n <= t)
+};
+
+// Reduction of per-CTA partials into parameter gradients.
+enum RedKind { RK_DIRECT = 0, RK_MARGINAL = 1 };
+struct RedJob {
+  long long part_off;  // offset (doubles) of the launch's partials, layout [nvals][nblk]
+  int nblk;            // CTAs of the launch
+  int nvals;
+  int blk_per_sample;
+  int kind;            // RedKind
+  int nout;            // gradient outputs of the job
+  int source;          // QC_SRC_THETA or QC_SRC_INPUT
+  int out_off;         // index of output 0 in theta / x[b]
+  int first;           // index of this job's first entry in the per-output map
+  int per_sample_out;  // 1 when every sample's CTA set must be reduced separately
+};
+// Per-output map entry: RK_DIRECT: value index; RK_MARGINAL: z-bit and scale.
+struct RedOut {
+  int val;             // DIRECT: value index; MARGINAL: z-bit p (value 1 + p)
+  int pidx;            // index in theta (THETA) or x[b] (INPUT)
+  double scale;        // MARGINAL: g = scale * (V[0] - 2 V[1 + p]); DIRECT: g = scale * V[val]
+};
+
+// Whole-circuit-in-shared-memory program (one CTA per sample).
+struct SmemLayer {
+  int cls;
+  int kind;
+  int real;
+  int zmode, has_phase, tb;
+  int ngates, np_per_gate, parity;
+  long long coef, bstride;
+  int slot;          // first gradient slot (per-sample partial vector), -1 if none
+  double gscale;
+};
+
+}  // namespace qc

@@ -1,0 +1,1469 @@
+// CUDA kernels of the layered state-vector simulator (sm_103a).
+//
+// State: psi[b][k] interleaved complex (float2 / double2), qubit q = bit n-1-q.
+// Every kernel here is bandwidth-shaped: a CTA streams a tile or a contiguous
+// chunk of one sample's state through shared memory or registers once.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "qc_gates.cuh"
+#include "qc_internal.h"
+#include "qc_kernels.h"
+
+namespace qc {
+
+template <class R> struct CT;
+template <> struct CT<float> { using C = float2; };
+template <> struct CT<double> { using C = double2; };
+template <class R> using cx = typename CT<R>::C;
+
+template <class R> __device__ __forceinline__ cx<R> mk(R a, R b) { cx<R> r; r.x = a; r.y = b; return r; }
+template <class R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <class R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
+  return mk<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// m * v + acc
+template <class R> __device__ __forceinline__ cx<R> cfma(cx<R> m, cx<R> v, cx<R> acc) {
+  return mk<R>(fma(m.x, v.x, fma(-m.y, v.y, acc.x)), fma(m.x, v.y, fma(m.y, v.x, acc.y)));
+}
+// conj(m) * v + acc
+template <class R> __device__ __forceinline__ cx<R> cfmac(cx<R> m, cx<R> v, cx<R> acc) {
+  return mk<R>(fma(m.x, v.x, fma(m.y, v.y, acc.x)), fma(m.x, v.y, fma(-m.y, v.x, acc.y)));
+}
+template <class R> __device__ __forceinline__ R re_cdot(cx<R> l, cx<R> v) {  // Re(conj(l) v)
+  return l.x * v.x + l.y * v.y;
+}
+template <class R> __device__ __forceinline__ R im_cdot(cx<R> l, cx<R> v) {  // Im(conj(l) v)
+  return l.x * v.y - l.y * v.x;
+}
+template <class R> __device__ __forceinline__ cx<R> ldc(const R* p) { return mk<R>(p[0], p[1]); }
+
+// Shared-memory swizzle: spreads strided accesses over banks.
+__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 31); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Coefficients: gate matrices, generators, diagonal phase tables
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double param_of(const CoefJob& J, int b, int j, const double* x,
+                                           const double* theta, int n_in) {
+  if (J.source == QC_SRC_THETA) return theta[J.offset + j];
+  if (J.source == QC_SRC_INPUT) return x[(long long)b * n_in + J.offset + j];
+  return 0.0;
+}
+
+template <class R>
+__global__ void k_coef(const CoefJob* __restrict__ jobs, int njobs, int n, int batch, int n_in,
+                       const double* __restrict__ x, const double* __restrict__ theta,
+                       R* __restrict__ coef) {
+  const CoefJob J = jobs[blockIdx.x];
+  const int b = blockIdx.y;
+  if (!J.per_sample && b > 0) return;
+  R* out = coef + J.coef_off + (long long)b * J.bstride;
+  __shared__ dc dvec[kMaxQubits][2];
+  if (J.cls == LC_ROT1) {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      double t = param_of(J, b, q, x, theta, n_in);
+      dc M[4], D[4], A[4];
+      gate1q(J.kind, t, M);
+      dgate1q(J.kind, t, D);
+      mdag_mul(M, D, A, 2);
+      R* o = out + (long long)q * kRec1q;
+      for (int i = 0; i < 4; ++i) {
+        o[2 * i] = (R)M[i].x; o[2 * i + 1] = (R)M[i].y;
+        o[8 + 2 * i] = (R)A[i].x; o[8 + 2 * i + 1] = (R)A[i].y;
+      }
+    }
+  } else if (J.cls == LC_DENSE2) {
+    for (int g = threadIdx.x; g < J.ngates; g += blockDim.x) {
+      dc M[16], D[16], A[16];
+      R* o = out + (long long)g * kRec2q;
+      for (int i = 0; i < kRec2q; ++i) o[i] = (R)0;
+      if (J.kind == QC_L_MS_BRICK) {
+        double p0 = param_of(J, b, 3 * g, x, theta, n_in);
+        double p1 = param_of(J, b, 3 * g + 1, x, theta, n_in);
+        double th = param_of(J, b, 3 * g + 2, x, theta, n_in);
+        gate_ms(p0, p1, th, M);
+        for (int w = 0; w < 3; ++w) {
+          dgate_ms(p0, p1, th, w, D);
+          mdag_mul(M, D, A, 4);
+          for (int i = 0; i < 16; ++i) {
+            o[32 + 32 * w + 2 * i] = (R)A[i].x;
+            o[32 + 32 * w + 2 * i + 1] = (R)A[i].y;
+          }
+        }
+      } else {
+        gate_ecr(M);
+      }
+      for (int i = 0; i < 16; ++i) { o[2 * i] = (R)M[i].x; o[2 * i + 1] = (R)M[i].y; }
+    }
+  } else if (J.cls == LC_DIAG || J.cls == LC_XCOMP) {
+    if (!J.has_phase) return;
+    // per-bit phase pair d_p = (phase if z-bit p = 0, phase if z-bit p = 1)
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+      int j;
+      if (J.kind == QC_L_ISINGZZ_RING) j = ((n - 2 - p) % n + n) % n;
+      else j = n - 1 - p;
+      double t = param_of(J, b, j, x, theta, n_in);
+      if (J.kind == QC_L_GPI) {
+        dvec[p][0] = dexpi(2.0 * kPi * t);
+        dvec[p][1] = dexpi(-2.0 * kPi * t);
+      } else {  // RZ, IsingZZ: exp(-i t/2 * (+1 / -1))
+        dvec[p][0] = dexpi(-0.5 * t);
+        dvec[p][1] = dexpi(0.5 * t);
+      }
+    }
+    __syncthreads();
+    const int tb = J.tb, T = 1 << tb;
+    for (int e = threadIdx.x; e < kDiagTables * T; e += blockDim.x) {
+      int s = e / T, idx = e % T;
+      dc v = dmk(1, 0);
+      for (int i = 0; i < tb; ++i) {
+        int p = s * tb + i;
+        if (p >= n) break;
+        v = dmul(v, dvec[p][(idx >> i) & 1]);
+      }
+      out[2LL * e] = (R)v.x;
+      out[2LL * e + 1] = (R)v.y;
+    }
+  }
+}
+
+// Product state of the leading single-qubit layers: v[b][p] = M_m ... M_1 |0>
+// for qubit q = n-1-p (two complex numbers per qubit).
+template <class R>
+__global__ void k_prodvec(ProdVecJob P, int n, int batch, int n_in, const double* __restrict__ x,
+                          const double* __restrict__ theta, R* __restrict__ pv) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= batch * n) return;
+  int b = idx / n, q = idx % n;
+  dc v0 = dmk(1, 0), v1 = dmk(0, 0);
+  for (int l = 0; l < P.nl; ++l) {
+    CoefJob J;
+    J.source = P.source[l];
+    J.offset = P.offset[l];
+    double t = param_of(J, b, q, x, theta, n_in);
+    dc M[4];
+    gate1q(P.kind[l], t, M);
+    dc a = dadd(dmul(M[0], v0), dmul(M[1], v1));
+    dc c = dadd(dmul(M[2], v0), dmul(M[3], v1));
+    v0 = a; v1 = c;
+  }
+  int p = n - 1 - q;
+  R* o = pv + ((long long)b * n + p) * 4;
+  o[0] = (R)v0.x; o[1] = (R)v0.y; o[2] = (R)v1.x; o[3] = (R)v1.y;
+}
+
+// psi[b][k] = prod_p v[b][p][bit_p(k)], one contiguous chunk of 2^cb per CTA.
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* __restrict__ pv,
+                                                       cx<R>* __restrict__ psi) {
+  using C = cx<R>;
+  __shared__ C Ta[64], Tb[64];
+  const int nch_bits = n - cb;
+  const long long blk = blockIdx.x;
+  const int b = (int)(blk >> nch_bits);
+  const long long chunk = blk & ((1LL << nch_bits) - 1);
+  const long long base = chunk << cb;
+  const R* v = pv + (long long)b * n * 4;
+  const int la = cb < 6 ? cb : 6, lb = cb - la;
+  // constant factor of the chunk's fixed high bits
+  C H = mk<R>(1, 0);
+  for (int p = cb; p < n; ++p) {
+    int bit = (int)((base >> p) & 1);
+    H = cmul<R>(H, ldc<R>(v + p * 4 + 2 * bit));
+  }
+  for (int e = threadIdx.x; e < 128; e += blockDim.x) {
+    if (e < 64) {
+      C a = mk<R>(1, 0);
+      for (int i = 0; i < la; ++i) a = cmul<R>(a, ldc<R>(v + i * 4 + 2 * ((e >> i) & 1)));
+      Ta[e] = a;
+    } else {
+      int f = e - 64;
+      C a = H;
+      for (int i = 0; i < lb; ++i) a = cmul<R>(a, ldc<R>(v + (la + i) * 4 + 2 * ((f >> i) & 1)));
+      Tb[f] = a;
+    }
+  }
+  __syncthreads();
+  C* out = psi + ((long long)b << n) + base;
+  const int CH = 1 << cb, ma = (1 << la) - 1;
+  for (int i = threadIdx.x; i < CH; i += blockDim.x) out[i] = cmul<R>(Tb[i >> la], Ta[i & ma]);
+}
+
+// ---------------------------------------------------------------------------
+// Tile pass: register-blocked single-qubit and two-qubit gate ops
+// ---------------------------------------------------------------------------
+
+// forward single-qubit op on register bit I
+template <class R, int RB, int I>
+__device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
+  using C = cx<R>;
+  if (real) {
+    const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        C x0 = v[a], x1 = v[a | (1 << I)];
+        v[a] = mk<R>(fma(m00, x0.x, m01 * x1.x), fma(m00, x0.y, m01 * x1.y));
+        v[a | (1 << I)] = mk<R>(fma(m10, x0.x, m11 * x1.x), fma(m10, x0.y, m11 * x1.y));
+      }
+  } else {
+    const C m00 = ldc<R>(m), m01 = ldc<R>(m + 2), m10 = ldc<R>(m + 4), m11 = ldc<R>(m + 6);
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        C x0 = v[a], x1 = v[a | (1 << I)];
+        v[a] = cfma<R>(m01, x1, cmul<R>(m00, x0));
+        v[a | (1 << I)] = cfma<R>(m11, x1, cmul<R>(m10, x0));
+      }
+  }
+}
+
+// backward single-qubit op: undo M on psi and lambda, then accumulate
+// 2 Re <lambda| A |psi> on the gate's input side.
+template <class R, int RB, int I>
+__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, R* acc) {
+  using C = cx<R>;
+  if (real) {
+    // M^dagger = M^T for a real M
+    const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
+    const R a00 = m[8], a01 = m[10], a10 = m[12], a11 = m[14];
+    R g = 0;
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        const int a1 = a | (1 << I);
+        C x0 = p[a], x1 = p[a1];
+        C y0 = mk<R>(fma(m00, x0.x, m10 * x1.x), fma(m00, x0.y, m10 * x1.y));
+        C y1 = mk<R>(fma(m01, x0.x, m11 * x1.x), fma(m01, x0.y, m11 * x1.y));
+        p[a] = y0; p[a1] = y1;
+        C u0 = l[a], u1 = l[a1];
+        C w0 = mk<R>(fma(m00, u0.x, m10 * u1.x), fma(m00, u0.y, m10 * u1.y));
+        C w1 = mk<R>(fma(m01, u0.x, m11 * u1.x), fma(m01, u0.y, m11 * u1.y));
+        l[a] = w0; l[a1] = w1;
+        if (np) {
+          g += a00 * re_cdot<R>(w0, y0) + a01 * re_cdot<R>(w0, y1) + a10 * re_cdot<R>(w1, y0) +
+               a11 * re_cdot<R>(w1, y1);
+        }
+      }
+    if (np) acc[I * 3] += 2 * g;
+  } else {
+    const C m00 = ldc<R>(m), m01 = ldc<R>(m + 2), m10 = ldc<R>(m + 4), m11 = ldc<R>(m + 6);
+    const C a00 = ldc<R>(m + 8), a01 = ldc<R>(m + 10), a10 = ldc<R>(m + 12), a11 = ldc<R>(m + 14);
+    R g = 0;
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        const int a1 = a | (1 << I);
+        C x0 = p[a], x1 = p[a1];
+        // y = M^dagger x: y0 = conj(m00) x0 + conj(m10) x1; y1 = conj(m01) x0 + conj(m11) x1
+        C y0 = cfmac<R>(m10, x1, cfmac<R>(m00, x0, mk<R>(0, 0)));
+        C y1 = cfmac<R>(m11, x1, cfmac<R>(m01, x0, mk<R>(0, 0)));
+        p[a] = y0; p[a1] = y1;
+        C u0 = l[a], u1 = l[a1];
+        C w0 = cfmac<R>(m10, u1, cfmac<R>(m00, u0, mk<R>(0, 0)));
+        C w1 = cfmac<R>(m11, u1, cfmac<R>(m01, u0, mk<R>(0, 0)));
+        l[a] = w0; l[a1] = w1;
+        if (np) {
+          C t0 = cfma<R>(a01, y1, cmul<R>(a00, y0));
+          C t1 = cfma<R>(a11, y1, cmul<R>(a10, y0));
+          g += re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1);
+        }
+      }
+    if (np) acc[I * 3] += 2 * g;
+  }
+}
+
+// forward two-qubit op on register bits (I, I+1); 4x4 index = 2*bit(I+1) + bit(I)
+template <class R, int RB, int I>
+__device__ __forceinline__ void ap2(cx<R>* v, const R* m) {
+  using C = cx<R>;
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (3 << I))) {
+      C x[4], y[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) x[s] = v[a | (s << I)];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        C t = mk<R>(0, 0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(m + 2 * (r * 4 + s)), x[s], t);
+        y[r] = t;
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) v[a | (s << I)] = y[s];
+    }
+}
+
+template <class R, int RB, int I>
+__device__ __forceinline__ void bw2(cx<R>* p, cx<R>* l, const R* m, int np, R* acc) {
+  using C = cx<R>;
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (3 << I))) {
+      C x[4], u[4], y[4], w[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) { x[s] = p[a | (s << I)]; u[s] = l[a | (s << I)]; }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        C t = mk<R>(0, 0), z = mk<R>(0, 0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          C ms = ldc<R>(m + 2 * (s * 4 + r));  // (M^dagger)[r][s] = conj(M[s][r])
+          t = cfmac<R>(ms, x[s], t);
+          z = cfmac<R>(ms, u[s], z);
+        }
+        y[r] = t; w[r] = z;
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) { p[a | (s << I)] = y[s]; l[a | (s << I)] = w[s]; }
+      for (int k = 0; k < np; ++k) {
+        const R* A = m + 32 + 32 * k;
+        R g = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          C t = mk<R>(0, 0);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(A + 2 * (r * 4 + s)), y[s], t);
+          g += re_cdot<R>(w[r], t);
+        }
+        acc[I * 3 + k] += 2 * g;
+      }
+    }
+}
+
+template <class R, int NS, int RB>
+__device__ __forceinline__ void tile_dispatch(const TileOp& o, int i, cx<R>* v0, cx<R>* v1,
+                                              const R* mc, R* acc) {
+  if (NS == 1) {
+    if (!o.is2q) {
+      switch (i) {
+        case 0: ap1<R, RB, 0>(v0, mc, o.real); break;
+        case 1: if (RB > 1) ap1<R, RB, (RB > 1 ? 1 : 0)>(v0, mc, o.real); break;
+        case 2: if (RB > 2) ap1<R, RB, (RB > 2 ? 2 : 0)>(v0, mc, o.real); break;
+        case 3: if (RB > 3) ap1<R, RB, (RB > 3 ? 3 : 0)>(v0, mc, o.real); break;
+        case 4: if (RB > 4) ap1<R, RB, (RB > 4 ? 4 : 0)>(v0, mc, o.real); break;
+      }
+    } else {
+      switch (i) {
+        case 0: if (RB > 1) ap2<R, RB, 0>(v0, mc); break;
+        case 1: if (RB > 2) ap2<R, RB, (RB > 2 ? 1 : 0)>(v0, mc); break;
+        case 2: if (RB > 3) ap2<R, RB, (RB > 3 ? 2 : 0)>(v0, mc); break;
+        case 3: if (RB > 4) ap2<R, RB, (RB > 4 ? 3 : 0)>(v0, mc); break;
+      }
+    }
+  } else {
+    if (!o.is2q) {
+      switch (i) {
+        case 0: bw1<R, RB, 0>(v0, v1, mc, o.real, o.np, acc); break;
+        case 1: if (RB > 1) bw1<R, RB, (RB > 1 ? 1 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
+        case 2: if (RB > 2) bw1<R, RB, (RB > 2 ? 2 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
+        case 3: if (RB > 3) bw1<R, RB, (RB > 3 ? 3 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
+        case 4: if (RB > 4) bw1<R, RB, (RB > 4 ? 4 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
+      }
+    } else {
+      switch (i) {
+        case 0: if (RB > 1) bw2<R, RB, 0>(v0, v1, mc, o.np, acc); break;
+        case 1: if (RB > 2) bw2<R, RB, (RB > 2 ? 1 : 0)>(v0, v1, mc, o.np, acc); break;
+        case 2: if (RB > 3) bw2<R, RB, (RB > 3 ? 2 : 0)>(v0, v1, mc, o.np, acc); break;
+        case 3: if (RB > 4) bw2<R, RB, (RB > 4 ? 3 : 0)>(v0, v1, mc, o.np, acc); break;
+      }
+    }
+  }
+}
+
+// NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
+// lambda, accumulate gradient partials per CTA into part[slot][block]).
+template <class R, int NS, int RB>
+__global__ void __launch_bounds__(kThreads) k_tile(const __grid_constant__ TilePass P, const R* __restrict__ coef,
+                                                   const cx<R>* src0, cx<R>* dst0,
+                                                   const cx<R>* src1, cx<R>* dst1,
+                                                   double* __restrict__ part) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = P.t, n = P.n, c = P.c, h0 = P.h0;
+  const int T = 1 << t;
+  C* S0 = reinterpret_cast<C*>(smraw);
+  C* S1 = S0 + T;
+  R* sco = reinterpret_cast<R*>(S0 + NS * T);
+  double* sred = reinterpret_cast<double*>(sco + ((P.ncoef + 1) & ~1));
+
+  const int fb = n - t;
+  const long long tile = blockIdx.x;
+  const int b = (int)(tile >> fb);
+  const long long f = tile & ((1LL << fb) - 1);
+  const int m = t - c, gap = h0 - c;
+  const long long base = ((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m));
+  const long long soff = ((long long)b << n) + base;
+  const int cmask = (1 << c) - 1;
+
+  for (int k = 0; k < P.nops; ++k) {
+    const TileOp& o = P.ops[k];
+    const R* s = coef + o.coef + (long long)b * o.bstride;
+    for (int i = threadIdx.x; i < o.nco; i += kThreads) sco[o.soff + i] = s[i];
+  }
+  for (int i = threadIdx.x; i < T; i += kThreads) {
+    const long long gi = soff + (i & cmask) + ((long long)(i >> c) << h0);
+    S0[swz(i)] = src0[gi];
+    if (NS == 2) S1[swz(i)] = src1[gi];
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < P.nrounds; ++r) {
+    const int lo = P.rlo[r];
+    const int op0 = P.rop[r], op1 = P.rop[r + 1];
+    R acc[RB * 3];
+#pragma unroll
+    for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
+    for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
+      const int ib = (g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB));
+      C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
+#pragma unroll
+      for (int a = 0; a < (1 << RB); ++a) {
+        v0[a] = S0[swz(ib | (a << lo))];
+        if (NS == 2) v1[a] = S1[swz(ib | (a << lo))];
+      }
+      for (int k = op0; k < op1; ++k) {
+        const TileOp& o = P.ops[k];
+        tile_dispatch<R, NS, RB>(o, o.l - lo, v0, v1, sco + o.soff, acc);
+      }
+#pragma unroll
+      for (int a = 0; a < (1 << RB); ++a) {
+        S0[swz(ib | (a << lo))] = v0[a];
+        if (NS == 2) S1[swz(ib | (a << lo))] = v1[a];
+      }
+    }
+    if (NS == 2) {
+      for (int k = op0; k < op1; ++k) {
+        const TileOp& o = P.ops[k];
+        const int i = o.l - lo;
+        for (int q = 0; q < o.np; ++q) {
+          R val = 0;
+#pragma unroll
+          for (int s = 0; s < RB * 3; ++s)
+            if (s == i * 3 + q) val = acc[s];
+          double v = warp_sum((double)val);
+          if (lane == 0) sred[warp * P.nslots + o.slot + q] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (P.store) {
+    for (int i = threadIdx.x; i < T; i += kThreads) {
+      const long long gi = soff + (i & cmask) + ((long long)(i >> c) << h0);
+      dst0[gi] = S0[swz(i)];
+      if (NS == 2) dst1[gi] = S1[swz(i)];
+    }
+  }
+  if (NS == 2 && P.nslots > 0) {
+    for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
+      double v = 0;
+      for (int w = 0; w < kWarps; ++w) v += sred[w * P.nslots + s];
+      part[(long long)s * gridDim.x + blockIdx.x] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bit-marginal reduction shared by <Z>, diagonal-layer gradients
+// ---------------------------------------------------------------------------
+
+// Per thread: u_p = zt_p ? (W - accz_p) : accz_p, with accz_p the per-thread
+// sums over the compile-time j bits; written to sred[(1 + p) * kThreads + tid]
+// (added when `add`), sred[tid] holds W.
+template <int NA>
+__device__ __forceinline__ void marg_write(double* sred, int n, long long zt, float W,
+                                           const float* acc, int acc_lo, bool add) {
+  const int tid = threadIdx.x;
+  double w0 = add ? sred[tid] : 0.0;
+  sred[tid] = w0 + (double)W;
+  for (int p = 0; p < n; ++p) {
+    float a = 0.f;
+    const int q = p - acc_lo;
+#pragma unroll
+    for (int s = 0; s < NA; ++s)
+      if (s == q) a = acc[s];
+    float u = ((zt >> p) & 1) ? (W - a) : a;
+    double old = add ? sred[(1 + p) * kThreads + tid] : 0.0;
+    sred[(1 + p) * kThreads + tid] = old + (double)u;
+  }
+}
+
+// Sums sred[v][0..kThreads) for v <= n in a fixed order and writes
+// part[v * nblk + blk].
+__device__ __forceinline__ void marg_flush(const double* sred, int nvals, double* part,
+                                           long long nblk, long long blk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = warp; v < nvals; v += kWarps) {
+    double s = 0;
+    for (int e = 0; e < kThreads / 32; ++e) s += sred[v * kThreads + lane + 32 * e];
+    s = warp_sum(s);
+    if (lane == 0) part[(long long)v * nblk + blk] = s;
+  }
+}
+
+// compile-time z(j << 8) bits above bit 7 for the marginal accumulators
+template <int ZM>
+__device__ __forceinline__ constexpr int zj_bits(int j) {
+  return ZM == Z_RINGXOR ? ((j << 8) ^ (j << 7)) : (j << 8);
+}
+__device__ __forceinline__ long long ztrans(long long k, int n, int zm) {
+  if (zm == Z_RINGXOR) return k ^ ((k >> 1) | ((k & 1) << (n - 1)));
+  return k;
+}
+
+// phase(z) = T0[z0] T1[z1] T2[z2]
+template <class R>
+__device__ __forceinline__ cx<R> diag_phase(const R* tabs, int tb, long long z) {
+  const long long mask = (1LL << tb) - 1;
+  const long long T = 1LL << tb;
+  cx<R> a = ldc<R>(tabs + 2 * (z & mask));
+  cx<R> b = ldc<R>(tabs + 2 * (T + ((z >> tb) & mask)));
+  cx<R> c = ldc<R>(tabs + 2 * (2 * T + ((z >> (2 * tb)) & mask)));
+  return cmul<R>(cmul<R>(a, b), c);
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal / complement pass
+// ---------------------------------------------------------------------------
+// CTA = one chunk of CH = 2^cb amplitudes (XC: a chunk and its mirror chunk);
+// amplitude i of the chunk is handled by thread i % 256 at step j = i / 256.
+template <class R, int NS, int ZM, int XC, int JB>
+__global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __restrict__ coef,
+                                                   const cx<R>* src0, cx<R>* dst0,
+                                                   const cx<R>* src1, cx<R>* dst1,
+                                                   double* __restrict__ part) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sred = reinterpret_cast<double*>(smraw);
+  const int n = P.n, cb = P.cb;
+  const long long N = 1LL << n;
+  const int CH = 1 << cb;
+  const int nchb = n - cb;
+  const long long nch = 1LL << nchb;
+  const long long cpb = XC ? (nch > 1 ? nch / 2 : 1) : nch;  // CTAs per sample
+  const int b = (int)(blockIdx.x / cpb);
+  const long long ch = blockIdx.x % cpb;
+  const long long base = ch << cb;
+  const long long sb = (long long)b << n;
+  const R* tabs = coef + P.coef + (long long)b * P.bstride;
+  const int tid = threadIdx.x;
+  constexpr int NJ = 1 << JB;
+  const bool active = tid < CH;
+
+  if (!XC) {
+    float W = 0.f, acc[JB + 2];
+#pragma unroll
+    for (int s = 0; s < JB + 2; ++s) acc[s] = 0.f;
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const long long k = base + tid + (j << 8);
+        const long long z = ztrans(k, n, ZM);
+        const C ph = diag_phase<R>(tabs, P.tb, z);
+        const C x = src0[sb + k];
+        if (NS == 1) {
+          dst0[sb + k] = cmul<R>(ph, x);
+        } else {
+          const C y = cmulc<R>(ph, x);             // conj(phase) * psi
+          const C u = cmulc<R>(ph, src1[sb + k]);  // conj(phase) * lambda
+          dst0[sb + k] = y;
+          dst1[sb + k] = u;
+          const float w = (float)im_cdot<R>(u, y);
+          W += w;
+          constexpr int dummy = 0;
+          (void)dummy;
+#pragma unroll
+          for (int s = 0; s < JB + 2; ++s)
+            if ((zj_bits<ZM>(j) >> (7 + s)) & 1) acc[s] += w;
+        }
+      }
+    }
+    if (NS == 2) {
+      const long long zt = ztrans(base + tid, n, ZM);
+      marg_write<JB + 2>(sred, n, active ? zt : 0, W, acc, 7, false);
+      __syncthreads();
+      marg_flush(sred, P.nvals, part, gridDim.x, blockIdx.x);
+    }
+  } else {
+    // mirror chunk of `ch` is nch-1-ch; a single chunk is its own mirror
+    const bool single = (nch == 1);
+    const long long mbase = (nch - 1 - ch) << cb;
+    const int lim = single ? CH / 2 : CH;
+    float W = 0.f, acc[JB + 2], Wm = 0.f, accm[JB + 2];
+#pragma unroll
+    for (int s = 0; s < JB + 2; ++s) acc[s] = accm[s] = 0.f;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int i = tid + (j << 8);
+      if (i < lim) {
+        const long long k = base + i;
+        const long long km = N - 1 - k;  // = mbase + (CH - 1 - i)
+        if (NS == 1) {
+          const C xk = src0[sb + k], xm = src0[sb + km];
+          if (P.has_phase) {
+            dst0[sb + k] = cmul<R>(diag_phase<R>(tabs, P.tb, km), xm);
+            dst0[sb + km] = cmul<R>(diag_phase<R>(tabs, P.tb, k), xk);
+          } else {
+            dst0[sb + k] = xm;
+            dst0[sb + km] = xk;
+          }
+        } else {
+          const C pk = src0[sb + k], pm = src0[sb + km];
+          const C lk = src1[sb + k], lm = src1[sb + km];
+          C yk, ym, uk, um;
+          if (P.has_phase) {
+            const C phk = diag_phase<R>(tabs, P.tb, k), phm = diag_phase<R>(tabs, P.tb, km);
+            yk = cmulc<R>(phk, pm); uk = cmulc<R>(phk, lm);  // in[k] = conj(ph(k)) out[~k]
+            ym = cmulc<R>(phm, pk); um = cmulc<R>(phm, lk);
+          } else {
+            yk = pm; uk = lm; ym = pk; um = lk;
+          }
+          dst0[sb + k] = yk; dst1[sb + k] = uk;
+          dst0[sb + km] = ym; dst1[sb + km] = um;
+          const float wk = (float)im_cdot<R>(uk, yk), wm = (float)im_cdot<R>(um, ym);
+          W += wk;
+          Wm += wm;
+#pragma unroll
+          for (int s = 0; s < JB + 2; ++s) {
+            // z = k: j-bit contribution (j << 8); mirror: z = km, i' = CH-1-i
+            if (((j << 8) >> (7 + s)) & 1) acc[s] += wk;
+            if (((j << 8) >> (7 + s)) & 1) accm[s] += wm;
+          }
+        }
+      }
+    }
+    if (NS == 2) {
+      // k = base ^ tid ^ (j << 8); km = (mbase + CH - 1) ^ tid ^ (j << 8), so the
+      // mirror uses the same j-bit accumulators with the complemented constant.
+      const bool act = tid < lim || (tid < CH && !single);
+      const long long zt = base + tid;
+      const long long ztm = (mbase + CH - 1) ^ tid;
+      marg_write<JB + 2>(sred, n, act ? zt : 0, act ? W : 0.f, acc, 7, false);
+      marg_write<JB + 2>(sred, n, act ? ztm : 0, act ? Wm : 0.f, accm, 7, true);
+      __syncthreads();
+      marg_flush(sred, P.nvals, part, gridDim.x, blockIdx.x);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// <Z> marginals of |psi|^2 and lambda = O psi
+// ---------------------------------------------------------------------------
+template <class R, int JB>
+__global__ void __launch_bounds__(kThreads) k_expect(int n, int cb, const cx<R>* __restrict__ psi,
+                                                     double* __restrict__ part) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sred = reinterpret_cast<double*>(smraw);
+  const int nchb = n - cb;
+  const int b = (int)(blockIdx.x >> nchb);
+  const long long base = ((long long)blockIdx.x & ((1LL << nchb) - 1)) << cb;
+  const C* s = psi + ((long long)b << n) + base;
+  const int tid = threadIdx.x;
+  const bool active = tid < (1 << cb);
+  float W = 0.f, acc[JB + 2];
+#pragma unroll
+  for (int q = 0; q < JB + 2; ++q) acc[q] = 0.f;
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < (1 << JB); ++j) {
+      const C x = s[tid + (j << 8)];
+      const float w = (float)(x.x * x.x + x.y * x.y);
+      W += w;
+#pragma unroll
+      for (int q = 0; q < JB + 2; ++q)
+        if (((j << 8) >> (7 + q)) & 1) acc[q] += w;
+    }
+  }
+  marg_write<JB + 2>(sred, n, active ? (base + tid) : 0, W, acc, 7, false);
+  __syncthreads();
+  marg_flush(sred, n + 1, part, gridDim.x, blockIdx.x);
+}
+
+// lambda[b][k] = (sum_q g[b][q] (1 - 2 bit_{n-1-q}(k))) psi[b][k]
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_laminit(int n, int cb, const double* __restrict__ gez,
+                                                      const cx<R>* __restrict__ psi,
+                                                      cx<R>* __restrict__ lam) {
+  using C = cx<R>;
+  __shared__ double Sa[64], Sb[64];
+  const int nchb = n - cb;
+  const int b = (int)(blockIdx.x >> nchb);
+  const long long base = ((long long)blockIdx.x & ((1LL << nchb) - 1)) << cb;
+  const double* g = gez + (long long)b * n;
+  const int la = cb < 6 ? cb : 6, lb = cb - la;
+  double tot = 0, hi = 0;
+  for (int q = 0; q < n; ++q) {
+    tot += g[q];
+    const int p = n - 1 - q;
+    if (p >= cb && ((base >> p) & 1)) hi += g[q];
+  }
+  for (int e = threadIdx.x; e < 128; e += blockDim.x) {
+    double s = 0;
+    if (e < 64) {
+      for (int i = 0; i < la; ++i)
+        if ((e >> i) & 1) s += g[n - 1 - i];
+      Sa[e] = s;
+    } else {
+      const int f = e - 64;
+      for (int i = 0; i < lb; ++i)
+        if ((f >> i) & 1) s += g[n - 1 - (la + i)];
+      Sb[f] = s + hi;
+    }
+  }
+  __syncthreads();
+  const long long off = ((long long)b << n) + base;
+  const int CH = 1 << cb, ma = (1 << la) - 1;
+  for (int i = threadIdx.x; i < CH; i += blockDim.x) {
+    const R o = (R)(tot - 2.0 * (Sa[i & ma] + Sb[i >> la]));
+    const C x = psi[off + i];
+    lam[off + i] = mk<R>(o * x.x, o * x.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CNOT ring permutation (closed-form GF(2) index map)
+// ---------------------------------------------------------------------------
+// Ring = CNOT(q->q+1 mod n) for q = 0..n-1.  With bit p = n-1-q:
+//   forward  f(k):   bit p = parity(k >> p) for p <= n-2, bit n-1 = parity(k mod 2^(n-1))
+//   inverse  f^-1(k) = k ^ (k >> 1) ^ (k & 1 ? 3 << (n-2) : 0)
+__device__ __forceinline__ long long ring_finv(long long k, int n) {
+  return k ^ (k >> 1) ^ ((k & 1) ? (3LL << (n - 2)) : 0LL);
+}
+__device__ __forceinline__ int par64(long long v) { return __popcll((unsigned long long)v) & 1; }
+__device__ __forceinline__ long long ring_f(long long k, int n) {
+  // prefix parities from the top: s_p = parity(k >> p)
+  unsigned long long s = (unsigned long long)k;
+  s ^= s >> 1; s ^= s >> 2; s ^= s >> 4; s ^= s >> 8; s ^= s >> 16; s ^= s >> 32;
+  const long long low = (long long)(s & ((1ULL << (n - 1)) - 1));
+  const long long top = (long long)par64(k & ((1LL << (n - 1)) - 1));
+  return low | (top << (n - 1));
+}
+__device__ __forceinline__ int gray_inv(int x) {
+  x ^= x >> 1; x ^= x >> 2; x ^= x >> 4; x ^= x >> 8; x ^= x >> 16;
+  return x;
+}
+
+// NS = 1: out[k] = in[f^-1(k)] (forward).  NS = 2: new[y] = old[f(y)] for
+// psi and lambda (backward, the inverse permutation).
+template <class R, int NS>
+__global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>* src0, cx<R>* dst0,
+                                                   const cx<R>* src1, cx<R>* dst1) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* S = reinterpret_cast<C*>(smraw);
+  const int n = P.n;
+  if (P.whole) {
+    const int N = 1 << n;
+    const long long sb = (long long)blockIdx.x << n;
+    for (int s = 0; s < NS; ++s) {
+      const C* src = s ? src1 : src0;
+      C* dst = s ? dst1 : dst0;
+      for (int i = threadIdx.x; i < N; i += kThreads) S[i] = src[sb + i];
+      __syncthreads();
+      for (int k = threadIdx.x; k < N; k += kThreads)
+        dst[sb + k] = S[NS == 1 ? ring_finv(k, n) : ring_f(k, n)];
+      __syncthreads();
+    }
+    return;
+  }
+  const int t = P.t;
+  const int H = 1 << (t - 1);
+  const int fb = n - t;
+  const int b = (int)(blockIdx.x >> fb);
+  const long long f = blockIdx.x & ((1LL << fb) - 1);
+  const long long sb = (long long)b << n;
+  const long long tb = f << (t - 1);                       // tile base (bits t-1 .. n-2)
+  const long long ib = tb ^ (tb >> 1);                     // f^-1(tile base)
+  const long long A = ib & ~(long long)(H - 1);            // block A, B = A ^ 3 << (n-2)
+  const long long Bk = A ^ (3LL << (n - 2));
+  const int il = (int)(ib & (H - 1));
+  const long long topbit = 1LL << (n - 1);
+  for (int s = 0; s < NS; ++s) {
+    const C* src = s ? src1 : src0;
+    C* dst = s ? dst1 : dst0;
+    if (NS == 1) {
+      // load the two input blocks, write the output tile
+      for (int y = threadIdx.x; y < H; y += kThreads) {
+        S[y] = src[sb + A + y];
+        S[H + y] = src[sb + Bk + y];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
+        const int top = e >> (t - 1), jl = e & (H - 1);
+        const int u = (jl & 1) ^ top;
+        dst[sb + tb + jl + (top ? topbit : 0)] = S[u * H + (il ^ jl ^ (jl >> 1))];
+      }
+    } else {
+      // load the tile (old), write the two blocks (new[y] = old[f(y)])
+      for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
+        const int top = e >> (t - 1), jl = e & (H - 1);
+        S[e] = src[sb + tb + jl + (top ? topbit : 0)];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
+        const int u = e >> (t - 1), yl = e & (H - 1);
+        const int jl = gray_inv(yl ^ il);
+        const int top = u ^ (jl & 1);
+        dst[sb + (u ? Bk : A) + yl] = S[top * H + jl];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions of per-CTA partials (fixed order, float64)
+// ---------------------------------------------------------------------------
+// rows: job j has batch * nvals rows starting at row0[j]; V[row] = sum of the
+// sample's CTAs' partials for that value.
+__global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restrict__ jobs,
+                                                   const long long* __restrict__ row0, int njobs,
+                                                   long long rowbase, const double* __restrict__ part,
+                                                   double* __restrict__ V) {
+  const long long row = rowbase + blockIdx.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {  // last job with row0 <= row
+    int mid = (lo + hi + 1) >> 1;
+    if (row0[mid] <= row) lo = mid; else hi = mid - 1;
+  }
+  const RedJob J = jobs[lo];
+  const long long r = row - row0[lo];
+  const int bsm = (int)(r / J.nvals), v = (int)(r % J.nvals);
+  const double* p = part + J.part_off + (long long)v * J.nblk + (long long)bsm * J.blk_per_sample;
+  double s = 0;
+  for (int i = threadIdx.x; i < J.blk_per_sample; i += kThreads) s += p[i];
+  __shared__ double red[kWarps];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tsum = 0;
+    for (int w = 0; w < kWarps; ++w) tsum += red[w];
+    V[row] = tsum;
+  }
+}
+
+// one thread per output of a job group: combine values into gradients
+// (added to d_theta / d_x, which the caller zeroes first).
+__global__ void k_finalize(const RedJob* __restrict__ jobs, const long long* __restrict__ row0,
+                           const int* __restrict__ out0, int njobs, int outbase, int nout,
+                           const RedOut* __restrict__ outs, int batch, int n_in,
+                           const double* __restrict__ V, double* __restrict__ d_theta,
+                           double* __restrict__ d_x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nout) return;
+  const int o = outbase + t;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (out0[mid] <= o) lo = mid; else hi = mid - 1;
+  }
+  const RedJob J = jobs[lo];
+  const RedOut ro = outs[o];
+  const double* v = V + row0[lo];
+  double tot = 0;
+  for (int b = 0; b < batch; ++b) {
+    const double* vb = v + (long long)b * J.nvals;
+    const double g = J.kind == RK_DIRECT ? ro.scale * vb[ro.val]
+                                         : ro.scale * (vb[0] - 2.0 * vb[1 + ro.val]);
+    if (J.source == QC_SRC_INPUT) {
+      if (d_x) d_x[(long long)b * n_in + ro.pidx] += g;
+    } else {
+      tot += g;
+    }
+  }
+  if (J.source == QC_SRC_THETA && d_theta) d_theta[ro.pidx] += tot;
+}
+
+// <Z_q> from marginals: ez[b][q] = V[b][0] - 2 V[b][1 + (n-1-q)]
+__global__ void k_ez_from_marg(int n, int batch, int blk_per_sample, long long nblk,
+                               const double* __restrict__ part, double* __restrict__ ez) {
+  const int b = blockIdx.x;
+  __shared__ double vals[kMaxQubits + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = warp; v <= n; v += kWarps) {
+    const double* p = part + (long long)v * nblk + (long long)b * blk_per_sample;
+    double s = 0;
+    for (int i = lane; i < blk_per_sample; i += 32) s += p[i];
+    s = warp_sum(s);
+    if (lane == 0) vals[v] = s;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) ez[(long long)b * n + q] = vals[0] - 2.0 * vals[1 + (n - 1 - q)];
+}
+
+// ---------------------------------------------------------------------------
+// Whole circuit of one sample in shared memory (small n)
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void sm_1q_fwd(cx<R>* S, int n, int p, const R* m, int real) {
+  using C = cx<R>;
+  const int half = 1 << (n - 1);
+  const C m00 = ldc<R>(m), m01 = ldc<R>(m + 2), m10 = ldc<R>(m + 4), m11 = ldc<R>(m + 6);
+  for (int i = threadIdx.x; i < half; i += blockDim.x) {
+    const int a = ((i >> p) << (p + 1)) | (i & ((1 << p) - 1));
+    const int a1 = a | (1 << p);
+    const C x0 = S[a], x1 = S[a1];
+    S[a] = cfma<R>(m01, x1, cmul<R>(m00, x0));
+    S[a1] = cfma<R>(m11, x1, cmul<R>(m10, x0));
+  }
+  (void)real;
+}
+
+// undo a single-qubit gate on psi and lambda; returns this thread's share of
+// 2 Re <lambda|A|psi> (input side)
+template <class R>
+__device__ __forceinline__ double sm_1q_bwd(cx<R>* P, cx<R>* L, int n, int p, const R* m, int np) {
+  using C = cx<R>;
+  const int half = 1 << (n - 1);
+  const C m00 = ldc<R>(m), m01 = ldc<R>(m + 2), m10 = ldc<R>(m + 4), m11 = ldc<R>(m + 6);
+  const C a00 = ldc<R>(m + 8), a01 = ldc<R>(m + 10), a10 = ldc<R>(m + 12), a11 = ldc<R>(m + 14);
+  R g = 0;
+  for (int i = threadIdx.x; i < half; i += blockDim.x) {
+    const int a = ((i >> p) << (p + 1)) | (i & ((1 << p) - 1));
+    const int a1 = a | (1 << p);
+    C x0 = P[a], x1 = P[a1], u0 = L[a], u1 = L[a1];
+    C y0 = cfmac<R>(m10, x1, cfmac<R>(m00, x0, mk<R>(0, 0)));
+    C y1 = cfmac<R>(m11, x1, cfmac<R>(m01, x0, mk<R>(0, 0)));
+    C w0 = cfmac<R>(m10, u1, cfmac<R>(m00, u0, mk<R>(0, 0)));
+    C w1 = cfmac<R>(m11, u1, cfmac<R>(m01, u0, mk<R>(0, 0)));
+    P[a] = y0; P[a1] = y1; L[a] = w0; L[a1] = w1;
+    if (np) {
+      C t0 = cfma<R>(a01, y1, cmul<R>(a00, y0));
+      C t1 = cfma<R>(a11, y1, cmul<R>(a10, y0));
+      g += re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1);
+    }
+  }
+  return 2.0 * (double)g;
+}
+
+template <class R>
+__device__ __forceinline__ void sm_2q_fwd(cx<R>* S, int n, int plo, const R* m) {
+  using C = cx<R>;
+  const int quarter = 1 << (n - 2);
+  for (int i = threadIdx.x; i < quarter; i += blockDim.x) {
+    // insert zeros at bits plo and plo+1
+    const int a = ((i >> plo) << (plo + 2)) | (i & ((1 << plo) - 1));
+    C x[4], y[4];
+    for (int s = 0; s < 4; ++s) x[s] = S[a | (s << plo)];
+    for (int r = 0; r < 4; ++r) {
+      C t = mk<R>(0, 0);
+      for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(m + 2 * (r * 4 + s)), x[s], t);
+      y[r] = t;
+    }
+    for (int s = 0; s < 4; ++s) S[a | (s << plo)] = y[s];
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void sm_2q_bwd(cx<R>* P, cx<R>* L, int n, int plo, const R* m, int np,
+                                          double g[3]) {
+  using C = cx<R>;
+  const int quarter = 1 << (n - 2);
+  R gl[3] = {0, 0, 0};
+  for (int i = threadIdx.x; i < quarter; i += blockDim.x) {
+    const int a = ((i >> plo) << (plo + 2)) | (i & ((1 << plo) - 1));
+    C x[4], u[4], y[4], w[4];
+    for (int s = 0; s < 4; ++s) { x[s] = P[a | (s << plo)]; u[s] = L[a | (s << plo)]; }
+    for (int r = 0; r < 4; ++r) {
+      C t = mk<R>(0, 0), z = mk<R>(0, 0);
+      for (int s = 0; s < 4; ++s) {
+        C ms = ldc<R>(m + 2 * (s * 4 + r));
+        t = cfmac<R>(ms, x[s], t);
+        z = cfmac<R>(ms, u[s], z);
+      }
+      y[r] = t; w[r] = z;
+    }
+    for (int s = 0; s < 4; ++s) { P[a | (s << plo)] = y[s]; L[a | (s << plo)] = w[s]; }
+    for (int k = 0; k < np; ++k) {
+      const R* A = m + 32 + 32 * k;
+      for (int r = 0; r < 4; ++r) {
+        C t = mk<R>(0, 0);
+        for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(A + 2 * (r * 4 + s)), y[s], t);
+        gl[k] += re_cdot<R>(w[r], t);
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) g[k] = 2.0 * (double)gl[k];
+}
+
+// block sum of `v` (all threads participate); result valid in every thread.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0;
+  for (int w = 0; w < kWarps; ++w) s += red[w];
+  return s;
+}
+
+template <class R, int BWD>
+__global__ void __launch_bounds__(kThreads) k_smem(const SmemLayer* __restrict__ prog, int nl, int n,
+                                                   int batch, const R* __restrict__ coef,
+                                                   const cx<R>* psi_in, cx<R>* psi_out,
+                                                   double* __restrict__ ez,
+                                                   const double* __restrict__ gez,
+                                                   double* __restrict__ part, int nslots) {
+  using C = cx<R>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = 1 << n;
+  C* P = reinterpret_cast<C*>(smraw);
+  C* L = P + N;  // BWD only
+  double* red = reinterpret_cast<double*>(P + (BWD ? 2 * N : N));
+  double* marg = red + kWarps;  // (n + 1) values
+  const int b = blockIdx.x;
+  const long long sb = (long long)b << n;
+  (void)batch;
+
+  if (!BWD) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) P[i] = mk<R>(i == 0 ? 1 : 0, 0);
+  } else {
+    // lambda = O psi_L
+    const double* g = gez + (long long)b * n;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      double o = 0;
+      for (int q = 0; q < n; ++q) o += ((i >> (n - 1 - q)) & 1) ? -g[q] : g[q];
+      const C x = psi_in[sb + i];
+      P[i] = x;
+      L[i] = mk<R>((R)o * x.x, (R)o * x.y);
+    }
+  }
+  __syncthreads();
+
+  for (int li = 0; li < nl; ++li) {
+    const int l = BWD ? nl - 1 - li : li;
+    const SmemLayer Ly = prog[l];
+    const R* cf = coef + Ly.coef + (long long)b * Ly.bstride;
+    switch (Ly.cls) {
+      case LC_ROT1:
+        for (int q = 0; q < n; ++q) {
+          const int p = n - 1 - q;
+          if (!BWD) {
+            sm_1q_fwd<R>(P, n, p, cf + q * kRec1q, Ly.real);
+          } else {
+            double g = sm_1q_bwd<R>(P, L, n, p, cf + q * kRec1q, Ly.slot >= 0);
+            if (Ly.slot >= 0) {
+              g = block_sum(g, red);
+              if (threadIdx.x == 0) part[(long long)(Ly.slot + q) * batch + b] = g;
+            }
+          }
+          __syncthreads();
+        }
+        break;
+      case LC_DENSE2:
+        for (int gi = 0; gi < Ly.ngates; ++gi) {
+          const int q0 = Ly.parity + 2 * gi;
+          const int plo = n - 2 - q0;
+          const R* m = cf + gi * kRec2q;
+          if (!BWD) {
+            sm_2q_fwd<R>(P, n, plo, m);
+          } else {
+            double g[3];
+            const int np = Ly.slot >= 0 ? Ly.np_per_gate : 0;
+            sm_2q_bwd<R>(P, L, n, plo, m, np, g);
+            for (int k = 0; k < np; ++k) {
+              double s = block_sum(g[k], red);
+              if (threadIdx.x == 0) part[(long long)(Ly.slot + 3 * gi + k) * batch + b] = s;
+            }
+          }
+          __syncthreads();
+        }
+        break;
+      case LC_DIAG: {
+        if (!BWD) {
+          for (int k = threadIdx.x; k < N; k += blockDim.x)
+            P[k] = cmul<R>(diag_phase<R>(cf, Ly.tb, ztrans(k, n, Ly.zmode)), P[k]);
+          __syncthreads();
+        } else {
+          double W = 0, Mp[kMaxQubits];
+          for (int p = 0; p < n; ++p) Mp[p] = 0;
+          for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const long long z = ztrans(k, n, Ly.zmode);
+            const C ph = diag_phase<R>(cf, Ly.tb, z);
+            const C y = cmulc<R>(ph, P[k]), u = cmulc<R>(ph, L[k]);
+            P[k] = y; L[k] = u;
+            const double w = (double)im_cdot<R>(u, y);
+            W += w;
+            for (int p = 0; p < n; ++p)
+              if ((z >> p) & 1) Mp[p] += w;
+          }
+          if (Ly.slot >= 0) {
+            double Wt = block_sum(W, red);
+            for (int p = 0; p < n; ++p) {
+              double s = block_sum(Mp[p], red);
+              if (threadIdx.x == 0) marg[p] = s;
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+              const int p = Ly.kind == QC_L_ISINGZZ_RING ? ((n - 2 - j) % n + n) % n : n - 1 - j;
+              part[(long long)(Ly.slot + j) * batch + b] = Ly.gscale * (Wt - 2.0 * marg[p]);
+            }
+          }
+          __syncthreads();
+        }
+        break;
+      }
+      case LC_XCOMP: {
+        if (!BWD) {
+          for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+            const int km = N - 1 - k;
+            const C xk = P[k], xm = P[km];
+            if (Ly.has_phase) {
+              P[k] = cmul<R>(diag_phase<R>(cf, Ly.tb, km), xm);
+              P[km] = cmul<R>(diag_phase<R>(cf, Ly.tb, k), xk);
+            } else {
+              P[k] = xm; P[km] = xk;
+            }
+          }
+          __syncthreads();
+        } else {
+          double W = 0, Mp[kMaxQubits];
+          for (int p = 0; p < n; ++p) Mp[p] = 0;
+          for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+            const int km = N - 1 - k;
+            const C pk = P[k], pm = P[km], lk = L[k], lm = L[km];
+            C yk = pm, uk = lm, ym = pk, um = lk;
+            if (Ly.has_phase) {
+              const C phk = diag_phase<R>(cf, Ly.tb, k), phm = diag_phase<R>(cf, Ly.tb, km);
+              yk = cmulc<R>(phk, pm); uk = cmulc<R>(phk, lm);
+              ym = cmulc<R>(phm, pk); um = cmulc<R>(phm, lk);
+            }
+            P[k] = yk; L[k] = uk; P[km] = ym; L[km] = um;
+            if (Ly.slot >= 0) {
+              const double wk = (double)im_cdot<R>(uk, yk), wm = (double)im_cdot<R>(um, ym);
+              W += wk + wm;
+              for (int p = 0; p < n; ++p) {
+                if ((k >> p) & 1) Mp[p] += wk;
+                if ((km >> p) & 1) Mp[p] += wm;
+              }
+            }
+          }
+          if (Ly.slot >= 0) {
+            double Wt = block_sum(W, red);
+            for (int p = 0; p < n; ++p) {
+              double s = block_sum(Mp[p], red);
+              if (threadIdx.x == 0) marg[p] = s;
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < n; j += blockDim.x)
+              part[(long long)(Ly.slot + j) * batch + b] = Ly.gscale * (Wt - 2.0 * marg[n - 1 - j]);
+          }
+          __syncthreads();
+        }
+        break;
+      }
+      case LC_RING: {
+        constexpr int kMaxPer = 32;  // N <= 8192 with 256 threads
+        for (int s = 0; s < (BWD ? 2 : 1); ++s) {
+          C* S = s ? L : P;
+          C tmp[kMaxPer];
+#pragma unroll
+          for (int e = 0; e < kMaxPer; ++e) {
+            const int k = threadIdx.x + e * kThreads;
+            if (k < N) tmp[e] = S[BWD ? ring_f(k, n) : ring_finv(k, n)];
+          }
+          __syncthreads();
+#pragma unroll
+          for (int e = 0; e < kMaxPer; ++e) {
+            const int k = threadIdx.x + e * kThreads;
+            if (k < N) S[k] = tmp[e];
+          }
+          __syncthreads();
+        }
+        break;
+      }
+    }
+  }
+
+  if (!BWD) {
+    if (psi_out)
+      for (int i = threadIdx.x; i < N; i += blockDim.x) psi_out[sb + i] = P[i];
+    if (ez) {
+      double W = 0, Mp[kMaxQubits];
+      for (int p = 0; p < n; ++p) Mp[p] = 0;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const C x = P[k];
+        const double w = (double)x.x * x.x + (double)x.y * x.y;
+        W += w;
+        for (int p = 0; p < n; ++p)
+          if ((k >> p) & 1) Mp[p] += w;
+      }
+      double Wt = block_sum(W, red);
+      for (int p = 0; p < n; ++p) {
+        double s = block_sum(Mp[p], red);
+        if (threadIdx.x == 0) marg[p] = s;
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < n; q += blockDim.x) ez[(long long)b * n + q] = Wt - 2.0 * marg[n - 1 - q];
+    }
+  }
+  (void)nslots;
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (host)
+// ---------------------------------------------------------------------------
+template <class R>
+cudaError_t launch_coef(const CoefJob* jobs, int njobs, int n, int batch, int n_in, const double* x,
+                        const double* theta, void* coef, cudaStream_t st) {
+  if (njobs == 0) return cudaSuccess;
+  dim3 grid(njobs, batch);
+  k_coef<R><<<grid, 128, 0, st>>>(jobs, njobs, n, batch, n_in, x, theta, (R*)coef);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_prodvec(const ProdVecJob& P, int n, int batch, int n_in, const double* x,
+                           const double* theta, void* pv, cudaStream_t st) {
+  int tot = batch * n;
+  k_prodvec<R><<<(tot + 127) / 128, 128, 0, st>>>(P, n, batch, n_in, x, theta, (R*)pv);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi, cudaStream_t st) {
+  long long grid = (long long)batch << (n - cb);
+  k_prodinit<R><<<(unsigned)grid, kThreads, 0, st>>>(n, cb, (const R*)pv, (cx<R>*)psi);
+  return cudaGetLastError();
+}
+
+size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) {
+  size_t s = (size_t)ns * ((size_t)1 << P.t) * 2 * rsize;
+  s += (size_t)((P.ncoef + 1) & ~1) * rsize;
+  s += (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double);
+  return s;
+}
+
+template <class R, int NS, int RB>
+static cudaError_t launch_tile_rb(const TilePass& P, int batch, const void* coef, const void* s0,
+                                  void* d0, const void* s1, void* d1, double* part,
+                                  cudaStream_t st) {
+  size_t smem = tile_smem_bytes(P, NS, sizeof(R));
+  auto kern = k_tile<R, NS, RB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  long long grid = (long long)batch << (P.n - P.t);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const R*)coef, (const cx<R>*)s0, (cx<R>*)d0,
+                                               (const cx<R>*)s1, (cx<R>*)d1, part);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, const void* coef,
+                        const void* s0, void* d0, const void* s1, void* d1, double* part,
+                        cudaStream_t st) {
+  if (ns == 1) {
+    switch (rb) {
+      case 1: return launch_tile_rb<R, 1, 1>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 2: return launch_tile_rb<R, 1, 2>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 3: return launch_tile_rb<R, 1, 3>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 4: return launch_tile_rb<R, 1, 4>(P, batch, coef, s0, d0, s1, d1, part, st);
+    }
+  } else {
+    switch (rb) {
+      case 1: return launch_tile_rb<R, 2, 1>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 2: return launch_tile_rb<R, 2, 2>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 3: return launch_tile_rb<R, 2, 3>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 4: return launch_tile_rb<R, 2, 4>(P, batch, coef, s0, d0, s1, d1, part, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+long long diag_grid(const DiagPass& P, int batch) {
+  long long nch = 1LL << (P.n - P.cb);
+  long long cpb = P.xcomp ? (nch > 1 ? nch / 2 : 1) : nch;
+  return cpb * batch;
+}
+
+template <class R, int NS, int ZM, int XC, int JB>
+static cudaError_t launch_diag_jb(const DiagPass& P, int batch, const void* coef, const void* s0,
+                                  void* d0, const void* s1, void* d1, double* part,
+                                  cudaStream_t st) {
+  size_t smem = NS == 2 ? (size_t)(P.n + 1) * kThreads * sizeof(double) : 0;
+  auto kern = k_diag<R, NS, ZM, XC, JB>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<(unsigned)diag_grid(P, batch), kThreads, smem, st>>>(P, (const R*)coef, (const cx<R>*)s0,
+                                                              (cx<R>*)d0, (const cx<R>*)s1,
+                                                              (cx<R>*)d1, part);
+  return cudaGetLastError();
+}
+
+template <class R, int NS, int ZM, int XC>
+static cudaError_t launch_diag_z(const DiagPass& P, int batch, const void* coef, const void* s0,
+                                 void* d0, const void* s1, void* d1, double* part, cudaStream_t st) {
+  const int jb = P.cb > 8 ? P.cb - 8 : 0;
+  switch (jb) {
+    case 0: return launch_diag_jb<R, NS, ZM, XC, 0>(P, batch, coef, s0, d0, s1, d1, part, st);
+    case 1: return launch_diag_jb<R, NS, ZM, XC, 1>(P, batch, coef, s0, d0, s1, d1, part, st);
+    case 2: return launch_diag_jb<R, NS, ZM, XC, 2>(P, batch, coef, s0, d0, s1, d1, part, st);
+    case 3: return launch_diag_jb<R, NS, ZM, XC, 3>(P, batch, coef, s0, d0, s1, d1, part, st);
+    case 4: return launch_diag_jb<R, NS, ZM, XC, 4>(P, batch, coef, s0, d0, s1, d1, part, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class R>
+cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, const void* s0,
+                        void* d0, const void* s1, void* d1, double* part, cudaStream_t st) {
+  if (P.xcomp) {
+    if (ns == 1) return launch_diag_z<R, 1, Z_IDENT, 1>(P, batch, coef, s0, d0, s1, d1, part, st);
+    return launch_diag_z<R, 2, Z_IDENT, 1>(P, batch, coef, s0, d0, s1, d1, part, st);
+  }
+  if (P.zmode == Z_RINGXOR) {
+    if (ns == 1) return launch_diag_z<R, 1, Z_RINGXOR, 0>(P, batch, coef, s0, d0, s1, d1, part, st);
+    return launch_diag_z<R, 2, Z_RINGXOR, 0>(P, batch, coef, s0, d0, s1, d1, part, st);
+  }
+  if (ns == 1) return launch_diag_z<R, 1, Z_IDENT, 0>(P, batch, coef, s0, d0, s1, d1, part, st);
+  return launch_diag_z<R, 2, Z_IDENT, 0>(P, batch, coef, s0, d0, s1, d1, part, st);
+}
+
+size_t ring_smem_bytes(const RingPass& P, int rsize) {
+  size_t amps = P.whole ? ((size_t)1 << P.n) : ((size_t)1 << P.t);
+  return amps * 2 * rsize;
+}
+
+template <class R>
+cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, void* d0,
+                        const void* s1, void* d1, cudaStream_t st) {
+  size_t smem = ring_smem_bytes(P, sizeof(R));
+  long long grid = P.whole ? batch : ((long long)batch << (P.n - P.t));
+  if (ns == 1) {
+    auto kern = k_ring<R, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const cx<R>*)s0, (cx<R>*)d0, nullptr, nullptr);
+  } else {
+    auto kern = k_ring<R, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const cx<R>*)s0, (cx<R>*)d0, (const cx<R>*)s1,
+                                                 (cx<R>*)d1);
+  }
+  return cudaGetLastError();
+}
+
+template <class R, int JB>
+static cudaError_t launch_expect_jb(int n, int cb, int batch, const void* psi, double* part,
+                                    cudaStream_t st) {
+  size_t smem = (size_t)(n + 1) * kThreads * sizeof(double);
+  auto kern = k_expect<R, JB>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  long long grid = (long long)batch << (n - cb);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(n, cb, (const cx<R>*)psi, part);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_expect(int n, int cb, int batch, const void* psi, double* part, double* ez,
+                          cudaStream_t st) {
+  const int jb = cb > 8 ? cb - 8 : 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (jb) {
+    case 0: e = launch_expect_jb<R, 0>(n, cb, batch, psi, part, st); break;
+    case 1: e = launch_expect_jb<R, 1>(n, cb, batch, psi, part, st); break;
+    case 2: e = launch_expect_jb<R, 2>(n, cb, batch, psi, part, st); break;
+    case 3: e = launch_expect_jb<R, 3>(n, cb, batch, psi, part, st); break;
+    case 4: e = launch_expect_jb<R, 4>(n, cb, batch, psi, part, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  long long nblk = (long long)batch << (n - cb);
+  k_ez_from_marg<<<batch, kThreads, 0, st>>>(n, batch, 1 << (n - cb), nblk, part, ez);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_laminit(int n, int cb, int batch, const double* gez, const void* psi, void* lam,
+                           cudaStream_t st) {
+  long long grid = (long long)batch << (n - cb);
+  k_laminit<R><<<(unsigned)grid, kThreads, 0, st>>>(n, cb, gez, (const cx<R>*)psi, (cx<R>*)lam);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const RedJob* jobs, const long long* row0, const int* out0, int njobs,
+                          long long rowbase, long long nrows, int outbase, int nout,
+                          const RedOut* outs, int batch, int n_in, const double* part, double* V,
+                          double* d_theta, double* d_x, cudaStream_t st) {
+  if (njobs == 0) return cudaSuccess;
+  k_red1<<<(unsigned)nrows, kThreads, 0, st>>>(jobs, row0, njobs, rowbase, part, V);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_finalize<<<(nout + 127) / 128, 128, 0, st>>>(jobs, row0, out0, njobs, outbase, nout, outs, batch,
+                                                 n_in, V, d_theta, d_x);
+  return cudaGetLastError();
+}
+
+size_t smem_circuit_bytes(int n, int bwd, int rsize) {
+  size_t amps = (size_t)1 << n;
+  return amps * 2 * rsize * (bwd ? 2 : 1) + (kWarps + kMaxQubits + 1) * sizeof(double);
+}
+
+template <class R>
+cudaError_t launch_smem(const SmemLayer* prog, int nl, int n, int batch, int bwd, const void* coef,
+                        const void* psi_in, void* psi_out, double* ez, const double* gez,
+                        double* part, int nslots, cudaStream_t st) {
+  size_t smem = smem_circuit_bytes(n, bwd, sizeof(R));
+  if (!bwd) {
+    auto kern = k_smem<R, 0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<batch, kThreads, smem, st>>>(prog, nl, n, batch, (const R*)coef, (const cx<R>*)psi_in,
+                                        (cx<R>*)psi_out, ez, gez, part, nslots);
+  } else {
+    auto kern = k_smem<R, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<batch, kThreads, smem, st>>>(prog, nl, n, batch, (const R*)coef, (const cx<R>*)psi_in,
+                                        (cx<R>*)psi_out, ez, gez, part, nslots);
+  }
+  return cudaGetLastError();
+}
+
+#define QC_INST(R)                                                                                 \
+  template cudaError_t launch_coef<R>(const CoefJob*, int, int, int, int, const double*,           \
+                                      const double*, void*, cudaStream_t);                         \
+  template cudaError_t launch_prodvec<R>(const ProdVecJob&, int, int, int, const double*,          \
+                                         const double*, void*, cudaStream_t);                      \
+  template cudaError_t launch_prodinit<R>(int, int, int, const void*, void*, cudaStream_t);        \
+  template cudaError_t launch_tile<R>(const TilePass&, int, int, int, const void*, const void*,    \
+                                      void*, const void*, void*, double*, cudaStream_t);           \
+  template cudaError_t launch_diag<R>(const DiagPass&, int, int, const void*, const void*, void*,  \
+                                      const void*, void*, double*, cudaStream_t);                  \
+  template cudaError_t launch_ring<R>(const RingPass&, int, int, const void*, void*, const void*,  \
+                                      void*, cudaStream_t);                                        \
+  template cudaError_t launch_expect<R>(int, int, int, const void*, double*, double*,              \
+                                        cudaStream_t);                                             \
+  template cudaError_t launch_laminit<R>(int, int, int, const double*, const void*, void*,         \
+                                         cudaStream_t);                                            \
+  template cudaError_t launch_smem<R>(const SmemLayer*, int, int, int, int, const void*,           \
+                                      const void*, void*, double*, const double*, double*, int,    \
+                                      cudaStream_t);
+
+QC_INST(float)
+QC_INST(double)
+
+}  // namespace qc

@@ -1,0 +1,66 @@
+// Host-side launch wrappers of the kernels in qc_kernels.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "qc_internal.h"
+
+namespace qc {
+
+// Coefficient job: one layer's gate matrices / generators / phase tables.
+struct CoefJob {
+  int cls, kind, source, offset, parity;
+  int ngates;
+  int per_sample;
+  int has_phase;
+  int tb;
+  long long coef_off;
+  long long bstride;
+};
+
+constexpr int kMaxLeading = 32;
+struct ProdVecJob {
+  int nl;
+  int kind[kMaxLeading], source[kMaxLeading], offset[kMaxLeading];
+};
+
+template <class R>
+cudaError_t launch_coef(const CoefJob* jobs_dev, int njobs, int n, int batch, int n_in,
+                        const double* x, const double* theta, void* coef, cudaStream_t st);
+template <class R>
+cudaError_t launch_prodvec(const ProdVecJob& P, int n, int batch, int n_in, const double* x,
+                           const double* theta, void* pv, cudaStream_t st);
+template <class R>
+cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi, cudaStream_t st);
+template <class R>
+cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, const void* coef,
+                        const void* s0, void* d0, const void* s1, void* d1, double* part,
+                        cudaStream_t st);
+template <class R>
+cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, const void* s0,
+                        void* d0, const void* s1, void* d1, double* part, cudaStream_t st);
+template <class R>
+cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, void* d0,
+                        const void* s1, void* d1, cudaStream_t st);
+template <class R>
+cudaError_t launch_expect(int n, int cb, int batch, const void* psi, double* part, double* ez,
+                          cudaStream_t st);
+template <class R>
+cudaError_t launch_laminit(int n, int cb, int batch, const double* gez, const void* psi, void* lam,
+                           cudaStream_t st);
+template <class R>
+cudaError_t launch_smem(const SmemLayer* prog_dev, int nl, int n, int batch, int bwd,
+                        const void* coef, const void* psi_in, void* psi_out, double* ez,
+                        const double* gez, double* part, int nslots, cudaStream_t st);
+cudaError_t launch_reduce(const RedJob* jobs, const long long* row0, const int* out0, int njobs,
+                          long long rowbase, long long nrows, int outbase, int nout,
+                          const RedOut* outs, int batch, int n_in, const double* part, double* V,
+                          double* d_theta, double* d_x, cudaStream_t st);
+
+size_t tile_smem_bytes(const TilePass& P, int ns, int rsize);
+size_t ring_smem_bytes(const RingPass& P, int rsize);
+size_t smem_circuit_bytes(int n, int bwd, int rsize);
+long long diag_grid(const DiagPass& P, int batch);
+
+}  // namespace qc

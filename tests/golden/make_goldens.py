@@ -1,0 +1,84 @@
+"""Writes oracle reference values for the full-size workloads.
+
+Every value stored here comes from ``oracle/qsim_oracle.py`` (complex128,
+per-gate einsum, reverse-sweep adjoint) on inputs drawn by
+``paper_2506_04891_gb300.workloads.draw_inputs`` with seed 0.  The CUDA path is
+never called.  Usage:
+
+    python tests/golden/make_goldens.py hea12 ibm20 ionq20 zz26
+
+Output: tests/golden/<workload>.npz with, for each listed sample b:
+ez[b] (<Z_q>), dth[b] (per-sample d loss / d theta), dx[b], and the amplitudes
+psi[b][idx] at a fixed seeded set of indices; for hea12 also ez / dx of every
+sample and the batch-summed d theta.  The loss is sum_q <Z_q> / n per sample.
+"""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import qsim_oracle as O  # noqa: E402
+from paper_2506_04891_gb300 import workloads as W  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SAMPLES = {"hea12": "all", "ibm20": [0, 31], "ionq20": [0, 31], "zz26": [0]}
+N_PSI_IDX = 512
+
+
+def _one(args):
+    name, b = args
+    cfg = W.WORKLOADS[name]
+    n, layers = cfg["n"], cfg["layers"]()
+    x, theta, g = W.draw_inputs(n, layers, cfg["batch"], seed=0)
+    n_theta, n_in = W.circuit_params(n, layers)
+    t0 = time.time()
+    ez, dth, dx = O.adjoint_sample(n, layers, x[b], theta, g[b], n_theta, n_in)
+    psi = O.forward_sample(n, layers, x[b], theta)
+    rng = np.random.default_rng(1000 + b)
+    idx = np.sort(rng.choice(2 ** n, size=min(N_PSI_IDX, 2 ** n), replace=False))
+    return name, b, ez, dth, dx, idx, psi[idx], (psi if n <= 12 else None), time.time() - t0
+
+
+def main(names):
+    jobs = []
+    for name in names:
+        cfg = W.WORKLOADS[name]
+        sm = SAMPLES[name]
+        bs = list(range(cfg["batch"])) if sm == "all" else sm
+        jobs += [(name, b) for b in bs]
+    procs = int(os.environ.get("GOLDEN_PROCS", "4"))
+    ctx = mp.get_context("spawn")
+    res = {}
+    with ctx.Pool(procs) as pool:
+        for r in pool.imap_unordered(_one, jobs):
+            name, b = r[0], r[1]
+            res.setdefault(name, {})[b] = r
+            print(f"{name} sample {b}: {r[-1]:.1f} s", flush=True)
+    for name, per in res.items():
+        bs = sorted(per)
+        out = dict(samples=np.array(bs),
+                   ez=np.stack([per[b][2] for b in bs]),
+                   dth=np.stack([per[b][3] for b in bs]),
+                   dx=np.stack([per[b][4] for b in bs]),
+                   psi_idx=np.stack([per[b][5] for b in bs]),
+                   psi_val=np.stack([per[b][6] for b in bs]))
+        if SAMPLES[name] == "all":
+            out["dth_sum"] = out["dth"].sum(axis=0)
+            keep = [0, len(bs) - 1]
+            out["psi_full"] = np.stack([per[bs[k]][7] for k in keep])
+            out["psi_full_samples"] = np.array([bs[k] for k in keep])
+            out["dth"] = out["dth"][keep]
+            out["dth_samples"] = np.array([bs[k] for k in keep])
+        np.savez_compressed(os.path.join(HERE, f"{name}.npz"), **out)
+        print("wrote", name)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(SAMPLES))

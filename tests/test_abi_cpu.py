@@ -1,0 +1,205 @@
+"""Host-side checks of the C ABI and the planner (no GPU needed).
+
+qc_create, qc_num_params, qc_workspace_bytes and qc_describe_plan never touch
+the device, so the library loads and plans on a machine without a GPU.
+"""
+import os
+import re
+
+import pytest
+
+from paper_2506_04891_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qlayer.h")
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2506_04891_gb300 import build
+    if not os.path.exists(build.OUT):
+        build.build()
+    from paper_2506_04891_gb300 import qlayer
+    return qlayer
+
+
+def header_symbols():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"QC_API\s+[\w\s\*]+?\b(qc_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_header_symbol(q):
+    import ctypes
+    lib = ctypes.CDLL(q.LIB_PATH)
+    syms = header_symbols()
+    assert len(syms) >= 12
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(q.EXPORTED) <= set(syms)
+
+
+def test_nm_exports_are_extern_c(q):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", q.LIB_PATH], capture_output=True, text=True).stdout
+    names = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    for s in header_symbols():
+        assert s in names, s
+
+
+def test_version_and_defaults(q):
+    assert q.qc_version() == 100
+    o = q.qc_default_options()
+    assert (o.ckpt_every, o.path, o.fuse) == (-1, 0, 1)
+
+
+@pytest.mark.parametrize("name", sorted(W.WORKLOADS))
+def test_num_params_match_workload_definition(q, name):
+    cfg = W.WORKLOADS[name]
+    layers = cfg["layers"]()
+    h = q.qc_create(cfg["n"], cfg["dtype"], layers)
+    try:
+        assert q.qc_num_params(h) == W.circuit_params(cfg["n"], layers)
+    finally:
+        q.qc_destroy(h)
+
+
+def test_param_counts_from_the_survey(q):
+    # P = 8, 360, 320, 548, 624 for the five circuits
+    assert W.circuit_params(4, W.WORKLOADS["hea4"]["layers"]())[0] == 8
+    assert W.circuit_params(12, W.WORKLOADS["hea12"]["layers"]())[0] == 360
+    assert W.circuit_params(20, W.WORKLOADS["ibm20"]["layers"]())[0] == 320
+    assert W.circuit_params(20, W.WORKLOADS["ionq20"]["layers"]())[0] == 548
+    assert W.circuit_params(26, W.WORKLOADS["zz26"]["layers"]())[0] == 624
+
+
+@pytest.mark.parametrize("bad,err", [
+    (dict(n=0), 1), (dict(n=31), 1),
+    (dict(layers=[("CNOT_RING", "theta", 0, 0)]), 1),      # unparametrised with a source
+    (dict(n=1, layers=[("CNOT_RING", "none", 0, 0)]), 1),   # ring needs n >= 2
+    (dict(layers=[("MS_BRICK", "theta", 0, 2)]), 1),        # parity
+    (dict(layers=[("RX", "theta", -1, 0)]), 1),             # offset
+    (dict(n=20, path=1), 5),                                # smem path too large
+])
+def test_create_rejects_invalid(q, bad, err):
+    n = bad.get("n", 4)
+    layers = bad.get("layers", [("RX", "input", 0, 0)])
+    opt = q.qc_default_options()
+    opt.path = bad.get("path", 0)
+    with pytest.raises(q.QCError) as e:
+        q.qc_create(n, "c64", layers, opt)
+    assert e.value.status == err
+    assert q.qc_last_error()
+
+
+def test_unknown_kind_rejected(q):
+    import ctypes
+    arr = (q.qc_layer * 1)()
+    arr[0] = q.qc_layer(99, 0, 0, 0)
+    h = ctypes.c_void_p()
+    assert q._lib.qc_create(4, 0, arr, 1, None, ctypes.byref(h)) == 1
+    assert h.value is None
+
+
+def _plan(q, n, layers, dtype="c64", batch=4, path=2, ckpt=-1, fuse=1):
+    opt = q.qc_default_options()
+    opt.path = path
+    opt.ckpt_every = ckpt
+    opt.fuse = fuse
+    h = q.qc_create(n, dtype, layers, opt)
+    try:
+        return q.qc_describe_plan(h, batch), q.qc_workspace_bytes(h, batch)
+    finally:
+        q.qc_destroy(h)
+
+
+def _tile_passes(desc):
+    out = []
+    for line in desc.splitlines():
+        if " TILE " not in line:
+            continue
+        d = dict(re.findall(r"(\w+)=(-?\d+)", line.split("[")[0]))
+        ops = re.findall(r"\[l=(\d+)(,2q)? np=(\d+)\]", line)
+        out.append((line[0], int(d["layer"]), {k: int(v) for k, v in d.items()}, ops))
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [5, 11, 12, 13, 14, 17, 20, 23, 26])
+def test_tile_passes_cover_every_qubit_once(q, n, dtype):
+    layers = [("RY", "theta", 0, 0), ("MS_BRICK", "theta", n, 0), ("ECR_BRICK", "none", 0, 1),
+              ("RX", "theta", 0, 0)]
+    desc, _ = _plan(q, n, layers, dtype=dtype, fuse=0)
+    tmax = 12 if dtype == "c64" else 11
+    for tag in "FB":
+        covered = {}
+        for t_, layer, d, ops in _tile_passes(desc):
+            if t_ != tag:
+                continue
+            assert d["t"] <= tmax and d["t"] >= 1
+            c, h0, t = d["c"], d["h0"], d["t"]
+            for l, is2q, np_ in ops:
+                l = int(l)
+                glob = l if l < c else h0 + (l - c)
+                bits = [glob, glob + 1] if is2q else [glob]
+                if is2q:
+                    # both bits of a brick pair sit in the same range of the tile
+                    assert (l + 1 < c) or (l >= c), (layer, l, c)
+                for b in bits:
+                    key = (layer, b)
+                    assert key not in covered, (tag, layer, b)
+                    covered[key] = True
+        for layer, kind in enumerate(["RY", "MS", "ECR", "RX"]):
+            bits = {b for (l_, b) in covered if l_ == layer}
+            if kind in ("RY", "RX"):
+                assert bits == set(range(n)), (tag, layer)
+            elif kind == "MS":
+                assert bits == {b for q0 in range(0, n - 1, 2) for b in (n - 2 - q0, n - 1 - q0)}
+            else:
+                assert bits == {b for q0 in range(1, n - 1, 2) for b in (n - 2 - q0, n - 1 - q0)}
+
+
+def test_zz26_plan_checkpoints_and_workspace(q):
+    cfg = W.WORKLOADS["zz26"]
+    desc, ws = _plan(q, 26, cfg["layers"](), batch=8, path=0)
+    head = desc.splitlines()[0]
+    assert "path=layer" in head and "nlead=2" in head and "nckpt=9" in head
+    S = 8 * 2 ** 26 * 8
+    # 2 psi + 2 lambda running buffers + 9 checkpoints, plus gradient partials
+    assert 13 * S <= ws < 13 * S + 3 * 2 ** 30
+
+
+def test_small_circuits_use_shared_memory_path(q):
+    for name in ("hea4", "hea12", "hea12_c128"):
+        cfg = W.WORKLOADS[name]
+        desc, _ = _plan(q, cfg["n"], cfg["layers"](), dtype=cfg["dtype"], batch=cfg["batch"], path=0)
+        assert "path=smem" in desc.splitlines()[0]
+
+
+def test_forward_plan_ends_in_psi_out(q):
+    for name in ("ibm20", "ionq20", "zz26"):
+        cfg = W.WORKLOADS[name]
+        desc, _ = _plan(q, cfg["n"], cfg["layers"](), batch=cfg["batch"], path=0)
+        fwd = [l for l in desc.splitlines() if l.startswith("F ")]
+        assert fwd[-1].rstrip().endswith("dst=0"), fwd[-1]
+        # no forward step writes into a buffer it reads unless it is an in-place kind
+        for line in fwd:
+            if " RING " in line:
+                d = dict(re.findall(r"(\w+)=(-?\d+)", line))
+                assert d["src"] != d["dst"]
+
+
+def test_backward_never_writes_psi_out(q):
+    for name in ("ibm20", "zz26"):
+        cfg = W.WORKLOADS[name]
+        desc, _ = _plan(q, cfg["n"], cfg["layers"](), batch=cfg["batch"], path=0)
+        for line in desc.splitlines():
+            if line.startswith("B ") and "dst=" in line:
+                d = dict(re.findall(r"(\w+)=(-?\d+)", line))
+                assert d["dst"] != "0", line
+
+
+def test_workspace_grows_with_batch(q):
+    layers = W.hea_circuit(14, 2)
+    _, w1 = _plan(q, 14, layers, batch=1)
+    _, w8 = _plan(q, 14, layers, batch=8)
+    assert w8 > w1 > 0
