@@ -544,7 +544,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         Step s;
         s.type = ST_DIAG; s.ns = 2;
         memset(&s.dp, 0, sizeof(s.dp));
-        s.dp.n = n; s.dp.cb = std::min(n, 12); s.dp.zmode = Li.zmode;
+        s.dp.n = n; s.dp.cb = std::min(n, 14); s.dp.zmode = Li.zmode;
         s.dp.xcomp = Li.cls == LC_XCOMP; s.dp.has_phase = Li.has_phase; s.dp.tb = Li.tb;
         s.dp.coef = Li.coef_off; s.dp.bstride = Li.coef_bstride; s.dp.nvals = n + 1;
         passes.push_back(s);

@@ -42,8 +42,18 @@ template <class R> __device__ __forceinline__ R im_cdot(cx<R> l, cx<R> v) {  // 
 }
 template <class R> __device__ __forceinline__ cx<R> ldc(const R* p) { return mk<R>(p[0], p[1]); }
 
-// Shared-memory swizzle: spreads strided accesses over banks.
-__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 31); }
+// Shared-memory swizzle: spreads strided accesses over banks.  Flips index
+// bits 1..4 only, so 16-byte pairs of complex64 stay adjacent and aligned.
+__device__ __forceinline__ int swz(int i) { return i ^ (((i >> 5) & 15) << 1); }
+
+// 16-byte asynchronous global -> shared copy (Ampere+ LDGSTS path)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -387,7 +397,7 @@ __device__ __forceinline__ void tile_dispatch(const TileOp& o, int i, cx<R>* v0,
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials per CTA into part[slot][block]).
 template <class R, int NS, int RB>
-__global__ void __launch_bounds__(kThreads) k_tile(const __grid_constant__ TilePass P, const R* __restrict__ coef,
+__global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ TilePass P, const R* __restrict__ coef,
                                                    const cx<R>* src0, cx<R>* dst0,
                                                    const cx<R>* src1, cx<R>* dst1,
                                                    double* __restrict__ part) {
@@ -414,10 +424,18 @@ __global__ void __launch_bounds__(kThreads) k_tile(const __grid_constant__ TileP
     const R* s = coef + o.coef + (long long)b * o.bstride;
     for (int i = threadIdx.x; i < o.nco; i += kThreads) sco[o.soff + i] = s[i];
   }
-  for (int i = threadIdx.x; i < T; i += kThreads) {
-    const long long gi = soff + (i & cmask) + ((long long)(i >> c) << h0);
-    S0[swz(i)] = src0[gi];
-    if (NS == 2) S1[swz(i)] = src1[gi];
+  // 16-byte copies: 2 complex64 or 1 complex128 each; all issued before one wait
+  constexpr int EPC = 16 / sizeof(C);
+  {
+    const int nv = T / EPC;
+#pragma unroll 4
+    for (int v = threadIdx.x; v < nv; v += kThreads) {
+      const int i = v * EPC;
+      const long long gi = soff + (i & cmask) + ((long long)(i >> c) << h0);
+      cp_async16(&S0[swz(i)], &src0[gi]);
+      if (NS == 2) cp_async16(&S1[swz(i)], &src1[gi]);
+    }
+    cp_async_wait_all();
   }
   __syncthreads();
 
@@ -464,10 +482,13 @@ __global__ void __launch_bounds__(kThreads) k_tile(const __grid_constant__ TileP
   }
 
   if (P.store) {
-    for (int i = threadIdx.x; i < T; i += kThreads) {
+    const int nv = T / EPC;
+#pragma unroll 4
+    for (int v = threadIdx.x; v < nv; v += kThreads) {
+      const int i = v * EPC;
       const long long gi = soff + (i & cmask) + ((long long)(i >> c) << h0);
-      dst0[gi] = S0[swz(i)];
-      if (NS == 2) dst1[gi] = S1[swz(i)];
+      *reinterpret_cast<float4*>(&dst0[gi]) = *reinterpret_cast<const float4*>(&S0[swz(i)]);
+      if (NS == 2) *reinterpret_cast<float4*>(&dst1[gi]) = *reinterpret_cast<const float4*>(&S1[swz(i)]);
     }
   }
   if (NS == 2 && P.nslots > 0) {
@@ -486,19 +507,19 @@ __global__ void __launch_bounds__(kThreads) k_tile(const __grid_constant__ TileP
 // Per thread: u_p = zt_p ? (W - accz_p) : accz_p, with accz_p the per-thread
 // sums over the compile-time j bits; written to sred[(1 + p) * kThreads + tid]
 // (added when `add`), sred[tid] holds W.
-template <int NA>
-__device__ __forceinline__ void marg_write(double* sred, int n, long long zt, float W,
-                                           const float* acc, int acc_lo, bool add) {
+template <int NA, class A>
+__device__ __forceinline__ void marg_write(double* sred, int n, long long zt, A W,
+                                           const A* acc, int acc_lo, bool add) {
   const int tid = threadIdx.x;
   double w0 = add ? sred[tid] : 0.0;
   sred[tid] = w0 + (double)W;
   for (int p = 0; p < n; ++p) {
-    float a = 0.f;
+    A a = 0;
     const int q = p - acc_lo;
 #pragma unroll
     for (int s = 0; s < NA; ++s)
       if (s == q) a = acc[s];
-    float u = ((zt >> p) & 1) ? (W - a) : a;
+    A u = ((zt >> p) & 1) ? (W - a) : a;
     double old = add ? sred[(1 + p) * kThreads + tid] : 0.0;
     sred[(1 + p) * kThreads + tid] = old + (double)u;
   }
@@ -567,9 +588,9 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
   const bool active = tid < CH;
 
   if (!XC) {
-    float W = 0.f, acc[JB + 2];
+    R W = 0, acc[JB + 2];
 #pragma unroll
-    for (int s = 0; s < JB + 2; ++s) acc[s] = 0.f;
+    for (int s = 0; s < JB + 2; ++s) acc[s] = 0;
     if (active) {
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
@@ -584,7 +605,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
           const C u = cmulc<R>(ph, src1[sb + k]);  // conj(phase) * lambda
           dst0[sb + k] = y;
           dst1[sb + k] = u;
-          const float w = (float)im_cdot<R>(u, y);
+          const R w = im_cdot<R>(u, y);
           W += w;
           constexpr int dummy = 0;
           (void)dummy;
@@ -596,7 +617,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
     }
     if (NS == 2) {
       const long long zt = ztrans(base + tid, n, ZM);
-      marg_write<JB + 2>(sred, n, active ? zt : 0, W, acc, 7, false);
+      marg_write<JB + 2, R>(sred, n, active ? zt : 0, W, acc, 7, false);
       __syncthreads();
       marg_flush(sred, P.nvals, part, gridDim.x, blockIdx.x);
     }
@@ -605,9 +626,9 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
     const bool single = (nch == 1);
     const long long mbase = (nch - 1 - ch) << cb;
     const int lim = single ? CH / 2 : CH;
-    float W = 0.f, acc[JB + 2], Wm = 0.f, accm[JB + 2];
+    R W = 0, acc[JB + 2], Wm = 0, accm[JB + 2];
 #pragma unroll
-    for (int s = 0; s < JB + 2; ++s) acc[s] = accm[s] = 0.f;
+    for (int s = 0; s < JB + 2; ++s) acc[s] = accm[s] = 0;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const int i = tid + (j << 8);
@@ -636,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
           }
           dst0[sb + k] = yk; dst1[sb + k] = uk;
           dst0[sb + km] = ym; dst1[sb + km] = um;
-          const float wk = (float)im_cdot<R>(uk, yk), wm = (float)im_cdot<R>(um, ym);
+          const R wk = im_cdot<R>(uk, yk), wm = im_cdot<R>(um, ym);
           W += wk;
           Wm += wm;
 #pragma unroll
@@ -654,8 +675,8 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
       const bool act = tid < lim || (tid < CH && !single);
       const long long zt = base + tid;
       const long long ztm = (mbase + CH - 1) ^ tid;
-      marg_write<JB + 2>(sred, n, act ? zt : 0, act ? W : 0.f, acc, 7, false);
-      marg_write<JB + 2>(sred, n, act ? ztm : 0, act ? Wm : 0.f, accm, 7, true);
+      marg_write<JB + 2, R>(sred, n, act ? zt : 0, act ? W : (R)0, acc, 7, false);
+      marg_write<JB + 2, R>(sred, n, act ? ztm : 0, act ? Wm : (R)0, accm, 7, true);
       __syncthreads();
       marg_flush(sred, P.nvals, part, gridDim.x, blockIdx.x);
     }
@@ -677,21 +698,21 @@ __global__ void __launch_bounds__(kThreads) k_expect(int n, int cb, const cx<R>*
   const C* s = psi + ((long long)b << n) + base;
   const int tid = threadIdx.x;
   const bool active = tid < (1 << cb);
-  float W = 0.f, acc[JB + 2];
+  R W = 0, acc[JB + 2];
 #pragma unroll
-  for (int q = 0; q < JB + 2; ++q) acc[q] = 0.f;
+  for (int q = 0; q < JB + 2; ++q) acc[q] = 0;
   if (active) {
 #pragma unroll
     for (int j = 0; j < (1 << JB); ++j) {
       const C x = s[tid + (j << 8)];
-      const float w = (float)(x.x * x.x + x.y * x.y);
+      const R w = x.x * x.x + x.y * x.y;
       W += w;
 #pragma unroll
       for (int q = 0; q < JB + 2; ++q)
         if (((j << 8) >> (7 + q)) & 1) acc[q] += w;
     }
   }
-  marg_write<JB + 2>(sred, n, active ? (base + tid) : 0, W, acc, 7, false);
+  marg_write<JB + 2, R>(sred, n, active ? (base + tid) : 0, W, acc, 7, false);
   __syncthreads();
   marg_flush(sred, n + 1, part, gridDim.x, blockIdx.x);
 }
@@ -702,11 +723,12 @@ __global__ void __launch_bounds__(kThreads) k_laminit(int n, int cb, const doubl
                                                       const cx<R>* __restrict__ psi,
                                                       cx<R>* __restrict__ lam) {
   using C = cx<R>;
-  __shared__ double Sa[64], Sb[64];
+  __shared__ double Sa[64], Sb[64], g[kMaxQubits];
   const int nchb = n - cb;
   const int b = (int)(blockIdx.x >> nchb);
   const long long base = ((long long)blockIdx.x & ((1LL << nchb) - 1)) << cb;
-  const double* g = gez + (long long)b * n;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) g[q] = gez[(long long)b * n + q];
+  __syncthreads();
   const int la = cb < 6 ? cb : 6, lb = cb - la;
   double tot = 0, hi = 0;
   for (int q = 0; q < n; ++q) {
@@ -892,21 +914,33 @@ __global__ void k_finalize(const RedJob* __restrict__ jobs, const long long* __r
   if (J.source == QC_SRC_THETA && d_theta) d_theta[ro.pidx] += tot;
 }
 
-// <Z_q> from marginals: ez[b][q] = V[b][0] - 2 V[b][1 + (n-1-q)]
-__global__ void k_ez_from_marg(int n, int batch, int blk_per_sample, long long nblk,
-                               const double* __restrict__ part, double* __restrict__ ez) {
-  const int b = blockIdx.x;
-  __shared__ double vals[kMaxQubits + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = warp; v <= n; v += kWarps) {
-    const double* p = part + (long long)v * nblk + (long long)b * blk_per_sample;
-    double s = 0;
-    for (int i = lane; i < blk_per_sample; i += 32) s += p[i];
-    s = warp_sum(s);
-    if (lane == 0) vals[v] = s;
+// <Z_q> from marginals: ez[b][q] = W - 2 M_{n-1-q}, one block per (b, q)
+// summing the sample's CTA partials of W and of the qubit's bit marginal.
+__global__ void __launch_bounds__(kThreads) k_ez_from_marg(int n, int blk_per_sample, long long nblk,
+                                                           const double* __restrict__ part,
+                                                           double* __restrict__ ez) {
+  const int b = blockIdx.x / n, q = blockIdx.x % n;
+  const int p = n - 1 - q;
+  const double* w = part + (long long)b * blk_per_sample;
+  const double* m = part + (long long)(1 + p) * nblk + (long long)b * blk_per_sample;
+  double sw = 0, sm = 0;
+  for (int i = threadIdx.x; i < blk_per_sample; i += kThreads) {
+    sw += w[i];
+    sm += m[i];
+  }
+  __shared__ double red[2][kWarps];
+  sw = warp_sum(sw);
+  sm = warp_sum(sm);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sw;
+    red[1][threadIdx.x >> 5] = sm;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < n; q += blockDim.x) ez[(long long)b * n + q] = vals[0] - 2.0 * vals[1 + (n - 1 - q)];
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0;
+    for (int k = 0; k < kWarps; ++k) { a += red[0][k]; c += red[1][k]; }
+    ez[(long long)b * n + q] = a - 2.0 * c;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1320,6 +1354,8 @@ static cudaError_t launch_diag_z(const DiagPass& P, int batch, const void* coef,
     case 2: return launch_diag_jb<R, NS, ZM, XC, 2>(P, batch, coef, s0, d0, s1, d1, part, st);
     case 3: return launch_diag_jb<R, NS, ZM, XC, 3>(P, batch, coef, s0, d0, s1, d1, part, st);
     case 4: return launch_diag_jb<R, NS, ZM, XC, 4>(P, batch, coef, s0, d0, s1, d1, part, st);
+    case 5: return launch_diag_jb<R, NS, ZM, XC, 5>(P, batch, coef, s0, d0, s1, d1, part, st);
+    case 6: return launch_diag_jb<R, NS, ZM, XC, 6>(P, batch, coef, s0, d0, s1, d1, part, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -1392,7 +1428,7 @@ cudaError_t launch_expect(int n, int cb, int batch, const void* psi, double* par
   }
   if (e != cudaSuccess) return e;
   long long nblk = (long long)batch << (n - cb);
-  k_ez_from_marg<<<batch, kThreads, 0, st>>>(n, batch, 1 << (n - cb), nblk, part, ez);
+  k_ez_from_marg<<<batch * n, kThreads, 0, st>>>(n, 1 << (n - cb), nblk, part, ez);
   return cudaGetLastError();
 }
 
