@@ -50,7 +50,24 @@ def parse():
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget", type=float, default=15.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # smaller cases of the same circuit family, for profiling captures
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--depth", type=int, default=None)
     return ap.parse_args()
+
+
+def workload_cfg(args):
+    cfg = dict(W.WORKLOADS[args.workload])
+    if args.n is None and args.batch is None and args.depth is None:
+        return cfg, DESCR[args.workload]
+    n = args.n or cfg["n"]
+    B = args.batch or cfg["batch"]
+    fam = {"zz26": lambda d: W.zz_circuit(n, d or 12), "hea12": lambda d: W.hea_circuit(n, d or 10),
+           "ibm20": lambda d: W.ibm_circuit(n, d or 8), "ionq20": lambda d: W.ionq_circuit(n, d or 8)}
+    layers = fam[args.workload](args.depth)
+    cfg.update(n=n, batch=B, layers=lambda: layers)
+    return cfg, f"{args.workload} family at n={n}, batch {B}, depth {args.depth} (profiling case)"
 
 
 # ---------------------------------------------------------------------------
@@ -207,7 +224,7 @@ def gpu_arm(args):
     if world > 1:
         dist.init_process_group("nccl")
 
-    cfg = W.WORKLOADS[args.workload]
+    cfg, descr = workload_cfg(args)
     n, layers, B = cfg["n"], cfg["layers"](), cfg["batch"]
     circ = Q.Circuit(n, layers, dtype=cfg["dtype"])
     x_np, th_np, g_np = W.draw_inputs(n, layers, B, seed=rank)
@@ -313,7 +330,7 @@ def gpu_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if cfg["dtype"] == "c64" else "f64", "data": "synthetic",
-            "config": {"workload": DESCR[args.workload], "n": n, "batch_per_gpu": B,
+            "config": {"workload": descr, "n": n, "batch_per_gpu": B,
                        "global_batch": B * world, "layers": L, "n_theta": circ.n_theta,
                        "state_bytes": S, "l2": "inputs larger than L2: every pass streams the batch state",
                        "parallelism": f"dp{world}: batch sharded, d theta all-reduced" if world > 1 else "single GPU"},
@@ -326,7 +343,7 @@ def gpu_arm(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and descr == DESCR[args.workload]:
             try:
                 ob = oracle_baseline(args.workload, 15.0)
                 out["cpu_baseline"] = {"value": round(ob["evals_per_s"], 6), "unit": UNIT,

@@ -96,6 +96,7 @@ struct Step {
   DiagPass dp;
   RingPass rp;
   int cb = 12;
+  int cps = 1;  // tile passes: CTAs per sample
   int s0 = B_NONE, d0 = B_NONE, s1 = B_NONE, d1 = B_NONE;
   long long part_off = 0;
   int layer = -1;
@@ -161,9 +162,34 @@ struct qc_circuit {
 
 namespace {
 
+// Largest tile (log2 amplitudes): two buffers of ns states must leave room
+// for two CTAs per SM.
 int tile_tmax(const qc_circuit* c, int ns) {
-  (void)ns;
-  return c->dtype == QC_C64 ? 12 : 11;
+  if (c->dtype == QC_C64) return ns == 2 ? 11 : 12;
+  return ns == 2 ? 10 : 11;
+}
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      cached = v;
+    else
+      cached = 152;  // GB300; used when planning without a device
+    cudaGetLastError();
+  }
+  return cached;
+}
+
+// CTAs per sample of a persistent tile pass: two resident CTAs per SM.
+int tile_cps(int batch, int n, int t) {
+  const long long tps = 1LL << (n - t);
+  long long c = (2LL * sm_count() + batch - 1) / batch;
+  if (c > tps) c = tps;
+  if (c < 1) c = 1;
+  return (int)c;
 }
 int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 int reg_bits(const qc_circuit* c, int ns) {
@@ -192,7 +218,9 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
   // later passes share the bits left after the first one evenly
   const int rest = std::max(0, n - tmax);
   const int later_cap = tmax - cbits;
-  const int nlater = rest > 0 ? (rest + later_cap - 2) / (later_cap - 1) : 0;  // slack for pair cuts
+  // brick layers may have to end a pass one bit early so no pair is cut
+  const int eff_cap = L.cls == LC_DENSE2 ? later_cap - 1 : later_cap;
+  const int nlater = rest > 0 ? (rest + eff_cap - 1) / eff_cap : 0;
   const int even_cap = nlater > 0 ? (rest + nlater - 1) / nlater : later_cap;
   int s = 0;
   bool first = true;
@@ -206,7 +234,10 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     if (first) {
       P.c = e; P.h0 = e; P.t = e;
     } else {
-      P.c = std::min(cbits, s); P.h0 = s; P.t = P.c + (e - s);
+      // spare tile capacity widens the contiguous low segment
+      P.c = std::min(s, std::max(cbits, tmax - (e - s)));
+      P.h0 = s;
+      P.t = P.c + (e - s);
     }
     auto local = [&](int p) { return first ? p : P.c + (p - s); };
     struct OpTmp { TileOp op; std::vector<int> pidx; };
@@ -219,6 +250,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
         o.op.l = (int16_t)local(p);
         o.op.is2q = 0;
         o.op.real = (int8_t)L.real;
+        o.op.gk = (int8_t)(L.kind == QC_L_RX ? 1 : (L.kind == QC_L_RY ? 2 : 0));
         o.op.np = (int16_t)((ns == 2 && L.diff) ? 1 : 0);
         o.op.coef = L.coef_off + (long long)q * kRec1q;
         o.op.bstride = L.coef_bstride;
@@ -462,6 +494,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         for (auto& tp : plan_tile_layer(c, Li, 1, dummy)) {
           Step s;
           s.type = ST_TILE; s.ns = 1; s.tp = tp; s.rb = std::min(reg_bits(c, 1), tp.t);
+          s.cps = tile_cps(batch, n, tp.t);
           passes.push_back(s);
         }
       } else if (Li.cls == LC_DIAG || Li.cls == LC_XCOMP) {
@@ -538,6 +571,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         for (auto& tp : plan_tile_layer(c, Li, 2, pslots)) {
           Step s;
           s.type = ST_TILE; s.ns = 2; s.tp = tp; s.rb = std::min(reg_bits(c, 2), tp.t);
+          s.cps = tile_cps(batch, n, tp.t);
           passes.push_back(s);
         }
       } else if (Li.cls == LC_DIAG || Li.cls == LC_XCOMP) {
@@ -570,12 +604,12 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         if (l == 0 && i + 1 == passes.size() && s.type == ST_TILE) s.tp.store = 0;
         // gradient bookkeeping
         if (s.type == ST_TILE && s.tp.nslots > 0) {
-          const long long nblk = (long long)batch << (n - s.tp.t);
+          const long long nblk = (long long)batch * s.cps;
           s.part_off = part_off;
           std::vector<OutMap> outs;
           for (auto& e : pslots)
             if (e[0] == (int)i) outs.push_back(OutMap{0, e[1], e[2], 1.0});
-          add_job(p, RK_DIRECT, Li.source, part_off, nblk, s.tp.nslots, 1LL << (n - s.tp.t), outs);
+          add_job(p, RK_DIRECT, Li.source, part_off, nblk, s.tp.nslots, s.cps, outs);
           part_off += nblk * s.tp.nslots;
         } else if (s.type == ST_DIAG && Li.diff && Li.nparams > 0) {
           const long long nblk = diag_grid(s.dp, batch);
@@ -602,7 +636,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       if (s.type == ST_DIAG && s.part_off < 0) s.part_off = part_off;
     part_off += scratch_need;
     // <Z> partials (forward, ez requested)
-    const int cbe = std::min(n, 12);
+    const int cbe = std::min(n, 14);
     const long long ez_need = ((long long)batch << (n - cbe)) * (n + 1);
     p.part_doubles = (size_t)std::max(part_off, ez_need);
 
@@ -748,8 +782,8 @@ qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int 
       }
       case ST_TILE: {
         ProfScope ps(s.ns == 2 ? PC_TILE_B : PC_TILE_F, passb, st);
-        e = launch_tile<R>(s.tp, s.rb, s.ns, batch, coef, buf(s.s0), buf(s.d0), buf(s.s1), buf(s.d1),
-                           part + s.part_off, st);
+        e = launch_tile<R>(s.tp, s.rb, s.ns, batch, s.cps, coef, buf(s.s0), buf(s.d0), buf(s.s1),
+                           buf(s.d1), part + s.part_off, st);
         break;
       }
       case ST_DIAG: {
@@ -824,7 +858,7 @@ qc_status forward_impl(qc_circuit* c, int batch, const double* x, const double* 
     s = run_steps<R>(c, *p, p->fwd, batch, x, theta, nullptr, psi_out, ws, st);
     if (s != QC_OK) return s;
     if (ez) {
-      const int cbe = std::min(c->n, 12);
+      const int cbe = std::min(c->n, 14);
       ProfScope ps(PC_EXPECT, (double)p->S, st, 2);
       cudaError_t e = launch_expect<R>(c->n, cbe, batch, psi_out, (double*)(ws + p->off_part), ez, st);
       if (e != cudaSuccess) return cuda_fail(e, "expect kernel");
@@ -1019,7 +1053,7 @@ QC_API qc_status qc_expect_z(qc_circuit* c, int batch, const void* psi, double* 
   qc_status s = check_common(c, batch);
   if (s != QC_OK) return s;
   if (!psi || !ez) return fail(QC_ERR_INVALID, "psi and ez must be non-NULL");
-  const int n = c->n, cb = std::min(n, 12);
+  const int n = c->n, cb = std::min(n, 14);
   const size_t need = (size_t)(((long long)batch << (n - cb)) * (n + 1)) * sizeof(double);
   if (need > c->exp_scratch_bytes) {
     if (c->exp_scratch) {
@@ -1177,8 +1211,8 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
   auto dump = [&](const char* tag, const std::vector<Step>& v) {
     for (auto& st : v) {
       if (st.type == ST_TILE) {
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d rounds=%d ops=%d slots=%d store=%d src=%d dst=%d",
-                 tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.tp.nrounds, st.tp.nops, st.tp.nslots,
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d rounds=%d ops=%d slots=%d store=%d src=%d dst=%d",
+                 tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nrounds, st.tp.nops, st.tp.nslots,
                  st.tp.store, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {

@@ -54,6 +54,8 @@ struct TileOp {
   int16_t l;        // local bit (1q) or lower local bit of the pair (2q)
   int8_t is2q;
   int8_t real;      // 1q with a real matrix
+  int8_t gk;        // 1q generator: 0 generic A, 1 A = -i/2 X (RX), 2 A = -i/2 Y (RY)
+  int8_t pad0;
   int16_t np;       // gradient parameters produced (0, 1 or 3)
   int16_t slot;     // first gradient slot in the pass's partial vector
   int32_t soff;     // offset of the op's coefficients in the staged smem block (R units)

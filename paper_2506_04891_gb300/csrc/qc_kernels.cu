@@ -42,10 +42,6 @@ template <class R> __device__ __forceinline__ R im_cdot(cx<R> l, cx<R> v) {  // 
 }
 template <class R> __device__ __forceinline__ cx<R> ldc(const R* p) { return mk<R>(p[0], p[1]); }
 
-// Shared-memory swizzle: spreads strided accesses over banks.  Flips index
-// bits 1..4 only, so 16-byte pairs of complex64 stay adjacent and aligned.
-__device__ __forceinline__ int swz(int i) { return i ^ (((i >> 5) & 15) << 1); }
-
 // 16-byte asynchronous global -> shared copy (Ampere+ LDGSTS path)
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -243,8 +239,29 @@ __device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
 // backward single-qubit op: undo M on psi and lambda, then accumulate
 // 2 Re <lambda| A |psi> on the gate's input side.
 template <class R, int RB, int I>
-__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, R* acc) {
+__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, R* acc) {
   using C = cx<R>;
+  if (real && gk == 2) {
+    // RY: undo with M^T; 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
+    const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
+    R g = 0;
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        const int a1 = a | (1 << I);
+        C x0 = p[a], x1 = p[a1];
+        C y0 = mk<R>(fma(m00, x0.x, m10 * x1.x), fma(m00, x0.y, m10 * x1.y));
+        C y1 = mk<R>(fma(m01, x0.x, m11 * x1.x), fma(m01, x0.y, m11 * x1.y));
+        p[a] = y0; p[a1] = y1;
+        C u0 = l[a], u1 = l[a1];
+        C w0 = mk<R>(fma(m00, u0.x, m10 * u1.x), fma(m00, u0.y, m10 * u1.y));
+        C w1 = mk<R>(fma(m01, u0.x, m11 * u1.x), fma(m01, u0.y, m11 * u1.y));
+        l[a] = w0; l[a1] = w1;
+        g += re_cdot<R>(w1, y0) - re_cdot<R>(w0, y1);
+      }
+    if (np) acc[I * 3] += g;
+    return;
+  }
   if (real) {
     // M^dagger = M^T for a real M
     const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
@@ -286,12 +303,17 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
         C w1 = cfmac<R>(m11, u1, cfmac<R>(m01, u0, mk<R>(0, 0)));
         l[a] = w0; l[a1] = w1;
         if (np) {
-          C t0 = cfma<R>(a01, y1, cmul<R>(a00, y0));
-          C t1 = cfma<R>(a11, y1, cmul<R>(a10, y0));
-          g += re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1);
+          if (gk == 1) {
+            // RX: 2 Re <l|(-i/2 X)|p> = Im(l0* p1 + l1* p0)
+            g += im_cdot<R>(w0, y1) + im_cdot<R>(w1, y0);
+          } else {
+            C t0 = cfma<R>(a01, y1, cmul<R>(a00, y0));
+            C t1 = cfma<R>(a11, y1, cmul<R>(a10, y0));
+            g += 2 * (re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1));
+          }
         }
       }
-    if (np) acc[I * 3] += 2 * g;
+    if (np) acc[I * 3] += g;
   }
 }
 
@@ -377,11 +399,11 @@ __device__ __forceinline__ void tile_dispatch(const TileOp& o, int i, cx<R>* v0,
   } else {
     if (!o.is2q) {
       switch (i) {
-        case 0: bw1<R, RB, 0>(v0, v1, mc, o.real, o.np, acc); break;
-        case 1: if (RB > 1) bw1<R, RB, (RB > 1 ? 1 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
-        case 2: if (RB > 2) bw1<R, RB, (RB > 2 ? 2 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
-        case 3: if (RB > 3) bw1<R, RB, (RB > 3 ? 3 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
-        case 4: if (RB > 4) bw1<R, RB, (RB > 4 ? 4 : 0)>(v0, v1, mc, o.real, o.np, acc); break;
+        case 0: bw1<R, RB, 0>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
+        case 1: if (RB > 1) bw1<R, RB, (RB > 1 ? 1 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
+        case 2: if (RB > 2) bw1<R, RB, (RB > 2 ? 2 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
+        case 3: if (RB > 3) bw1<R, RB, (RB > 3 ? 3 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
+        case 4: if (RB > 4) bw1<R, RB, (RB > 4 ? 4 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
       }
     } else {
       switch (i) {
@@ -394,104 +416,162 @@ __device__ __forceinline__ void tile_dispatch(const TileOp& o, int i, cx<R>* v0,
   }
 }
 
+// Tile-pass shared-memory layout: XOR swizzle of index bits 0..3 by bits
+// 4..7.  It is linear over GF(2), so the address of (base | a << lo) is
+// swz(base) ^ swz(a << lo), and every round's half-warp accesses hit 16
+// distinct 8-byte bank pairs.
+__device__ __forceinline__ int tswz(int i) { return i ^ ((i >> 4) & 15); }
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Persistent tile pass.  CTA (b, r) of the cps CTAs of sample b handles tiles
+// f = r, r + cps, ... of that sample; the next tile is copied into the second
+// shared-memory buffer while the current one is processed.
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
-// lambda, accumulate gradient partials per CTA into part[slot][block]).
+// lambda, accumulate gradient partials into part[slot][block]).
 template <class R, int NS, int RB>
-__global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ TilePass P, const R* __restrict__ coef,
-                                                   const cx<R>* src0, cx<R>* dst0,
-                                                   const cx<R>* src1, cx<R>* dst1,
-                                                   double* __restrict__ part) {
+__global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ TilePass P,
+                                                      const R* __restrict__ coef,
+                                                      const cx<R>* src0, cx<R>* dst0,
+                                                      const cx<R>* src1, cx<R>* dst1,
+                                                      double* __restrict__ part, int cps) {
   using C = cx<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = P.t, n = P.n, c = P.c, h0 = P.h0;
   const int T = 1 << t;
-  C* S0 = reinterpret_cast<C*>(smraw);
-  C* S1 = S0 + T;
-  R* sco = reinterpret_cast<R*>(S0 + NS * T);
-  double* sred = reinterpret_cast<double*>(sco + ((P.ncoef + 1) & ~1));
+  C* buf = reinterpret_cast<C*>(smraw);  // [2][NS][T]
+  R* sco = reinterpret_cast<R*>(buf + 2 * NS * T);
+  double* sred = reinterpret_cast<double*>(sco + ((P.ncoef + 1) & ~1));  // [kWarps][nslots]
 
-  const int fb = n - t;
-  const long long tile = blockIdx.x;
-  const int b = (int)(tile >> fb);
-  const long long f = tile & ((1LL << fb) - 1);
+  const long long tps = 1LL << (n - t);
+  const int b = blockIdx.x / cps;
+  const int r0 = blockIdx.x % cps;
   const int m = t - c, gap = h0 - c;
-  const long long base = ((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m));
-  const long long soff = ((long long)b << n) + base;
   const int cmask = (1 << c) - 1;
+  const long long sb = (long long)b << n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   for (int k = 0; k < P.nops; ++k) {
     const TileOp& o = P.ops[k];
     const R* s = coef + o.coef + (long long)b * o.bstride;
     for (int i = threadIdx.x; i < o.nco; i += kThreads) sco[o.soff + i] = s[i];
   }
-  // 16-byte copies: 2 complex64 or 1 complex128 each; all issued before one wait
-  constexpr int EPC = 16 / sizeof(C);
-  {
-    const int nv = T / EPC;
-#pragma unroll 4
-    for (int v = threadIdx.x; v < nv; v += kThreads) {
-      const int i = v * EPC;
-      const long long gi = soff + (i & cmask) + ((long long)(i >> c) << h0);
-      cp_async16(&S0[swz(i)], &src0[gi]);
-      if (NS == 2) cp_async16(&S1[swz(i)], &src1[gi]);
-    }
-    cp_async_wait_all();
-  }
-  __syncthreads();
+  if (NS == 2)
+    for (int i = threadIdx.x; i < kWarps * P.nslots; i += kThreads) sred[i] = 0;
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = 0; r < P.nrounds; ++r) {
-    const int lo = P.rlo[r];
-    const int op0 = P.rop[r], op1 = P.rop[r + 1];
-    R acc[RB * 3];
-#pragma unroll
-    for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
-    for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
-      const int ib = (g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB));
-      C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
-#pragma unroll
-      for (int a = 0; a < (1 << RB); ++a) {
-        v0[a] = S0[swz(ib | (a << lo))];
-        if (NS == 2) v1[a] = S1[swz(ib | (a << lo))];
-      }
-      for (int k = op0; k < op1; ++k) {
-        const TileOp& o = P.ops[k];
-        tile_dispatch<R, NS, RB>(o, o.l - lo, v0, v1, sco + o.soff, acc);
-      }
-#pragma unroll
-      for (int a = 0; a < (1 << RB); ++a) {
-        S0[swz(ib | (a << lo))] = v0[a];
-        if (NS == 2) S1[swz(ib | (a << lo))] = v1[a];
-      }
+  auto tile_base = [&](long long f) -> long long {
+    return sb + (((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
+  };
+  auto issue = [&](long long f, int slot) {
+    const long long base = tile_base(f);
+    C* d0 = buf + (long long)slot * NS * T;
+    for (int i = threadIdx.x; i < T; i += kThreads) {
+      const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
+      cp_async_elem<sizeof(C)>(&d0[tswz(i)], &src0[gi]);
+      if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + tswz(i)], &src1[gi]);
     }
-    if (NS == 2) {
-      for (int k = op0; k < op1; ++k) {
-        const TileOp& o = P.ops[k];
-        const int i = o.l - lo;
-        for (int q = 0; q < o.np; ++q) {
-          R val = 0;
+  };
+
+  long long f = r0;
+  int slot = 0;
+  if (f < tps) issue(f, 0);
+  cp_async_commit();
+  for (; f < tps; f += cps) {
+    const long long fn = f + cps;
+    if (fn < tps) issue(fn, slot ^ 1);
+    cp_async_commit();
+    cp_async_wait_group<1>();
+    __syncthreads();
+    C* S0 = buf + (long long)slot * NS * T;
+    C* S1 = S0 + T;
+
+    for (int r = 0; r < P.nrounds; ++r) {
+      const int lo = P.rlo[r];
+      const int op0 = P.rop[r], op1 = P.rop[r + 1];
+      R acc[RB * 3];
 #pragma unroll
-          for (int s = 0; s < RB * 3; ++s)
-            if (s == i * 3 + q) val = acc[s];
-          double v = warp_sum((double)val);
-          if (lane == 0) sred[warp * P.nslots + o.slot + q] = v;
+      for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
+      int off[1 << RB];
+      off[0] = 0;
+#pragma unroll
+      for (int a = 1; a < (1 << RB); ++a) {
+        const int j = __ffs(a) - 1;
+        off[a] = off[a ^ (1 << j)] ^ tswz(1 << (lo + j));
+      }
+      for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
+        const int pb = tswz((g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB)));
+        C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
+#pragma unroll
+        for (int a = 0; a < (1 << RB); ++a) {
+          v0[a] = S0[pb ^ off[a]];
+          if (NS == 2) v1[a] = S1[pb ^ off[a]];
+        }
+        for (int k = op0; k < op1; ++k) {
+          const TileOp& o = P.ops[k];
+          tile_dispatch<R, NS, RB>(o, o.l - lo, v0, v1, sco + o.soff, acc);
+        }
+#pragma unroll
+        for (int a = 0; a < (1 << RB); ++a) {
+          S0[pb ^ off[a]] = v0[a];
+          if (NS == 2) S1[pb ^ off[a]] = v1[a];
+        }
+      }
+      if (NS == 2) {
+        for (int k = op0; k < op1; ++k) {
+          const TileOp& o = P.ops[k];
+          const int i = o.l - lo;
+          for (int q = 0; q < o.np; ++q) {
+            R val = 0;
+#pragma unroll
+            for (int s = 0; s < RB * 3; ++s)
+              if (s == i * 3 + q) val = acc[s];
+            double v = warp_sum((double)val);
+            if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    if (P.store) {
+      const long long base = tile_base(f);
+      if (sizeof(C) == 8) {
+        for (int i = 2 * threadIdx.x; i < T; i += 2 * kThreads) {
+          const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
+          const int pi = tswz(i);
+          C e0 = S0[pi], e1 = S0[pi ^ 1];
+          *reinterpret_cast<float4*>(&dst0[gi]) = make_float4(e0.x, e0.y, e1.x, e1.y);
+          if (NS == 2) {
+            C u0 = S1[pi], u1 = S1[pi ^ 1];
+            *reinterpret_cast<float4*>(&dst1[gi]) = make_float4(u0.x, u0.y, u1.x, u1.y);
+          }
+        }
+      } else {
+        for (int i = threadIdx.x; i < T; i += kThreads) {
+          const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
+          dst0[gi] = S0[tswz(i)];
+          if (NS == 2) dst1[gi] = S1[tswz(i)];
         }
       }
     }
     __syncthreads();
+    slot ^= 1;
   }
-
-  if (P.store) {
-    const int nv = T / EPC;
-#pragma unroll 4
-    for (int v = threadIdx.x; v < nv; v += kThreads) {
-      const int i = v * EPC;
-      const long long gi = soff + (i & cmask) + ((long long)(i >> c) << h0);
-      *reinterpret_cast<float4*>(&dst0[gi]) = *reinterpret_cast<const float4*>(&S0[swz(i)]);
-      if (NS == 2) *reinterpret_cast<float4*>(&dst1[gi]) = *reinterpret_cast<const float4*>(&S1[swz(i)]);
-    }
-  }
+  cp_async_wait_group<0>();
   if (NS == 2 && P.nslots > 0) {
+    __syncthreads();
     for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
       double v = 0;
       for (int w = 0; w < kWarps; ++w) v += sred[w * P.nslots + s];
@@ -752,6 +832,7 @@ __global__ void __launch_bounds__(kThreads) k_laminit(int n, int cb, const doubl
   __syncthreads();
   const long long off = ((long long)b << n) + base;
   const int CH = 1 << cb, ma = (1 << la) - 1;
+#pragma unroll 16
   for (int i = threadIdx.x; i < CH; i += blockDim.x) {
     const R o = (R)(tot - 2.0 * (Sa[i & ma] + Sb[i >> la]));
     const C x = psi[off + i];
@@ -1280,43 +1361,43 @@ cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi,
 }
 
 size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) {
-  size_t s = (size_t)ns * ((size_t)1 << P.t) * 2 * rsize;
+  size_t s = (size_t)2 * ns * ((size_t)1 << P.t) * 2 * rsize;
   s += (size_t)((P.ncoef + 1) & ~1) * rsize;
   s += (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double);
   return s;
 }
 
 template <class R, int NS, int RB>
-static cudaError_t launch_tile_rb(const TilePass& P, int batch, const void* coef, const void* s0,
-                                  void* d0, const void* s1, void* d1, double* part,
+static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const void* coef,
+                                  const void* s0, void* d0, const void* s1, void* d1, double* part,
                                   cudaStream_t st) {
   size_t smem = tile_smem_bytes(P, NS, sizeof(R));
   auto kern = k_tile<R, NS, RB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  long long grid = (long long)batch << (P.n - P.t);
+  long long grid = (long long)batch * cps;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const R*)coef, (const cx<R>*)s0, (cx<R>*)d0,
-                                               (const cx<R>*)s1, (cx<R>*)d1, part);
+                                               (const cx<R>*)s1, (cx<R>*)d1, part, cps);
   return cudaGetLastError();
 }
 
 template <class R>
-cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, const void* coef,
+cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, const void* coef,
                         const void* s0, void* d0, const void* s1, void* d1, double* part,
                         cudaStream_t st) {
   if (ns == 1) {
     switch (rb) {
-      case 1: return launch_tile_rb<R, 1, 1>(P, batch, coef, s0, d0, s1, d1, part, st);
-      case 2: return launch_tile_rb<R, 1, 2>(P, batch, coef, s0, d0, s1, d1, part, st);
-      case 3: return launch_tile_rb<R, 1, 3>(P, batch, coef, s0, d0, s1, d1, part, st);
-      case 4: return launch_tile_rb<R, 1, 4>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 1: return launch_tile_rb<R, 1, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 2: return launch_tile_rb<R, 1, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 3: return launch_tile_rb<R, 1, 3>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 4: return launch_tile_rb<R, 1, 4>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
     }
   } else {
     switch (rb) {
-      case 1: return launch_tile_rb<R, 2, 1>(P, batch, coef, s0, d0, s1, d1, part, st);
-      case 2: return launch_tile_rb<R, 2, 2>(P, batch, coef, s0, d0, s1, d1, part, st);
-      case 3: return launch_tile_rb<R, 2, 3>(P, batch, coef, s0, d0, s1, d1, part, st);
-      case 4: return launch_tile_rb<R, 2, 4>(P, batch, coef, s0, d0, s1, d1, part, st);
+      case 1: return launch_tile_rb<R, 2, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 2: return launch_tile_rb<R, 2, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 3: return launch_tile_rb<R, 2, 3>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 4: return launch_tile_rb<R, 2, 4>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
     }
   }
   return cudaErrorInvalidValue;
@@ -1425,6 +1506,8 @@ cudaError_t launch_expect(int n, int cb, int batch, const void* psi, double* par
     case 2: e = launch_expect_jb<R, 2>(n, cb, batch, psi, part, st); break;
     case 3: e = launch_expect_jb<R, 3>(n, cb, batch, psi, part, st); break;
     case 4: e = launch_expect_jb<R, 4>(n, cb, batch, psi, part, st); break;
+    case 5: e = launch_expect_jb<R, 5>(n, cb, batch, psi, part, st); break;
+    case 6: e = launch_expect_jb<R, 6>(n, cb, batch, psi, part, st); break;
   }
   if (e != cudaSuccess) return e;
   long long nblk = (long long)batch << (n - cb);
@@ -1485,8 +1568,9 @@ cudaError_t launch_smem(const SmemLayer* prog, int nl, int n, int batch, int bwd
   template cudaError_t launch_prodvec<R>(const ProdVecJob&, int, int, int, const double*,          \
                                          const double*, void*, cudaStream_t);                      \
   template cudaError_t launch_prodinit<R>(int, int, int, const void*, void*, cudaStream_t);        \
-  template cudaError_t launch_tile<R>(const TilePass&, int, int, int, const void*, const void*,    \
-                                      void*, const void*, void*, double*, cudaStream_t);           \
+  template cudaError_t launch_tile<R>(const TilePass&, int, int, int, int, const void*,           \
+                                      const void*, void*, const void*, void*, double*,             \
+                                      cudaStream_t);                                               \
   template cudaError_t launch_diag<R>(const DiagPass&, int, int, const void*, const void*, void*,  \
                                       const void*, void*, double*, cudaStream_t);                  \
   template cudaError_t launch_ring<R>(const RingPass&, int, int, const void*, void*, const void*,  \

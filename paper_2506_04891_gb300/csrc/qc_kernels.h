@@ -34,7 +34,7 @@ cudaError_t launch_prodvec(const ProdVecJob& P, int n, int batch, int n_in, cons
 template <class R>
 cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi, cudaStream_t st);
 template <class R>
-cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, const void* coef,
+cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, const void* coef,
                         const void* s0, void* d0, const void* s1, void* d1, double* part,
                         cudaStream_t st);
 template <class R>
