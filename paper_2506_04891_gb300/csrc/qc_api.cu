@@ -192,8 +192,10 @@ int tile_cps(int batch, int n, int t) {
   return (int)c;
 }
 int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
+// Register bits per round: the backward holds two states, so it takes one
+// bit fewer (every thread of a 2^11-amplitude tile then has work).
 int reg_bits(const qc_circuit* c, int ns) {
-  if (c->dtype == QC_C64) return 4;
+  (void)c;
   return ns == 2 ? 3 : 4;
 }
 
@@ -320,6 +322,24 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     P.ncoef = soff;
     P.nslots = slot;
     P.store = 1;
+    // deferred reduction when every gradient op is single-qubit and rounds fit
+    for (int r = 0; r < 4; ++r)
+      for (int i = 0; i < 4; ++i) P.rslot[r][i] = -1;
+    bool defer = P.nrounds <= 4 && slot > 0;
+    for (int k = 0; k < P.nops && defer; ++k) {
+      const TileOp& o = P.ops[k];
+      if (o.np == 0) continue;
+      if (o.is2q || o.np != 1) { defer = false; break; }
+      int r = 0;
+      while (r + 1 < P.nrounds && P.rop[r + 1] <= k) ++r;
+      const int i = o.l - P.rlo[r];
+      if (i < 0 || i >= 4) { defer = false; break; }
+      P.rslot[r][i] = o.slot;
+    }
+    P.defer = defer ? 1 : 0;
+    if (!defer)
+      for (int r = 0; r < 4; ++r)
+        for (int i = 0; i < 4; ++i) P.rslot[r][i] = -1;
     out.push_back(P);
     s = e;
     first = false;

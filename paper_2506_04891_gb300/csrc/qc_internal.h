@@ -76,6 +76,10 @@ struct TilePass {
   int nslots;                        // gradient slots (bwd)
   int store;                         // 0: gradient only, no store
   int ncoef;                         // R units of staged coefficients
+  // deferred gradient reduction (single-qubit ops only, <= 4 rounds): slot of
+  // the op on register bit i of round r, -1 if none
+  int defer;
+  int16_t rslot[4][4];
   TileOp ops[kMaxTileOps];
 };
 

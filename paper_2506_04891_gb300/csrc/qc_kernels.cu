@@ -11,6 +11,11 @@
 #include "qc_internal.h"
 #include "qc_kernels.h"
 
+// resident CTAs per SM the backward tile pass is compiled for
+#ifndef QC_BWD_MINB
+#define QC_BWD_MINB 3
+#endif
+
 namespace qc {
 
 template <class R> struct CT;
@@ -442,7 +447,7 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials into part[slot][block]).
 template <class R, int NS, int RB>
-__global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ TilePass P,
+__global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(const __grid_constant__ TilePass P,
                                                       const R* __restrict__ coef,
                                                       const cx<R>* src0, cx<R>* dst0,
                                                       const cx<R>* src1, cx<R>* dst1,
@@ -484,6 +489,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ Ti
     }
   };
 
+  float acct[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acct[r][i] = 0.f;
+
   long long f = r0;
   int slot = 0;
   if (f < tps) issue(f, 0);
@@ -497,6 +508,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ Ti
     C* S0 = buf + (long long)slot * NS * T;
     C* S1 = S0 + T;
 
+#pragma unroll 1
     for (int r = 0; r < P.nrounds; ++r) {
       const int lo = P.rlo[r];
       const int op0 = P.rop[r], op1 = P.rop[r + 1];
@@ -529,16 +541,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ Ti
         }
       }
       if (NS == 2) {
-        for (int k = op0; k < op1; ++k) {
-          const TileOp& o = P.ops[k];
-          const int i = o.l - lo;
-          for (int q = 0; q < o.np; ++q) {
-            R val = 0;
+        if (P.defer) {
+          // keep per-thread sums across tiles; reduced once after the last tile
 #pragma unroll
-            for (int s = 0; s < RB * 3; ++s)
-              if (s == i * 3 + q) val = acc[s];
-            double v = warp_sum((double)val);
-            if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
+          for (int rr = 0; rr < 4; ++rr)
+            if (rr == r) {
+#pragma unroll
+              for (int i = 0; i < (RB < 4 ? RB : 4); ++i) acct[rr][i] += acc[i * 3];
+            }
+        } else {
+          for (int k = op0; k < op1; ++k) {
+            const TileOp& o = P.ops[k];
+            const int i = o.l - lo;
+            for (int q = 0; q < o.np; ++q) {
+              R val = 0;
+#pragma unroll
+              for (int s = 0; s < RB * 3; ++s)
+                if (s == i * 3 + q) val = acc[s];
+              double v = warp_sum((double)val);
+              if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
+            }
           }
         }
       }
@@ -570,6 +592,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile(const __grid_constant__ Ti
     slot ^= 1;
   }
   cp_async_wait_group<0>();
+  if (NS == 2 && P.defer) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int sl = P.rslot[r][i];
+        if (sl >= 0) {
+          const double v = warp_sum((double)acct[r][i]);
+          if (lane == 0) sred[warp * P.nslots + sl] += v;
+        }
+      }
+  }
   if (NS == 2 && P.nslots > 0) {
     __syncthreads();
     for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
