@@ -13,7 +13,7 @@
 
 // resident CTAs per SM the backward tile pass is compiled for
 #ifndef QC_BWD_MINB
-#define QC_BWD_MINB 3
+#define QC_BWD_MINB 2
 #endif
 
 namespace qc {
@@ -489,11 +489,11 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(
     }
   };
 
-  float acct[4][4];
+  R acct[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acct[r][i] = 0.f;
+    for (int i = 0; i < 4; ++i) acct[r][i] = 0;
 
   long long f = r0;
   int slot = 0;
