@@ -322,6 +322,13 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     P.ncoef = soff;
     P.nslots = slot;
     P.store = 1;
+    P.kind = L.cls == LC_DENSE2 ? 2 : (L.real ? 1 : 0);
+    for (int r = 0; r < kMaxRounds; ++r)
+      for (int i = 0; i < 5; ++i) P.rbit[r][i] = -1;
+    for (int k = 0, r = 0; k < P.nops; ++k) {
+      while (r + 1 < P.nrounds && P.rop[r + 1] <= k) ++r;
+      P.rbit[r][P.ops[k].l - P.rlo[r]] = (int8_t)k;
+    }
     // deferred reduction when every gradient op is single-qubit and rounds fit
     for (int r = 0; r < 4; ++r)
       for (int i = 0; i < 4; ++i) P.rslot[r][i] = -1;

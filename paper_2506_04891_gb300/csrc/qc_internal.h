@@ -80,6 +80,9 @@ struct TilePass {
   // the op on register bit i of round r, -1 if none
   int defer;
   int16_t rslot[4][4];
+  // op on register bit i of round r (lower bit for two-qubit ops), -1 if none
+  int8_t rbit[kMaxRounds][5];
+  int kind;                          // 0: complex 1q, 1: real 1q, 2: two-qubit (uniform per pass)
   TileOp ops[kMaxTileOps];
 };
 

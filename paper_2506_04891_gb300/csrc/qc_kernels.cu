@@ -381,43 +381,22 @@ __device__ __forceinline__ void bw2(cx<R>* p, cx<R>* l, const R* m, int np, R* a
     }
 }
 
-template <class R, int NS, int RB>
-__device__ __forceinline__ void tile_dispatch(const TileOp& o, int i, cx<R>* v0, cx<R>* v1,
-                                              const R* mc, R* acc) {
+// Applies the round's op on register bit I (if any).  KIND is uniform over a
+// pass: 0 complex single-qubit, 1 real single-qubit, 2 two-qubit on (I, I+1).
+template <class R, int NS, int RB, int KIND, int I>
+__device__ __forceinline__ void tile_bit(const TilePass& P, int r, cx<R>* v0, cx<R>* v1,
+                                         const R* sco, R* acc) {
+  if (KIND == 2 && I + 1 >= RB) return;
+  const int k = P.rbit[r][I];
+  if (k < 0) return;
+  const TileOp& o = P.ops[k];
+  const R* mc = sco + o.soff;
   if (NS == 1) {
-    if (!o.is2q) {
-      switch (i) {
-        case 0: ap1<R, RB, 0>(v0, mc, o.real); break;
-        case 1: if (RB > 1) ap1<R, RB, (RB > 1 ? 1 : 0)>(v0, mc, o.real); break;
-        case 2: if (RB > 2) ap1<R, RB, (RB > 2 ? 2 : 0)>(v0, mc, o.real); break;
-        case 3: if (RB > 3) ap1<R, RB, (RB > 3 ? 3 : 0)>(v0, mc, o.real); break;
-        case 4: if (RB > 4) ap1<R, RB, (RB > 4 ? 4 : 0)>(v0, mc, o.real); break;
-      }
-    } else {
-      switch (i) {
-        case 0: if (RB > 1) ap2<R, RB, 0>(v0, mc); break;
-        case 1: if (RB > 2) ap2<R, RB, (RB > 2 ? 1 : 0)>(v0, mc); break;
-        case 2: if (RB > 3) ap2<R, RB, (RB > 3 ? 2 : 0)>(v0, mc); break;
-        case 3: if (RB > 4) ap2<R, RB, (RB > 4 ? 3 : 0)>(v0, mc); break;
-      }
-    }
+    if (KIND == 2) ap2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, mc);
+    else ap1<R, RB, I>(v0, mc, KIND == 1);
   } else {
-    if (!o.is2q) {
-      switch (i) {
-        case 0: bw1<R, RB, 0>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
-        case 1: if (RB > 1) bw1<R, RB, (RB > 1 ? 1 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
-        case 2: if (RB > 2) bw1<R, RB, (RB > 2 ? 2 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
-        case 3: if (RB > 3) bw1<R, RB, (RB > 3 ? 3 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
-        case 4: if (RB > 4) bw1<R, RB, (RB > 4 ? 4 : 0)>(v0, v1, mc, o.real, o.np, o.gk, acc); break;
-      }
-    } else {
-      switch (i) {
-        case 0: if (RB > 1) bw2<R, RB, 0>(v0, v1, mc, o.np, acc); break;
-        case 1: if (RB > 2) bw2<R, RB, (RB > 2 ? 1 : 0)>(v0, v1, mc, o.np, acc); break;
-        case 2: if (RB > 3) bw2<R, RB, (RB > 3 ? 2 : 0)>(v0, v1, mc, o.np, acc); break;
-        case 3: if (RB > 4) bw2<R, RB, (RB > 4 ? 3 : 0)>(v0, v1, mc, o.np, acc); break;
-      }
-    }
+    if (KIND == 2) bw2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, v1, mc, o.np, acc);
+    else bw1<R, RB, I>(v0, v1, mc, KIND == 1, o.np, o.gk, acc);
   }
 }
 
@@ -446,7 +425,7 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // shared-memory buffer while the current one is processed.
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials into part[slot][block]).
-template <class R, int NS, int RB>
+template <class R, int NS, int RB, int KIND>
 __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(const __grid_constant__ TilePass P,
                                                       const R* __restrict__ coef,
                                                       const cx<R>* src0, cx<R>* dst0,
@@ -515,29 +494,34 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(
       R acc[RB * 3];
 #pragma unroll
       for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
-      int off[1 << RB];
-      off[0] = 0;
+      // address of register element a = pb ^ (XOR of basis[j] over set bits j of a)
+      int basis[RB];
 #pragma unroll
-      for (int a = 1; a < (1 << RB); ++a) {
-        const int j = __ffs(a) - 1;
-        off[a] = off[a ^ (1 << j)] ^ tswz(1 << (lo + j));
-      }
+      for (int j = 0; j < RB; ++j) basis[j] = tswz(1 << (lo + j));
       for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
         const int pb = tswz((g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB)));
         C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
 #pragma unroll
         for (int a = 0; a < (1 << RB); ++a) {
-          v0[a] = S0[pb ^ off[a]];
-          if (NS == 2) v1[a] = S1[pb ^ off[a]];
+          int ad = pb;
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            if (a & (1 << j)) ad ^= basis[j];
+          v0[a] = S0[ad];
+          if (NS == 2) v1[a] = S1[ad];
         }
-        for (int k = op0; k < op1; ++k) {
-          const TileOp& o = P.ops[k];
-          tile_dispatch<R, NS, RB>(o, o.l - lo, v0, v1, sco + o.soff, acc);
-        }
+        tile_bit<R, NS, RB, KIND, 0>(P, r, v0, v1, sco, acc);
+        if (RB > 1) tile_bit<R, NS, RB, KIND, (RB > 1 ? 1 : 0)>(P, r, v0, v1, sco, acc);
+        if (RB > 2) tile_bit<R, NS, RB, KIND, (RB > 2 ? 2 : 0)>(P, r, v0, v1, sco, acc);
+        if (RB > 3) tile_bit<R, NS, RB, KIND, (RB > 3 ? 3 : 0)>(P, r, v0, v1, sco, acc);
 #pragma unroll
         for (int a = 0; a < (1 << RB); ++a) {
-          S0[pb ^ off[a]] = v0[a];
-          if (NS == 2) S1[pb ^ off[a]] = v1[a];
+          int ad = pb;
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            if (a & (1 << j)) ad ^= basis[j];
+          S0[ad] = v0[a];
+          if (NS == 2) S1[ad] = v1[a];
         }
       }
       if (NS == 2) {
@@ -1401,18 +1385,30 @@ size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) {
   return s;
 }
 
-template <class R, int NS, int RB>
-static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const void* coef,
-                                  const void* s0, void* d0, const void* s1, void* d1, double* part,
-                                  cudaStream_t st) {
+template <class R, int NS, int RB, int KIND>
+static cudaError_t launch_tile_k(const TilePass& P, int batch, int cps, const void* coef,
+                                 const void* s0, void* d0, const void* s1, void* d1, double* part,
+                                 cudaStream_t st) {
   size_t smem = tile_smem_bytes(P, NS, sizeof(R));
-  auto kern = k_tile<R, NS, RB>;
+  auto kern = k_tile<R, NS, RB, KIND>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   long long grid = (long long)batch * cps;
   kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const R*)coef, (const cx<R>*)s0, (cx<R>*)d0,
                                                (const cx<R>*)s1, (cx<R>*)d1, part, cps);
   return cudaGetLastError();
+}
+
+template <class R, int NS, int RB>
+static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const void* coef,
+                                  const void* s0, void* d0, const void* s1, void* d1, double* part,
+                                  cudaStream_t st) {
+  switch (P.kind) {
+    case 0: return launch_tile_k<R, NS, RB, 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+    case 1: return launch_tile_k<R, NS, RB, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+    case 2: return launch_tile_k<R, NS, RB, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <class R>
