@@ -7,6 +7,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "qc_gates.cuh"
 #include "qc_internal.h"
 #include "qc_kernels.h"
@@ -46,6 +48,25 @@ template <class R> __device__ __forceinline__ R im_cdot(cx<R> l, cx<R> v) {  // 
   return l.x * v.y - l.y * v.x;
 }
 template <class R> __device__ __forceinline__ cx<R> ldc(const R* p) { return mk<R>(p[0], p[1]); }
+
+// Real coefficient times complex value, packed over (re, im): one FMUL2 /
+// FFMA2 on sm_100+ for float, two scalar ops for double.
+template <class R>
+__device__ __forceinline__ cx<R> rmul(R a, cx<R> x) {
+  if constexpr (std::is_same<R, float>::value) return __fmul2_rn(make_float2(a, a), x);
+  else return mk<R>(a * x.x, a * x.y);
+}
+template <class R>
+__device__ __forceinline__ cx<R> rfma(R a, cx<R> x, cx<R> acc) {
+  if constexpr (std::is_same<R, float>::value) return __ffma2_rn(make_float2(a, a), x, acc);
+  else return mk<R>(fma(a, x.x, acc.x), fma(a, x.y, acc.y));
+}
+// componentwise l * v + acc (sum of the components = Re(conj(l) v) contributions)
+template <class R>
+__device__ __forceinline__ cx<R> pfma(cx<R> l, cx<R> v, cx<R> acc) {
+  if constexpr (std::is_same<R, float>::value) return __ffma2_rn(l, v, acc);
+  else return mk<R>(fma(l.x, v.x, acc.x), fma(l.y, v.y, acc.y));
+}
 
 // 16-byte asynchronous global -> shared copy (Ampere+ LDGSTS path)
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -226,8 +247,8 @@ __device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
     for (int a = 0; a < (1 << RB); ++a)
       if (!(a & (1 << I))) {
         C x0 = v[a], x1 = v[a | (1 << I)];
-        v[a] = mk<R>(fma(m00, x0.x, m01 * x1.x), fma(m00, x0.y, m01 * x1.y));
-        v[a | (1 << I)] = mk<R>(fma(m10, x0.x, m11 * x1.x), fma(m10, x0.y, m11 * x1.y));
+        v[a] = rfma<R>(m01, x1, rmul<R>(m00, x0));
+        v[a | (1 << I)] = rfma<R>(m11, x1, rmul<R>(m10, x0));
       }
   } else {
     const C m00 = ldc<R>(m), m01 = ldc<R>(m + 2), m10 = ldc<R>(m + 4), m11 = ldc<R>(m + 6);
@@ -249,22 +270,23 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
   if (real && gk == 2) {
     // RY: undo with M^T; 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
     const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
-    R g = 0;
+    C ga = mk<R>(0, 0), gb = mk<R>(0, 0);
 #pragma unroll
     for (int a = 0; a < (1 << RB); ++a)
       if (!(a & (1 << I))) {
         const int a1 = a | (1 << I);
         C x0 = p[a], x1 = p[a1];
-        C y0 = mk<R>(fma(m00, x0.x, m10 * x1.x), fma(m00, x0.y, m10 * x1.y));
-        C y1 = mk<R>(fma(m01, x0.x, m11 * x1.x), fma(m01, x0.y, m11 * x1.y));
+        C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
+        C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
         p[a] = y0; p[a1] = y1;
         C u0 = l[a], u1 = l[a1];
-        C w0 = mk<R>(fma(m00, u0.x, m10 * u1.x), fma(m00, u0.y, m10 * u1.y));
-        C w1 = mk<R>(fma(m01, u0.x, m11 * u1.x), fma(m01, u0.y, m11 * u1.y));
+        C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
+        C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
         l[a] = w0; l[a1] = w1;
-        g += re_cdot<R>(w1, y0) - re_cdot<R>(w0, y1);
+        ga = pfma<R>(w1, y0, ga);
+        gb = pfma<R>(w0, y1, gb);
       }
-    if (np) acc[I * 3] += g;
+    if (np) acc[I * 3] += (ga.x + ga.y) - (gb.x + gb.y);
     return;
   }
   if (real) {
@@ -277,12 +299,12 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
       if (!(a & (1 << I))) {
         const int a1 = a | (1 << I);
         C x0 = p[a], x1 = p[a1];
-        C y0 = mk<R>(fma(m00, x0.x, m10 * x1.x), fma(m00, x0.y, m10 * x1.y));
-        C y1 = mk<R>(fma(m01, x0.x, m11 * x1.x), fma(m01, x0.y, m11 * x1.y));
+        C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
+        C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
         p[a] = y0; p[a1] = y1;
         C u0 = l[a], u1 = l[a1];
-        C w0 = mk<R>(fma(m00, u0.x, m10 * u1.x), fma(m00, u0.y, m10 * u1.y));
-        C w1 = mk<R>(fma(m01, u0.x, m11 * u1.x), fma(m01, u0.y, m11 * u1.y));
+        C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
+        C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
         l[a] = w0; l[a1] = w1;
         if (np) {
           g += a00 * re_cdot<R>(w0, y0) + a01 * re_cdot<R>(w0, y1) + a10 * re_cdot<R>(w1, y0) +
