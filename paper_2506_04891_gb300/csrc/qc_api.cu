@@ -946,6 +946,14 @@ int layer_class(int kind) {
 
 }  // namespace
 
+namespace qc {
+void circuit_shape(const qc_circuit* c, int* n, int* dtype) {
+  *n = c->n;
+  *dtype = (int)c->dtype;
+}
+qc_status set_error(qc_status s, const char* msg) { return fail(s, msg); }
+}  // namespace qc
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

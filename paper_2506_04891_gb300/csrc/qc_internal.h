@@ -138,4 +138,9 @@ struct SmemLayer {
   double gscale;
 };
 
+// Shape of a circuit handle and the thread-local error message, for entry
+// points defined outside qc_api.cu.
+void circuit_shape(const qc_circuit* c, int* n, int* dtype);
+qc_status set_error(qc_status s, const char* msg);
+
 }  // namespace qc
