@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <map>
 #include <memory>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -100,6 +101,10 @@ struct Step {
   int s0 = B_NONE, d0 = B_NONE, s1 = B_NONE, d1 = B_NONE;
   long long part_off = 0;
   int layer = -1;
+  int post_layer = -1;  // PRODINIT: diagonal layer applied to the product state
+  long long post_coef = 0, post_bstride = 0;
+  int post_tb = 0, post_zmode = 0;
+  int laminit = 0;      // backward RING: lambda formed from psi (first backward step)
 };
 
 struct OutMap {
@@ -277,6 +282,11 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
         for (int k = 0; k < np; ++k) o.pidx.push_back(L.offset + 3 * i + k);
         ops.push_back(o);
       }
+    }
+    if (ops.empty()) {  // e.g. the unpaired top qubit of an odd brick
+      s = e;
+      first = false;
+      continue;
     }
     // rounds of RB register bits
     const int RB = std::min(reg_bits(c, ns), P.t);
@@ -470,10 +480,86 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
     off = align256(off + (size_t)p.nrows * 8);
     p.ws_fwd = p.ws_bwd = std::max<size_t>(off, 256);
   } else {
-    // ---------------- forward ----------------
     const int ck = c->opt.ckpt_every < 0 ? (p.S >= ((size_t)1 << 30) ? 4 : 0) : c->opt.ckpt_every;
+    const bool fuse = c->opt.fuse != 0;
+    auto is_tile = [&](int l) { return l >= 0 && l < L && (LI[l].cls == LC_ROT1 || LI[l].cls == LC_DENSE2); };
+    auto is_phase = [&](int l) { return l >= 0 && l < L && LI[l].cls == LC_DIAG; };
+    auto is_ring = [&](int l) { return l >= 0 && l < L && LI[l].cls == LC_RING; };
+    auto tile_steps = [&](const LayerInfo& Li, int ns, std::vector<std::vector<int>>& pslots) {
+      std::vector<Step> v;
+      for (auto& tp : plan_tile_layer(c, Li, ns, pslots)) {
+        Step st;
+        st.type = ST_TILE; st.ns = ns; st.tp = tp; st.rb = std::min(reg_bits(c, ns), tp.t);
+        st.cps = tile_cps(batch, n, tp.t);
+        v.push_back(st);
+      }
+      return v;
+    };
+    auto diag_step = [&](const LayerInfo& Li, int ns) {
+      Step st;
+      st.type = ST_DIAG; st.ns = ns;
+      memset(&st.dp, 0, sizeof(st.dp));
+      st.dp.n = n; st.dp.cb = std::min(n, ns == 2 ? 14 : 12); st.dp.zmode = Li.zmode;
+      st.dp.xcomp = Li.cls == LC_XCOMP; st.dp.has_phase = Li.has_phase; st.dp.tb = Li.tb;
+      st.dp.coef = Li.coef_off; st.dp.bstride = Li.coef_bstride; st.dp.nvals = n + 1;
+      return st;
+    };
+    auto ring_step = [&](int ns) {
+      Step st;
+      st.type = ST_RING; st.ns = ns;
+      memset(&st.rp, 0, sizeof(st.rp));
+      st.rp.n = n;
+      const size_t w = 2 * c->rsize;
+      st.rp.whole = ((size_t)1 << n) * w * ns <= 96 * 1024;
+      st.rp.t = std::min(tile_tmax(c, ns), n - 1);
+      return st;
+    };
+
+    // need[l]: some layer <= l has gradients
+    std::vector<int> need(L, 0);
+    for (int l = 0; l < L; ++l) need[l] = (l > 0 ? need[l - 1] : 0) || (LI[l].diff && LI[l].nparams > 0);
+
+    // ---------------- backward groups (reverse order) ----------------
+    struct BGroup {
+      int hi, lo;               // layers covered; the group's input is the state after `hi`
+      std::vector<Step> steps;
+      std::vector<std::vector<int>> pslots;
+      int layer;                // layer whose parameters the group differentiates
+    };
+    std::vector<BGroup> bgroups;
+    bool laminit_fused = false;
+    {
+      int i = L - 1;
+      while (i >= 0 && need[i]) {
+        BGroup g;
+        g.hi = i;
+        g.layer = i;
+        const LayerInfo& Li = LI[i];
+        if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
+          g.steps = tile_steps(Li, 2, g.pslots);
+          g.lo = i;
+          if (fuse && !g.steps.empty() && is_ring(i - 1) && need[i - 1]) {
+            g.steps.back().tp.scatter = 1;  // the last (top) pass holds bit n-1
+            g.lo = i - 1;
+          }
+        } else if (Li.cls == LC_RING) {
+          g.steps.push_back(ring_step(2));
+          g.lo = i;
+          if (fuse && bgroups.empty()) laminit_fused = true;
+        } else {
+          g.steps.push_back(diag_step(Li, 2));
+          g.lo = i;
+        }
+        i = g.lo - 1;
+        bgroups.push_back(std::move(g));
+      }
+    }
+    std::set<int> bstarts;
+    for (auto& g : bgroups) bstarts.insert(g.hi);
+
+    // ---------------- forward groups ----------------
     int lead = 0;
-    if (c->opt.fuse) {
+    if (fuse) {
       while (lead < L && lead < kMaxLeading) {
         const LayerInfo& Li = LI[lead];
         const bool single = Li.cls == LC_ROT1 || (Li.cls == LC_DIAG && Li.kind == QC_L_RZ) ||
@@ -489,169 +575,194 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       p.pv.source[l] = LI[l].source;
       p.pv.offset[l] = LI[l].offset;
     }
-    // checkpoint slots: state after layer l for (l + 1) % ck == 0, l < L-1, l >= lead-1
-    std::map<int, int> ck_slot;
-    if (ck > 0) {
-      for (int l = std::max(lead - 1, 0); l < L - 1; ++l)
-        if ((l + 1) % ck == 0) {
-          ck_slot[l] = (int)p.ckpt_after.size();
-          p.ckpt_after.push_back(l);
-        }
-    }
-    p.nckpt = (int)p.ckpt_after.size();
-    // symbolic buffers: A = 1, B = 2 (renamed at the end), CK = B_CKPT + slot
-    const int A = 1, Bb = 2;
-    auto other = [&](int x) { return x == A ? Bb : A; };
-    int cur;
+    struct FGroup {
+      int hi;
+      std::vector<Step> steps;
+    };
+    std::vector<FGroup> fgroups;
     {
-      Step s;
-      s.type = ST_PRODINIT;
-      s.cb = std::min(n, 12);
-      const int l0 = lead - 1;
-      s.d0 = (l0 >= 0 && ck_slot.count(l0)) ? B_CKPT + ck_slot[l0] : A;
-      s.layer = l0;
-      p.fwd.push_back(s);
-      cur = s.d0;
-    }
-    std::vector<std::vector<int>> dummy;
-    for (int l = lead; l < L; ++l) {
-      const LayerInfo& Li = LI[l];
-      std::vector<Step> passes;
-      if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
-        for (auto& tp : plan_tile_layer(c, Li, 1, dummy)) {
-          Step s;
-          s.type = ST_TILE; s.ns = 1; s.tp = tp; s.rb = std::min(reg_bits(c, 1), tp.t);
-          s.cps = tile_cps(batch, n, tp.t);
-          passes.push_back(s);
+      FGroup g;
+      Step st;
+      st.type = ST_PRODINIT;
+      st.cb = std::min(n, 12);
+      st.layer = lead - 1;
+      st.post_layer = -1;
+      int i = lead;
+      if (fuse && lead > 0 && is_phase(i)) {  // diagonal right after the product block
+        st.post_layer = i;
+        st.post_coef = LI[i].coef_off;
+        st.post_bstride = LI[i].coef_bstride;
+        st.post_tb = LI[i].tb;
+        st.post_zmode = LI[i].zmode;
+        ++i;
+      }
+      g.hi = i - 1;
+      g.steps.push_back(st);
+      fgroups.push_back(std::move(g));
+      int pend_ring = -1, pend_pre = -1;
+      while (i < L) {
+        const LayerInfo& Li = LI[i];
+        if (fuse && pend_ring < 0 && pend_pre < 0 && is_ring(i) &&
+            (is_tile(i + 1) || (is_phase(i + 1) && is_tile(i + 2)))) {
+          pend_ring = i++;
+          continue;
         }
-      } else if (Li.cls == LC_DIAG || Li.cls == LC_XCOMP) {
-        Step s;
-        s.type = ST_DIAG; s.ns = 1;
-        memset(&s.dp, 0, sizeof(s.dp));
-        s.dp.n = n; s.dp.cb = std::min(n, 12); s.dp.zmode = Li.zmode;
-        s.dp.xcomp = Li.cls == LC_XCOMP; s.dp.has_phase = Li.has_phase; s.dp.tb = Li.tb;
-        s.dp.coef = Li.coef_off; s.dp.bstride = Li.coef_bstride; s.dp.nvals = n + 1;
-        passes.push_back(s);
-      } else if (Li.cls == LC_RING) {
-        Step s;
-        s.type = ST_RING; s.ns = 1;
-        memset(&s.rp, 0, sizeof(s.rp));
-        s.rp.n = n;
-        const size_t w = 2 * c->rsize;
-        s.rp.whole = ((size_t)1 << n) * w <= 96 * 1024;
-        s.rp.t = std::min(tile_tmax(c, 1), n - 1);
-        passes.push_back(s);
+        if (fuse && pend_pre < 0 && is_phase(i) && is_tile(i + 1)) {
+          pend_pre = i++;
+          continue;
+        }
+        FGroup h;
+        std::vector<std::vector<int>> dummy;
+        std::vector<Step> tsteps;
+        if (is_tile(i)) tsteps = tile_steps(Li, 1, dummy);
+        if (is_tile(i) && tsteps.empty()) {
+          // a brick layer without pairs: nothing to apply; pending neighbours run on their own
+          for (int l : {pend_ring, pend_pre}) {
+            if (l < 0) continue;
+            FGroup q;
+            q.steps.push_back(LI[l].cls == LC_RING ? ring_step(1) : diag_step(LI[l], 1));
+            q.hi = l;
+            fgroups.push_back(std::move(q));
+          }
+          pend_ring = pend_pre = -1;
+          ++i;
+          continue;
+        }
+        if (is_tile(i)) {
+          h.steps = tsteps;
+          if (pend_ring >= 0) {  // top pass first: it gathers through the ring
+            std::rotate(h.steps.begin(), h.steps.end() - 1, h.steps.end());
+            h.steps.front().tp.gather = 1;
+          }
+          if (pend_pre >= 0) {
+            const LayerInfo& D = LI[pend_pre];
+            TilePass& tp = h.steps.front().tp;
+            tp.pre = 1; tp.pre_zmode = D.zmode; tp.pre_tb = D.tb;
+            tp.pre_coef = D.coef_off; tp.pre_bstride = D.coef_bstride;
+          }
+          int hi = i;
+          if (fuse && is_phase(i + 1)) {
+            const LayerInfo& D = LI[i + 1];
+            TilePass& tp = h.steps.back().tp;
+            tp.post = 1; tp.post_zmode = D.zmode; tp.post_tb = D.tb;
+            tp.post_coef = D.coef_off; tp.post_bstride = D.coef_bstride;
+            hi = i + 1;
+          }
+          pend_ring = pend_pre = -1;
+          h.hi = hi;
+          i = hi + 1;
+        } else {
+          if (Li.cls == LC_RING) h.steps.push_back(ring_step(1));
+          else h.steps.push_back(diag_step(Li, 1));
+          h.hi = i++;
+        }
+        fgroups.push_back(std::move(h));
       }
-      const bool to_ck = ck_slot.count(l) > 0;
-      for (size_t i = 0; i < passes.size(); ++i) {
-        Step& s = passes[i];
-        s.layer = l;
-        s.s0 = cur;
-        const bool last = i + 1 == passes.size();
-        const bool inplace_ok = s.type != ST_RING;
-        if (last && to_ck) s.d0 = B_CKPT + ck_slot[l];
-        else if (inplace_ok && (cur == A || cur == Bb)) s.d0 = cur;
-        else if (cur == A || cur == Bb) s.d0 = other(cur);
-        else s.d0 = A;
-        cur = s.d0;
-        p.fwd.push_back(s);
-      }
-    }
-    // rename so that the final state lands in psi_out
-    const int fin = cur;  // A or B (the last layer is never checkpointed)
-    for (auto& s : p.fwd) {
-      auto ren = [&](int& b) {
-        if (b == fin) b = B_PSIOUT;
-        else if (b == A || b == Bb) b = B_RUN0;
-      };
-      ren(s.s0);
-      ren(s.d0);
-    }
-    if (fin >= B_CKPT) {
-      // only when the circuit is the product init alone with a checkpoint: not produced
     }
 
-    // ---------------- backward ----------------
-    // need[l]: some layer <= l has gradients
-    std::vector<int> need(L, 0);
-    for (int l = 0; l < L; ++l) need[l] = (l > 0 ? need[l - 1] : 0) || (LI[l].diff && LI[l].nparams > 0);
+    // checkpoints: forward group ends that are also backward group inputs
+    std::map<int, int> ck_slot;
+    if (ck > 0) {
+      int last = -1;
+      for (auto& g : fgroups) {
+        const int l = g.hi;
+        if (l < 0 || l >= L - 1 || !bstarts.count(l)) continue;
+        if (l - last >= ck) {
+          ck_slot[l] = (int)p.ckpt_after.size();
+          p.ckpt_after.push_back(l);
+          last = l;
+        }
+      }
+    }
+    p.nckpt = (int)p.ckpt_after.size();
+
+    // forward buffers: symbolic A/B renamed at the end so the final state is psi_out
     {
-      Step s;
-      s.type = ST_LAMINIT;
-      s.cb = std::min(n, 12);
-      s.s0 = B_PSIOUT;
-      s.d1 = B_LAM0;
-      p.bwd.push_back(s);
+      const int A = 1, Bb = 2;
+      auto other = [&](int x) { return x == A ? Bb : A; };
+      int cur = -1;
+      for (auto& g : fgroups) {
+        const bool to_ck = ck_slot.count(g.hi) > 0;
+        for (size_t k = 0; k < g.steps.size(); ++k) {
+          Step& st = g.steps[k];
+          if (st.layer < 0 || st.type != ST_PRODINIT) st.layer = g.hi;
+          const bool last = k + 1 == g.steps.size();
+          if (st.type == ST_PRODINIT) {
+            st.d0 = to_ck ? B_CKPT + ck_slot[g.hi] : A;
+          } else {
+            st.s0 = cur;
+            const bool inplace_ok = st.type != ST_RING && !(st.type == ST_TILE && st.tp.gather);
+            if (last && to_ck) st.d0 = B_CKPT + ck_slot[g.hi];
+            else if (inplace_ok && (cur == A || cur == Bb)) st.d0 = cur;
+            else if (cur == A || cur == Bb) st.d0 = other(cur);
+            else st.d0 = A;
+          }
+          cur = st.d0;
+          p.fwd.push_back(st);
+        }
+      }
+      const int fin = cur;
+      for (auto& st : p.fwd) {
+        auto ren = [&](int& bb) {
+          if (bb == fin) bb = B_PSIOUT;
+          else if (bb == A || bb == Bb) bb = B_RUN0;
+        };
+        ren(st.s0);
+        ren(st.d0);
+      }
+    }
+
+    // backward buffers and gradient bookkeeping
+    if (!bgroups.empty() && !laminit_fused) {
+      Step st;
+      st.type = ST_LAMINIT;
+      st.cb = std::min(n, 12);
+      st.s0 = B_PSIOUT;
+      st.d1 = B_LAM0;
+      p.bwd.push_back(st);
     }
     int cp = B_PSIOUT, cl = B_LAM0;
     long long part_off = 0;
     auto isrun = [](int x) { return x == B_RUN0 || x == B_RUN1; };
     auto orun = [](int x) { return x == B_RUN0 ? B_RUN1 : B_RUN0; };
     auto olam = [](int x) { return x == B_LAM0 ? B_LAM1 : B_LAM0; };
-    for (int l = L - 1; l >= 0; --l) {
-      if (!need[l]) break;
-      const LayerInfo& Li = LI[l];
-      const int srcp = ck_slot.count(l) ? B_CKPT + ck_slot[l] : cp;
-      std::vector<Step> passes;
-      std::vector<std::vector<int>> pslots;  // (pass index, slot, pidx)
-      if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
-        for (auto& tp : plan_tile_layer(c, Li, 2, pslots)) {
-          Step s;
-          s.type = ST_TILE; s.ns = 2; s.tp = tp; s.rb = std::min(reg_bits(c, 2), tp.t);
-          s.cps = tile_cps(batch, n, tp.t);
-          passes.push_back(s);
-        }
-      } else if (Li.cls == LC_DIAG || Li.cls == LC_XCOMP) {
-        Step s;
-        s.type = ST_DIAG; s.ns = 2;
-        memset(&s.dp, 0, sizeof(s.dp));
-        s.dp.n = n; s.dp.cb = std::min(n, 14); s.dp.zmode = Li.zmode;
-        s.dp.xcomp = Li.cls == LC_XCOMP; s.dp.has_phase = Li.has_phase; s.dp.tb = Li.tb;
-        s.dp.coef = Li.coef_off; s.dp.bstride = Li.coef_bstride; s.dp.nvals = n + 1;
-        passes.push_back(s);
-      } else if (Li.cls == LC_RING) {
-        Step s;
-        s.type = ST_RING; s.ns = 2;
-        memset(&s.rp, 0, sizeof(s.rp));
-        s.rp.n = n;
-        const size_t w = 2 * c->rsize;
-        s.rp.whole = ((size_t)1 << n) * w * 2 <= 96 * 1024;
-        s.rp.t = std::min(tile_tmax(c, 2), n - 1);
-        passes.push_back(s);
-      }
-      int sp = srcp;
-      for (size_t i = 0; i < passes.size(); ++i) {
-        Step& s = passes[i];
-        s.layer = l;
-        s.s0 = sp;
-        s.s1 = cl;
-        const bool inplace_ok = s.type != ST_RING;
-        s.d0 = (inplace_ok && isrun(sp)) ? sp : (isrun(sp) ? orun(sp) : B_RUN0);
-        s.d1 = inplace_ok ? cl : olam(cl);
-        if (l == 0 && i + 1 == passes.size() && s.type == ST_TILE) s.tp.store = 0;
-        // gradient bookkeeping
-        if (s.type == ST_TILE && s.tp.nslots > 0) {
-          const long long nblk = (long long)batch * s.cps;
-          s.part_off = part_off;
+    for (size_t gi = 0; gi < bgroups.size(); ++gi) {
+      BGroup& g = bgroups[gi];
+      const LayerInfo& Li = LI[g.layer];
+      int sp = ck_slot.count(g.hi) ? B_CKPT + ck_slot[g.hi] : cp;
+      for (size_t k = 0; k < g.steps.size(); ++k) {
+        Step& st = g.steps[k];
+        st.layer = g.layer;
+        st.s0 = sp;
+        st.s1 = cl;
+        const bool lam_here = laminit_fused && gi == 0 && st.type == ST_RING;
+        st.laminit = lam_here ? 1 : 0;
+        const bool oop = st.type == ST_RING || (st.type == ST_TILE && st.tp.scatter);
+        st.d0 = (!oop && isrun(sp)) ? sp : (isrun(sp) ? orun(sp) : B_RUN0);
+        st.d1 = lam_here ? B_LAM0 : (!oop ? cl : olam(cl));
+        if (g.lo == 0 && k + 1 == g.steps.size() && st.type == ST_TILE) st.tp.store = 0;
+        if (st.type == ST_TILE && st.tp.nslots > 0) {
+          const long long nblk = (long long)batch * st.cps;
+          st.part_off = part_off;
           std::vector<OutMap> outs;
-          for (auto& e : pslots)
-            if (e[0] == (int)i) outs.push_back(OutMap{0, e[1], e[2], 1.0});
-          add_job(p, RK_DIRECT, Li.source, part_off, nblk, s.tp.nslots, s.cps, outs);
-          part_off += nblk * s.tp.nslots;
-        } else if (s.type == ST_DIAG && Li.diff && Li.nparams > 0) {
-          const long long nblk = diag_grid(s.dp, batch);
-          s.part_off = part_off;
+          for (auto& e : g.pslots)
+            if (e[0] == (int)k) outs.push_back(OutMap{0, e[1], e[2], 1.0});
+          add_job(p, RK_DIRECT, Li.source, part_off, nblk, st.tp.nslots, st.cps, outs);
+          part_off += nblk * st.tp.nslots;
+        } else if (st.type == ST_DIAG && Li.diff && Li.nparams > 0) {
+          const long long nblk = diag_grid(st.dp, batch);
+          st.part_off = part_off;
           std::vector<OutMap> outs;
           for (int j = 0; j < Li.nparams; ++j)
             outs.push_back(OutMap{0, diag_zbit(Li, n, j), Li.offset + j, Li.gscale});
           add_job(p, RK_MARGINAL, Li.source, part_off, nblk, n + 1, nblk / batch, outs);
           part_off += nblk * (n + 1);
-        } else if (s.type == ST_DIAG) {
-          s.part_off = -1;  // no gradient: marginals go to a scratch region
+        } else if (st.type == ST_DIAG) {
+          st.part_off = -1;  // no gradient: marginals go to a scratch region
         }
-        sp = s.d0;
-        cl = s.d1;
-        p.bwd.push_back(s);
+        sp = st.d0;
+        cl = st.d1;
+        p.bwd.push_back(st);
       }
       cp = sp;
     }
@@ -804,7 +915,12 @@ qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int 
       case ST_PRODINIT: {
         ProfScope ps(PC_PRODINIT, S, st, 2);
         e = launch_prodvec<R>(p.pv, c->n, batch, c->n_in, x, theta, ws + p.off_pv, st);
-        if (e == cudaSuccess) e = launch_prodinit<R>(c->n, s.cb, batch, ws + p.off_pv, buf(s.d0), st);
+        if (e == cudaSuccess) {
+          const bool post = s.post_layer >= 0;
+          e = launch_prodinit<R>(c->n, s.cb, batch, ws + p.off_pv, buf(s.d0),
+                                 post ? coef + s.post_coef * sizeof(R) : nullptr, s.post_bstride,
+                                 s.post_tb, s.post_zmode, st);
+        }
         break;
       }
       case ST_TILE: {
@@ -821,7 +937,8 @@ qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int 
       }
       case ST_RING: {
         ProfScope ps(s.ns == 2 ? PC_RING_B : PC_RING_F, passb, st);
-        e = launch_ring<R>(s.rp, s.ns, batch, buf(s.s0), buf(s.d0), buf(s.s1), buf(s.d1), st);
+        e = launch_ring<R>(s.rp, s.ns, batch, buf(s.s0), buf(s.d0), s.laminit ? nullptr : buf(s.s1),
+                           buf(s.d1), s.laminit ? gez : nullptr, st);
         break;
       }
       case ST_LAMINIT: {
@@ -1019,7 +1136,9 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
       case QC_L_MS_BRICK: L.nparams = 3 * L.ngates; break;
       default: L.nparams = 0;
     }
-    if (L.nparams == 0 && in.source != QC_SRC_NONE)
+    const bool never_param = in.kind == QC_L_CNOT_RING || in.kind == QC_L_X || in.kind == QC_L_SX ||
+                             in.kind == QC_L_ECR_BRICK;
+    if (never_param && in.source != QC_SRC_NONE)
       return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unparametrised kind needs source NONE");
     if (in.source != QC_SRC_NONE && in.offset < 0)
       return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": negative offset");

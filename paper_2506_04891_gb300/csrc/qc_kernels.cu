@@ -83,6 +83,47 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Ring = CNOT(q->q+1 mod n) for q = 0..n-1.  With bit p = n-1-q:
+//   forward  f(k):   bit p = parity(k >> p) for p <= n-2, bit n-1 = parity(k mod 2^(n-1))
+//   inverse  f^-1(k) = k ^ (k >> 1) ^ (k & 1 ? 3 << (n-2) : 0)
+__device__ __forceinline__ long long ring_finv(long long k, int n) {
+  return k ^ (k >> 1) ^ ((k & 1) ? (3LL << (n - 2)) : 0LL);
+}
+__device__ __forceinline__ int par64(long long v) { return __popcll((unsigned long long)v) & 1; }
+__device__ __forceinline__ long long ring_f(long long k, int n) {
+  // prefix parities from the top: s_p = parity(k >> p)
+  unsigned long long s = (unsigned long long)k;
+  s ^= s >> 1; s ^= s >> 2; s ^= s >> 4; s ^= s >> 8; s ^= s >> 16; s ^= s >> 32;
+  const long long low = (long long)(s & ((1ULL << (n - 1)) - 1));
+  const long long top = (long long)par64(k & ((1LL << (n - 1)) - 1));
+  return low | (top << (n - 1));
+}
+__device__ __forceinline__ int gray_inv(int x) {
+  x ^= x >> 1; x ^= x >> 2; x ^= x >> 4; x ^= x >> 8; x ^= x >> 16;
+  return x;
+}
+
+// compile-time z(j << 8) bits above bit 7 for the marginal accumulators
+template <int ZM>
+__device__ __forceinline__ constexpr int zj_bits(int j) {
+  return ZM == Z_RINGXOR ? ((j << 8) ^ (j << 7)) : (j << 8);
+}
+__device__ __forceinline__ long long ztrans(long long k, int n, int zm) {
+  if (zm == Z_RINGXOR) return k ^ ((k >> 1) | ((k & 1) << (n - 1)));
+  return k;
+}
+
+// phase(z) = T0[z0] T1[z1] T2[z2]
+template <class R>
+__device__ __forceinline__ cx<R> diag_phase(const R* tabs, int tb, long long z) {
+  const long long mask = (1LL << tb) - 1;
+  const long long T = 1LL << tb;
+  cx<R> a = ldc<R>(tabs + 2 * (z & mask));
+  cx<R> b = ldc<R>(tabs + 2 * (T + ((z >> tb) & mask)));
+  cx<R> c = ldc<R>(tabs + 2 * (2 * T + ((z >> (2 * tb)) & mask)));
+  return cmul<R>(cmul<R>(a, b), c);
+}
+
 // ---------------------------------------------------------------------------
 // Coefficients: gate matrices, generators, diagonal phase tables
 // ---------------------------------------------------------------------------
@@ -197,9 +238,14 @@ __global__ void k_prodvec(ProdVecJob P, int n, int batch, int n_in, const double
 }
 
 // psi[b][k] = prod_p v[b][p][bit_p(k)], one contiguous chunk of 2^cb per CTA.
+// With post_tabs != NULL the product state is multiplied by the diagonal
+// phase of the following diagonal layer (tables as in k_diag).
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* __restrict__ pv,
-                                                       cx<R>* __restrict__ psi) {
+                                                       cx<R>* __restrict__ psi,
+                                                       const R* __restrict__ post_tabs,
+                                                       long long post_bstride, int post_tb,
+                                                       int post_zmode) {
   using C = cx<R>;
   __shared__ C Ta[64], Tb[64];
   const int nch_bits = n - cb;
@@ -230,7 +276,14 @@ __global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* _
   __syncthreads();
   C* out = psi + ((long long)b << n) + base;
   const int CH = 1 << cb, ma = (1 << la) - 1;
-  for (int i = threadIdx.x; i < CH; i += blockDim.x) out[i] = cmul<R>(Tb[i >> la], Ta[i & ma]);
+  if (post_tabs) {
+    const R* tabs = post_tabs + (long long)b * post_bstride;
+    for (int i = threadIdx.x; i < CH; i += blockDim.x)
+      out[i] = cmul<R>(diag_phase<R>(tabs, post_tb, ztrans(base + i, n, post_zmode)),
+                       cmul<R>(Tb[i >> la], Ta[i & ma]));
+  } else {
+    for (int i = threadIdx.x; i < CH; i += blockDim.x) out[i] = cmul<R>(Tb[i >> la], Ta[i & ma]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -484,7 +537,8 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(
     const long long base = tile_base(f);
     C* d0 = buf + (long long)slot * NS * T;
     for (int i = threadIdx.x; i < T; i += kThreads) {
-      const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
+      long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
+      if (P.gather) gi = sb + ring_finv(gi - sb, n);
       cp_async_elem<sizeof(C)>(&d0[tswz(i)], &src0[gi]);
       if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + tswz(i)], &src1[gi]);
     }
@@ -508,6 +562,16 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(
     __syncthreads();
     C* S0 = buf + (long long)slot * NS * T;
     C* S1 = S0 + T;
+    if (NS == 1 && P.pre) {
+      const long long base = tile_base(f) - sb;
+      const R* tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
+      for (int i = threadIdx.x; i < T; i += kThreads) {
+        const long long k = base + (i & cmask) + ((long long)(i >> c) << h0);
+        const int pi = tswz(i);
+        S0[pi] = cmul<R>(diag_phase<R>(tabs, P.pre_tb, ztrans(k, n, P.pre_zmode)), S0[pi]);
+      }
+      __syncthreads();
+    }
 
 #pragma unroll 1
     for (int r = 0; r < P.nrounds; ++r) {
@@ -575,7 +639,18 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(
 
     if (P.store) {
       const long long base = tile_base(f);
-      if (sizeof(C) == 8) {
+      if (P.post || P.scatter) {
+        const R* tabs = coef + P.post_coef + (long long)b * P.post_bstride;
+        for (int i = threadIdx.x; i < T; i += kThreads) {
+          const long long kl = base - sb + (i & cmask) + ((long long)(i >> c) << h0);
+          const int pi = tswz(i);
+          C e = S0[pi];
+          if (NS == 1 && P.post) e = cmul<R>(diag_phase<R>(tabs, P.post_tb, ztrans(kl, n, P.post_zmode)), e);
+          const long long gd = sb + (P.scatter ? ring_finv(kl, n) : kl);
+          dst0[gd] = e;
+          if (NS == 2) dst1[gd] = S1[pi];
+        }
+      } else if (sizeof(C) == 8) {
         for (int i = 2 * threadIdx.x; i < T; i += 2 * kThreads) {
           const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
           const int pi = tswz(i);
@@ -656,27 +731,6 @@ __device__ __forceinline__ void marg_flush(const double* sred, int nvals, double
     s = warp_sum(s);
     if (lane == 0) part[(long long)v * nblk + blk] = s;
   }
-}
-
-// compile-time z(j << 8) bits above bit 7 for the marginal accumulators
-template <int ZM>
-__device__ __forceinline__ constexpr int zj_bits(int j) {
-  return ZM == Z_RINGXOR ? ((j << 8) ^ (j << 7)) : (j << 8);
-}
-__device__ __forceinline__ long long ztrans(long long k, int n, int zm) {
-  if (zm == Z_RINGXOR) return k ^ ((k >> 1) | ((k & 1) << (n - 1)));
-  return k;
-}
-
-// phase(z) = T0[z0] T1[z1] T2[z2]
-template <class R>
-__device__ __forceinline__ cx<R> diag_phase(const R* tabs, int tb, long long z) {
-  const long long mask = (1LL << tb) - 1;
-  const long long T = 1LL << tb;
-  cx<R> a = ldc<R>(tabs + 2 * (z & mask));
-  cx<R> b = ldc<R>(tabs + 2 * (T + ((z >> tb) & mask)));
-  cx<R> c = ldc<R>(tabs + 2 * (2 * T + ((z >> (2 * tb)) & mask)));
-  return cmul<R>(cmul<R>(a, b), c);
 }
 
 // ---------------------------------------------------------------------------
@@ -883,35 +937,81 @@ __global__ void __launch_bounds__(kThreads) k_laminit(int n, int cb, const doubl
 // ---------------------------------------------------------------------------
 // CNOT ring permutation (closed-form GF(2) index map)
 // ---------------------------------------------------------------------------
-// Ring = CNOT(q->q+1 mod n) for q = 0..n-1.  With bit p = n-1-q:
-//   forward  f(k):   bit p = parity(k >> p) for p <= n-2, bit n-1 = parity(k mod 2^(n-1))
-//   inverse  f^-1(k) = k ^ (k >> 1) ^ (k & 1 ? 3 << (n-2) : 0)
-__device__ __forceinline__ long long ring_finv(long long k, int n) {
-  return k ^ (k >> 1) ^ ((k & 1) ? (3LL << (n - 2)) : 0LL);
-}
-__device__ __forceinline__ int par64(long long v) { return __popcll((unsigned long long)v) & 1; }
-__device__ __forceinline__ long long ring_f(long long k, int n) {
-  // prefix parities from the top: s_p = parity(k >> p)
-  unsigned long long s = (unsigned long long)k;
-  s ^= s >> 1; s ^= s >> 2; s ^= s >> 4; s ^= s >> 8; s ^= s >> 16; s ^= s >> 32;
-  const long long low = (long long)(s & ((1ULL << (n - 1)) - 1));
-  const long long top = (long long)par64(k & ((1LL << (n - 1)) - 1));
-  return low | (top << (n - 1));
-}
-__device__ __forceinline__ int gray_inv(int x) {
-  x ^= x >> 1; x ^= x >> 2; x ^= x >> 4; x ^= x >> 8; x ^= x >> 16;
-  return x;
-}
-
 // NS = 1: out[k] = in[f^-1(k)] (forward).  NS = 2: new[y] = old[f(y)] for
 // psi and lambda (backward, the inverse permutation).
+// With gez != NULL (backward only) lambda is not read: lambda = O psi with
+// O = sum_q g[b][q] Z_q is formed from the loaded psi (the first backward step).
 template <class R, int NS>
 __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>* src0, cx<R>* dst0,
-                                                   const cx<R>* src1, cx<R>* dst1) {
+                                                   const cx<R>* src1, cx<R>* dst1,
+                                                   const double* __restrict__ gez) {
   using C = cx<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* S = reinterpret_cast<C*>(smraw);
   const int n = P.n;
+  if (NS == 2 && gez) {
+    __shared__ double Sg[kMaxQubits], Sa[64], Sb[64];
+    __shared__ double tot_hi[2];
+    const int b = P.whole ? (int)blockIdx.x : (int)(blockIdx.x >> (n - P.t));
+    const long long sb = (long long)b << n;
+    for (int q = threadIdx.x; q < n; q += kThreads) Sg[q] = gez[(long long)b * n + q];
+    __syncthreads();
+    if (P.whole) {
+      const int N = 1 << n;
+      for (int i = threadIdx.x; i < N; i += kThreads) S[i] = src0[sb + i];
+      __syncthreads();
+      for (int k = threadIdx.x; k < N; k += kThreads) {
+        const int y = ring_f(k, n);
+        double o = 0;
+        for (int q = 0; q < n; ++q) o += ((y >> (n - 1 - q)) & 1) ? -Sg[q] : Sg[q];
+        const C x = S[y];
+        dst0[sb + k] = x;
+        dst1[sb + k] = mk<R>((R)o * x.x, (R)o * x.y);
+      }
+      return;
+    }
+    const int t = P.t, H = 1 << (t - 1);
+    const long long f = blockIdx.x & ((1LL << (n - t)) - 1);
+    const long long tb = f << (t - 1);
+    const long long ib = tb ^ (tb >> 1);
+    const long long A = ib & ~(long long)(H - 1);
+    const long long Bk = A ^ (3LL << (n - 2));
+    const int il = (int)(ib & (H - 1));
+    const long long topbit = 1LL << (n - 1);
+    // o(k) = sum_q g_q - 2 sum_{bits p of k} g_{n-1-p}, split into the low 6 bits, the
+    // next bits of the half tile, the tile's fixed bits and the top bit
+    for (int e = threadIdx.x; e < 128; e += kThreads) {
+      double acc = 0;
+      const int lo = e < 64 ? 0 : 6, v = e & 63;
+      for (int i = 0; i < 6; ++i)
+        if (((v >> i) & 1) && lo + i < t - 1) acc += Sg[n - 1 - (lo + i)];
+      if (e < 64) Sa[v] = acc; else Sb[v] = acc;
+    }
+    if (threadIdx.x == 0) {
+      double tot = 0, hi = 0;
+      for (int q = 0; q < n; ++q) tot += Sg[q];
+      for (int p = t - 1; p < n - 1; ++p)
+        if ((tb >> p) & 1) hi += Sg[n - 1 - p];
+      tot_hi[0] = tot;
+      tot_hi[1] = hi;
+    }
+    for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
+      const int top = e >> (t - 1), jl = e & (H - 1);
+      S[e] = src0[sb + tb + jl + (top ? topbit : 0)];
+    }
+    __syncthreads();
+    const double tot = tot_hi[0], hi = tot_hi[1], g0 = Sg[0];
+    for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
+      const int u = e >> (t - 1), yl = e & (H - 1);
+      const int jl = gray_inv(yl ^ il);
+      const int top = u ^ (jl & 1);
+      const C x = S[top * H + jl];
+      const double o = tot - 2.0 * (Sa[jl & 63] + Sb[(jl >> 6) & 63] + hi + (top ? g0 : 0.0));
+      dst0[sb + (u ? Bk : A) + yl] = x;
+      dst1[sb + (u ? Bk : A) + yl] = mk<R>((R)o * x.x, (R)o * x.y);
+    }
+    return;
+  }
   if (P.whole) {
     const int N = 1 << n;
     const long long sb = (long long)blockIdx.x << n;
@@ -1394,9 +1494,13 @@ cudaError_t launch_prodvec(const ProdVecJob& P, int n, int batch, int n_in, cons
 }
 
 template <class R>
-cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi, cudaStream_t st) {
+cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi,
+                           const void* post_tabs, long long post_bstride, int post_tb,
+                           int post_zmode, cudaStream_t st) {
   long long grid = (long long)batch << (n - cb);
-  k_prodinit<R><<<(unsigned)grid, kThreads, 0, st>>>(n, cb, (const R*)pv, (cx<R>*)psi);
+  k_prodinit<R><<<(unsigned)grid, kThreads, 0, st>>>(n, cb, (const R*)pv, (cx<R>*)psi,
+                                                     (const R*)post_tabs, post_bstride, post_tb,
+                                                     post_zmode);
   return cudaGetLastError();
 }
 
@@ -1515,20 +1619,21 @@ size_t ring_smem_bytes(const RingPass& P, int rsize) {
 
 template <class R>
 cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, void* d0,
-                        const void* s1, void* d1, cudaStream_t st) {
+                        const void* s1, void* d1, const double* gez, cudaStream_t st) {
   size_t smem = ring_smem_bytes(P, sizeof(R));
   long long grid = P.whole ? batch : ((long long)batch << (P.n - P.t));
   if (ns == 1) {
     auto kern = k_ring<R, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const cx<R>*)s0, (cx<R>*)d0, nullptr, nullptr);
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const cx<R>*)s0, (cx<R>*)d0, nullptr, nullptr,
+                                                 nullptr);
   } else {
     auto kern = k_ring<R, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const cx<R>*)s0, (cx<R>*)d0, (const cx<R>*)s1,
-                                                 (cx<R>*)d1);
+                                                 (cx<R>*)d1, gez);
   }
   return cudaGetLastError();
 }
@@ -1619,14 +1724,15 @@ cudaError_t launch_smem(const SmemLayer* prog, int nl, int n, int batch, int bwd
                                       const double*, void*, cudaStream_t);                         \
   template cudaError_t launch_prodvec<R>(const ProdVecJob&, int, int, int, const double*,          \
                                          const double*, void*, cudaStream_t);                      \
-  template cudaError_t launch_prodinit<R>(int, int, int, const void*, void*, cudaStream_t);        \
+  template cudaError_t launch_prodinit<R>(int, int, int, const void*, void*, const void*,          \
+                                          long long, int, int, cudaStream_t);                      \
   template cudaError_t launch_tile<R>(const TilePass&, int, int, int, int, const void*,           \
                                       const void*, void*, const void*, void*, double*,             \
                                       cudaStream_t);                                               \
   template cudaError_t launch_diag<R>(const DiagPass&, int, int, const void*, const void*, void*,  \
                                       const void*, void*, double*, cudaStream_t);                  \
   template cudaError_t launch_ring<R>(const RingPass&, int, int, const void*, void*, const void*,  \
-                                      void*, cudaStream_t);                                        \
+                                      void*, const double*, cudaStream_t);                         \
   template cudaError_t launch_expect<R>(int, int, int, const void*, double*, double*,              \
                                         cudaStream_t);                                             \
   template cudaError_t launch_laminit<R>(int, int, int, const double*, const void*, void*,         \

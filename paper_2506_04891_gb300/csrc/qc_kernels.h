@@ -32,7 +32,9 @@ template <class R>
 cudaError_t launch_prodvec(const ProdVecJob& P, int n, int batch, int n_in, const double* x,
                            const double* theta, void* pv, cudaStream_t st);
 template <class R>
-cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi, cudaStream_t st);
+cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi,
+                           const void* post_tabs, long long post_bstride, int post_tb,
+                           int post_zmode, cudaStream_t st);
 template <class R>
 cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, const void* coef,
                         const void* s0, void* d0, const void* s1, void* d1, double* part,
@@ -42,7 +44,7 @@ cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, 
                         void* d0, const void* s1, void* d1, double* part, cudaStream_t st);
 template <class R>
 cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, void* d0,
-                        const void* s1, void* d1, cudaStream_t st);
+                        const void* s1, void* d1, const double* gez, cudaStream_t st);
 template <class R>
 cudaError_t launch_expect(int n, int cb, int batch, const void* psi, double* part, double* ez,
                           cudaStream_t st);

@@ -69,10 +69,18 @@ def test_layer_path_multi_tile(name, dtype, n):
     compare(dtype, n, CIRCUITS[name](n), 2, seed=2, path=2)
 
 
-@pytest.mark.parametrize("fuse,ckpt", [(0, 0), (1, 0), (0, 2), (1, 3)])
-def test_layer_path_fusion_and_checkpoints(fuse, ckpt):
+@pytest.mark.parametrize("name", sorted(CIRCUITS))
+@pytest.mark.parametrize("n", [2, 3])
+@pytest.mark.parametrize("path", [1, 2])
+def test_every_circuit_family_at_n2_n3(name, n, path):
+    compare("c128", n, CIRCUITS[name](n), 2, seed=12, path=path)
+
+
+@pytest.mark.parametrize("fuse,ckpt", [(0, 0), (1, 0), (0, 2), (1, 3), (1, 1)])
+@pytest.mark.parametrize("name", ["zz", "hea", "ibm"])
+def test_layer_path_fusion_and_checkpoints(fuse, ckpt, name):
     n = 14
-    layers = W.zz_circuit(n, 3)
+    layers = {"zz": W.zz_circuit(n, 3), "hea": W.hea_circuit(n, 3), "ibm": W.ibm_circuit(n, 3)}[name]
     compare("c64", n, layers, 2, seed=3, path=2, fuse=fuse, ckpt=ckpt)
 
 
