@@ -14,6 +14,7 @@
 //   small n       -> the whole circuit of a sample in one CTA's shared memory.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -167,9 +168,19 @@ struct qc_circuit {
 
 namespace {
 
+// Tuning knobs for benchmarks (environment, read once): QC_TMAX_FWD, QC_TMAX_BWD
+// (tile bits), QC_RB_FWD, QC_RB_BWD (register bits per round).  0 = default.
+int env_knob(const char* name) {
+  const char* v = getenv(name);
+  return v ? atoi(v) : 0;
+}
+
 // Largest tile (log2 amplitudes): two buffers of ns states must leave room
 // for two CTAs per SM.
 int tile_tmax(const qc_circuit* c, int ns) {
+  static const int kf = env_knob("QC_TMAX_FWD"), kb = env_knob("QC_TMAX_BWD");
+  if (ns == 1 && kf > 0) return kf;
+  if (ns == 2 && kb > 0) return kb;
   if (c->dtype == QC_C64) return ns == 2 ? 11 : 12;
   return ns == 2 ? 10 : 11;
 }
@@ -201,6 +212,9 @@ int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 // bit fewer (every thread of a 2^11-amplitude tile then has work).
 int reg_bits(const qc_circuit* c, int ns) {
   (void)c;
+  static const int kf = env_knob("QC_RB_FWD"), kb = env_knob("QC_RB_BWD");
+  if (ns == 1 && kf > 0) return kf;
+  if (ns == 2 && kb > 0) return kb;
   return ns == 2 ? 3 : 4;
 }
 

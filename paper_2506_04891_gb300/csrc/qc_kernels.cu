@@ -17,6 +17,9 @@
 #ifndef QC_BWD_MINB
 #define QC_BWD_MINB 2
 #endif
+#ifndef QC_FWD_MINB
+#define QC_FWD_MINB 2
+#endif
 
 namespace qc {
 
@@ -501,7 +504,7 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials into part[slot][block]).
 template <class R, int NS, int RB, int KIND>
-__global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : 2)) k_tile(const __grid_constant__ TilePass P,
+__global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB)) k_tile(const __grid_constant__ TilePass P,
                                                       const R* __restrict__ coef,
                                                       const cx<R>* src0, cx<R>* dst0,
                                                       const cx<R>* src1, cx<R>* dst1,
