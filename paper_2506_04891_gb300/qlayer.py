@@ -256,6 +256,11 @@ class Circuit:
     def describe(self, batch: int) -> str:
         return qc_describe_plan(self.handle, batch)
 
+    def uses_checkpoints(self, batch: int) -> bool:
+        import re
+        m = re.search(r"nckpt=(\d+)", self.describe(batch).splitlines()[0])
+        return bool(m and int(m.group(1)) > 0)
+
     def workspace(self, batch: int, device=None):
         import torch
         ws = self._ws.get(batch)
