@@ -24,7 +24,7 @@ class QLayerFunction(torch.autograd.Function):
         ctx.x_dtype = x.dtype
         ctx.t_dtype = theta.dtype
         ctx.save_for_backward(x, theta, psi)
-        return ez.to(x.dtype)
+        return ez.to(device=x.device, dtype=x.dtype)
 
     @staticmethod
     def backward(ctx, g: torch.Tensor):
@@ -35,8 +35,8 @@ class QLayerFunction(torch.autograd.Function):
                                "with re-anchoring checkpoints the backward must follow its forward "
                                "(or create the circuit with ckpt_every=0)")
         dth, dx = circ.backward(x, theta, psi, g.contiguous())
-        gx = dx.to(ctx.x_dtype) if ctx.needs_input_grad[1] and dx is not None else None
-        gt = dth.to(ctx.t_dtype) if ctx.needs_input_grad[2] else None
+        gx = dx.to(device=x.device, dtype=ctx.x_dtype) if ctx.needs_input_grad[1] and dx is not None else None
+        gt = dth.to(device=theta.device, dtype=ctx.t_dtype) if ctx.needs_input_grad[2] else None
         return None, gx, gt
 
 
@@ -44,13 +44,13 @@ class QuantumLayer(torch.nn.Module):
     """<Z_q> of a layered circuit as a differentiable layer: forward(x) -> [B, n]."""
 
     def __init__(self, n: int, layers, dtype: str = "c64", theta=None, ckpt_every: int = -1,
-                 seed: int = 0):
+                 seed: int = 0, device: str = "cuda"):
         super().__init__()
         self.circuit = Q.Circuit(n, layers, dtype=dtype, ckpt_every=ckpt_every)
         if theta is None:
             gen = torch.Generator().manual_seed(seed)
             theta = 2 * torch.pi * torch.rand(self.circuit.n_theta, generator=gen, dtype=torch.float64)
-        self.theta = torch.nn.Parameter(torch.as_tensor(theta, dtype=torch.float64).clone())
+        self.theta = torch.nn.Parameter(torch.as_tensor(theta, dtype=torch.float64).clone().to(device))
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         return QLayerFunction.apply(self.circuit, x, self.theta)

@@ -74,8 +74,8 @@ class BudgetCheckingScheduler(S.Scheduler):
 def test_mixed_results_equal_direct_computation(slots):
     ex = FakeExecutor(polls=2)
     reqs = _reqs()
-    sch = BudgetCheckingScheduler(ex.footprint(9, 9), slots, ex.footprint)
-    arrivals = list(np.linspace(0.0, 0.002, len(reqs)))
+    sch = BudgetCheckingScheduler(ex.footprint(9, 24), slots, ex.footprint)
+    arrivals = [0.0] * (len(reqs) // 2) + list(np.linspace(0.0, 0.002, len(reqs) - len(reqs) // 2))
     results, stats = S.Server(ex, sch).run(reqs, arrivals)
     assert len(results) == len(reqs)
     for r in reqs:

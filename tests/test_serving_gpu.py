@@ -13,7 +13,8 @@ def test_mixed_equals_alone_and_oracle():
     from oracle import qsim_oracle as O
     ex = S.GpuExecutor(slots=4)
     reqs = S.make_requests(24, seed=5, n_range=(8, 14), b_range=(1, 48))
-    budget = ex.footprint(14, 20)  # the largest requests split into chunks
+    big = max(reqs, key=lambda r: (r.batch << r.n))
+    budget = ex.footprint(big.n, max(1, big.batch // 3))  # the largest request splits into chunks
     mixed, stats = S.Server(ex, S.Scheduler(budget, 4, ex.footprint)).run(
         reqs, S.poisson_arrivals(len(reqs), 400.0, seed=5))
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
