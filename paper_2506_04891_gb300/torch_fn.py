@@ -44,9 +44,9 @@ class QuantumLayer(torch.nn.Module):
     """<Z_q> of a layered circuit as a differentiable layer: forward(x) -> [B, n]."""
 
     def __init__(self, n: int, layers, dtype: str = "c64", theta=None, ckpt_every: int = -1,
-                 seed: int = 0, device: str = "cuda"):
+                 seed: int = 0, device: str = "cuda", path: int = 0):
         super().__init__()
-        self.circuit = Q.Circuit(n, layers, dtype=dtype, ckpt_every=ckpt_every)
+        self.circuit = Q.Circuit(n, layers, dtype=dtype, ckpt_every=ckpt_every, path=path)
         if theta is None:
             gen = torch.Generator().manual_seed(seed)
             theta = 2 * torch.pi * torch.rand(self.circuit.n_theta, generator=gen, dtype=torch.float64)

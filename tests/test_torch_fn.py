@@ -43,8 +43,9 @@ def test_training_step_and_checkpoint_guard():
     opt.step()
     assert not torch.equal(before, layer.theta.detach())
     # with checkpoints, a second forward before the first backward is refused
-    ck = QuantumLayer(12, W.zz_circuit(12, 3), dtype="c64", ckpt_every=2, seed=4)
-    xa = torch.rand((2, 12), dtype=torch.float64, device="cuda")
+    ck = QuantumLayer(14, W.zz_circuit(14, 3), dtype="c64", ckpt_every=2, seed=4, path=2)
+    assert ck.circuit.uses_checkpoints(2)
+    xa = torch.rand((2, 14), dtype=torch.float64, device="cuda")
     la = ck(xa).sum()
     lb = ck(xa * 0.5).sum()
     with pytest.raises(RuntimeError):
