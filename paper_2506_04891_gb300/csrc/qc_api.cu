@@ -229,9 +229,13 @@ struct PassOpInfo {
   int pidx;  // absolute parameter index of the op's first parameter (or -1)
 };
 
-// Builds the tile passes of a ROT1 or DENSE2 layer.
+// Builds the tile passes of a ROT1 or DENSE2 layer.  pidx_per_slot gets one
+// entry {pass, slot, parameter index, companion} per gradient slot.  `comp`
+// (backward, ROT1 only): the preceding RX / RY layer, whose gradients the ops
+// also produce (companion slots follow the pass's own slots).
 std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, int ns,
-                                      std::vector<std::vector<int>>& pidx_per_slot) {
+                                      std::vector<std::vector<int>>& pidx_per_slot,
+                                      const LayerInfo* comp = nullptr) {
   const int n = c->n;
   const int tmax = tile_tmax(c, ns);
   const int cbits = contig_bits(c);
@@ -261,7 +265,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
       P.t = P.c + (e - s);
     }
     auto local = [&](int p) { return first ? p : P.c + (p - s); };
-    struct OpTmp { TileOp op; std::vector<int> pidx; };
+    struct OpTmp { TileOp op; std::vector<int> pidx; int cpidx; };
     std::vector<OpTmp> ops;
     if (L.cls == LC_ROT1) {
       for (int p = s; p < e; ++p) {
@@ -277,6 +281,11 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
         o.op.bstride = L.coef_bstride;
         o.op.nco = ns == 2 ? kRec1q : 8;
         if (o.op.np) o.pidx.push_back(L.offset + q);
+        o.cpidx = -1;
+        if (ns == 2 && comp) {
+          o.op.ck = (int8_t)(comp->kind == QC_L_RX ? 1 : 2);
+          o.cpidx = comp->offset + q;
+        }
         ops.push_back(o);
       }
     } else {
@@ -286,6 +295,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
         if (plo < s || phi >= e) continue;
         OpTmp o;
         memset(&o.op, 0, sizeof(o.op));
+        o.cpidx = -1;
         o.op.l = (int16_t)local(plo);
         o.op.is2q = 1;
         const int np = (ns == 2 && L.diff && L.kind == QC_L_MS_BRICK) ? 3 : 0;
@@ -308,6 +318,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     int nass = 0, nr = 0;
     std::vector<TileOp> ordered;
     std::vector<std::vector<int>> ordered_pidx;
+    std::vector<int> ordered_cpidx;
     P.rop[0] = 0;
     while (nass < (int)ops.size()) {
       int lo = 1 << 30;
@@ -325,6 +336,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
           ++got;
           ordered.push_back(ops[k].op);
           ordered_pidx.push_back(ops[k].pidx);
+          ordered_cpidx.push_back(ops[k].cpidx);
         }
       }
       if (!got || nr >= kMaxRounds) break;  // cannot happen for valid geometry
@@ -340,8 +352,16 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
       P.ops[k].soff = soff;
       soff += P.ops[k].nco;
       P.ops[k].slot = (int16_t)slot;
-      for (int q = 0; q < P.ops[k].np; ++q) pidx_per_slot.push_back({(int)out.size(), slot + q, ordered_pidx[k][q]});
+      P.ops[k].cslot = -1;
+      for (int q = 0; q < P.ops[k].np; ++q) pidx_per_slot.push_back({(int)out.size(), slot + q, ordered_pidx[k][q], 0});
       slot += P.ops[k].np;
+    }
+    for (int k = 0; k < P.nops; ++k) {
+      if (!P.ops[k].ck) continue;
+      P.ops[k].cslot = (int16_t)slot;
+      pidx_per_slot.push_back({(int)out.size(), slot, ordered_cpidx[k], 1});
+      ++slot;
+      ++P.ncomp;
     }
     P.ncoef = soff;
     P.nslots = slot;
@@ -355,22 +375,23 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     }
     // deferred reduction when every gradient op is single-qubit and rounds fit
     for (int r = 0; r < 4; ++r)
-      for (int i = 0; i < 4; ++i) P.rslot[r][i] = -1;
+      for (int i = 0; i < 4; ++i) P.rslot[r][i] = P.rcslot[r][i] = -1;
     bool defer = P.nrounds <= 4 && slot > 0;
     for (int k = 0; k < P.nops && defer; ++k) {
       const TileOp& o = P.ops[k];
-      if (o.np == 0) continue;
-      if (o.is2q || o.np != 1) { defer = false; break; }
+      if (o.np == 0 && !o.ck) continue;
+      if (o.is2q || o.np > 1) { defer = false; break; }
       int r = 0;
       while (r + 1 < P.nrounds && P.rop[r + 1] <= k) ++r;
       const int i = o.l - P.rlo[r];
       if (i < 0 || i >= 4) { defer = false; break; }
-      P.rslot[r][i] = o.slot;
+      if (o.np) P.rslot[r][i] = o.slot;
+      if (o.ck) P.rcslot[r][i] = o.cslot;
     }
     P.defer = defer ? 1 : 0;
     if (!defer)
       for (int r = 0; r < 4; ++r)
-        for (int i = 0; i < 4; ++i) P.rslot[r][i] = -1;
+        for (int i = 0; i < 4; ++i) P.rslot[r][i] = P.rcslot[r][i] = -1;
     out.push_back(P);
     s = e;
     first = false;
@@ -499,9 +520,10 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
     auto is_tile = [&](int l) { return l >= 0 && l < L && (LI[l].cls == LC_ROT1 || LI[l].cls == LC_DENSE2); };
     auto is_phase = [&](int l) { return l >= 0 && l < L && LI[l].cls == LC_DIAG; };
     auto is_ring = [&](int l) { return l >= 0 && l < L && LI[l].cls == LC_RING; };
-    auto tile_steps = [&](const LayerInfo& Li, int ns, std::vector<std::vector<int>>& pslots) {
+    auto tile_steps = [&](const LayerInfo& Li, int ns, std::vector<std::vector<int>>& pslots,
+                          const LayerInfo* comp = nullptr) {
       std::vector<Step> v;
-      for (auto& tp : plan_tile_layer(c, Li, ns, pslots)) {
+      for (auto& tp : plan_tile_layer(c, Li, ns, pslots, comp)) {
         Step st;
         st.type = ST_TILE; st.ns = ns; st.tp = tp; st.rb = std::min(reg_bits(c, ns), tp.t);
         st.cps = tile_cps(batch, n, tp.t);
@@ -539,6 +561,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       std::vector<Step> steps;
       std::vector<std::vector<int>> pslots;
       int layer;                // layer whose parameters the group differentiates
+      int comp = -1;            // layer whose gradients ride along as companions
     };
     std::vector<BGroup> bgroups;
     bool laminit_fused = false;
@@ -549,7 +572,16 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         g.hi = i;
         g.layer = i;
         const LayerInfo& Li = LI[i];
-        if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
+        // a leading RX / RY layer right before a single-qubit layer: its
+        // gradients come from this layer's passes and it is never undone
+        const bool fold = fuse && Li.cls == LC_ROT1 && i >= 1 && LI[i - 1].cls == LC_ROT1 &&
+                          (LI[i - 1].kind == QC_L_RX || LI[i - 1].kind == QC_L_RY) &&
+                          LI[i - 1].diff && LI[i - 1].nparams > 0 && (i == 1 || !need[i - 2]);
+        if (fold) {
+          g.comp = i - 1;
+          g.steps = tile_steps(Li, 2, g.pslots, &LI[i - 1]);
+          g.lo = i - 1;
+        } else if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
           g.steps = tile_steps(Li, 2, g.pslots);
           g.lo = i;
           if (fuse && !g.steps.empty() && is_ring(i - 1) && need[i - 1]) {
@@ -758,10 +790,19 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         if (st.type == ST_TILE && st.tp.nslots > 0) {
           const long long nblk = (long long)batch * st.cps;
           st.part_off = part_off;
-          std::vector<OutMap> outs;
+          std::vector<OutMap> outs, couts;
+          int nown = 0;
           for (auto& e : g.pslots)
-            if (e[0] == (int)k) outs.push_back(OutMap{0, e[1], e[2], 1.0});
-          add_job(p, RK_DIRECT, Li.source, part_off, nblk, st.tp.nslots, st.cps, outs);
+            if (e[0] == (int)k && !e[3]) ++nown;
+          for (auto& e : g.pslots) {
+            if (e[0] != (int)k) continue;
+            if (e[3]) couts.push_back(OutMap{0, e[1] - nown, e[2], 1.0});
+            else outs.push_back(OutMap{0, e[1], e[2], 1.0});
+          }
+          if (nown > 0) add_job(p, RK_DIRECT, Li.source, part_off, nblk, nown, st.cps, outs);
+          if (!couts.empty())
+            add_job(p, RK_DIRECT, LI[g.comp].source, part_off + nblk * nown, nblk,
+                    st.tp.nslots - nown, st.cps, couts);
           part_off += nblk * st.tp.nslots;
         } else if (st.type == ST_DIAG && Li.diff && Li.nparams > 0) {
           const long long nblk = diag_grid(st.dp, batch);
@@ -1384,7 +1425,8 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
                  st.tp.store, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {
-          snprintf(line, sizeof line, " [l=%d%s np=%d]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "", st.tp.ops[k].np);
+          snprintf(line, sizeof line, " [l=%d%s np=%d%s]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "",
+                   st.tp.ops[k].np, st.tp.ops[k].ck ? (st.tp.ops[k].ck == 1 ? " +X" : " +Y") : "");
           o += line;
         }
         o += "\n";

@@ -55,9 +55,13 @@ struct TileOp {
   int8_t is2q;
   int8_t real;      // 1q with a real matrix
   int8_t gk;        // 1q generator: 0 generic A, 1 A = -i/2 X (RX), 2 A = -i/2 Y (RY)
-  int8_t pad0;
+  int8_t ck;        // companion generator (1q): 0 none, 1 X, 2 Y -- the gradient of the
+                    // preceding RX / RY layer's gate on the same qubit, taken on the
+                    // states between the two layers
   int16_t np;       // gradient parameters produced (0, 1 or 3)
   int16_t slot;     // first gradient slot in the pass's partial vector
+  int16_t cslot;    // companion gradient slot (ck != 0)
+  int16_t pad1;
   int32_t soff;     // offset of the op's coefficients in the staged smem block (R units)
   int32_t nco;      // number of R to stage
   long long coef;   // coefficient offset (R units) for sample 0
@@ -74,12 +78,16 @@ struct TilePass {
   int16_t rop[kMaxRounds + 1];       // ops of round r: [rop[r], rop[r+1])
   int nops;
   int nslots;                        // gradient slots (bwd)
+  int ncomp;                         // companion slots: the last ncomp of the nslots
   int store;                         // 0: gradient only, no store
   int ncoef;                         // R units of staged coefficients
   // deferred gradient reduction (single-qubit ops only, <= 4 rounds): slot of
-  // the op on register bit i of round r, -1 if none
+  // the op on register bit i of round r and of its companion, -1 if none.
+  // Per-thread sums stay in registers (own slots) and in shared memory
+  // (companions, [ncomp][kThreads] R) until the CTA's last tile.
   int defer;
   int16_t rslot[4][4];
+  int16_t rcslot[4][4];
   // op on register bit i of round r (lower bit for two-qubit ops), -1 if none
   int8_t rbit[kMaxRounds][5];
   int kind;                          // 0: complex 1q, 1: real 1q, 2: two-qubit (uniform per pass)

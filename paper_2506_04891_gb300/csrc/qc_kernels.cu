@@ -318,30 +318,66 @@ __device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
   }
 }
 
+// 2 Re <l|(-i/2 G)|p> on one amplitude pair, G = X (ck 1) or Y (ck 2):
+// Im(l0* p1 + l1* p0) and Re(l1* p0) - Re(l0* p1).
+template <class R>
+__device__ __forceinline__ R pauli_grad(int ck, cx<R> w0, cx<R> w1, cx<R> y0, cx<R> y1) {
+  if (ck == 1) return im_cdot<R>(w0, y1) + im_cdot<R>(w1, y0);
+  return re_cdot<R>(w1, y0) - re_cdot<R>(w0, y1);
+}
+
 // backward single-qubit op: undo M on psi and lambda, then accumulate
-// 2 Re <lambda| A |psi> on the gate's input side.
+// 2 Re <lambda| A |psi> on the gate's input side into acc[3 I].  With a
+// companion generator ck, also the gradient of the preceding layer's RX / RY
+// gate on the same qubit into acc[3 I + 1]: its generator commutes with that
+// gate, so the pair just undone (that layer's output side) gives it.
 template <class R, int RB, int I>
-__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, R* acc) {
+__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, int ck,
+                                    R* acc) {
   using C = cx<R>;
   if (real && gk == 2) {
     // RY: undo with M^T; 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
     const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
     C ga = mk<R>(0, 0), gb = mk<R>(0, 0);
+    if (ck == 1) {
+      // companion RX: Im(l0* p1 + l1* p0), packed as l * swap(p)
+      C hc = mk<R>(0, 0);
 #pragma unroll
-    for (int a = 0; a < (1 << RB); ++a)
-      if (!(a & (1 << I))) {
-        const int a1 = a | (1 << I);
-        C x0 = p[a], x1 = p[a1];
-        C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
-        C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
-        p[a] = y0; p[a1] = y1;
-        C u0 = l[a], u1 = l[a1];
-        C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
-        C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
-        l[a] = w0; l[a1] = w1;
-        ga = pfma<R>(w1, y0, ga);
-        gb = pfma<R>(w0, y1, gb);
-      }
+      for (int a = 0; a < (1 << RB); ++a)
+        if (!(a & (1 << I))) {
+          const int a1 = a | (1 << I);
+          C x0 = p[a], x1 = p[a1];
+          C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
+          C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
+          p[a] = y0; p[a1] = y1;
+          C u0 = l[a], u1 = l[a1];
+          C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
+          C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
+          l[a] = w0; l[a1] = w1;
+          ga = pfma<R>(w1, y0, ga);
+          gb = pfma<R>(w0, y1, gb);
+          hc = pfma<R>(w0, mk<R>(y1.y, y1.x), hc);
+          hc = pfma<R>(w1, mk<R>(y0.y, y0.x), hc);
+        }
+      acc[I * 3 + 1] += hc.x - hc.y;
+    } else {
+#pragma unroll
+      for (int a = 0; a < (1 << RB); ++a)
+        if (!(a & (1 << I))) {
+          const int a1 = a | (1 << I);
+          C x0 = p[a], x1 = p[a1];
+          C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
+          C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
+          p[a] = y0; p[a1] = y1;
+          C u0 = l[a], u1 = l[a1];
+          C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
+          C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
+          l[a] = w0; l[a1] = w1;
+          ga = pfma<R>(w1, y0, ga);
+          gb = pfma<R>(w0, y1, gb);
+          if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
+        }
+    }
     if (np) acc[I * 3] += (ga.x + ga.y) - (gb.x + gb.y);
     return;
   }
@@ -366,6 +402,7 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
           g += a00 * re_cdot<R>(w0, y0) + a01 * re_cdot<R>(w0, y1) + a10 * re_cdot<R>(w1, y0) +
                a11 * re_cdot<R>(w1, y1);
         }
+        if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
       }
     if (np) acc[I * 3] += 2 * g;
   } else {
@@ -395,6 +432,7 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
             g += 2 * (re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1));
           }
         }
+        if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
       }
     if (np) acc[I * 3] += g;
   }
@@ -474,7 +512,7 @@ __device__ __forceinline__ void tile_bit(const TilePass& P, int r, cx<R>* v0, cx
     else ap1<R, RB, I>(v0, mc, KIND == 1);
   } else {
     if (KIND == 2) bw2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, v1, mc, o.np, acc);
-    else bw1<R, RB, I>(v0, v1, mc, KIND == 1, o.np, o.gk, acc);
+    else bw1<R, RB, I>(v0, v1, mc, KIND == 1, o.np, o.gk, o.ck, acc);
   }
 }
 
@@ -516,6 +554,7 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
   C* buf = reinterpret_cast<C*>(smraw);  // [2][NS][T]
   R* sco = reinterpret_cast<R*>(buf + 2 * NS * T);
   double* sred = reinterpret_cast<double*>(sco + ((P.ncoef + 1) & ~1));  // [kWarps][nslots]
+  R* sdef = reinterpret_cast<R*>(sred + kWarps * (P.nslots > 0 ? P.nslots : 1));  // [ncomp][kThreads]
 
   const long long tps = 1LL << (n - t);
   const int b = blockIdx.x / cps;
@@ -530,8 +569,17 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
     const R* s = coef + o.coef + (long long)b * o.bstride;
     for (int i = threadIdx.x; i < o.nco; i += kThreads) sco[o.soff + i] = s[i];
   }
-  if (NS == 2)
+  if (NS == 2) {
     for (int i = threadIdx.x; i < kWarps * P.nslots; i += kThreads) sred[i] = 0;
+    if (P.defer)
+      for (int s = 0; s < P.ncomp; ++s) sdef[s * kThreads + threadIdx.x] = 0;
+  }
+
+  R acct[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acct[r][i] = 0;
 
   auto tile_base = [&](long long f) -> long long {
     return sb + (((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
@@ -546,12 +594,6 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
       if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + tswz(i)], &src1[gi]);
     }
   };
-
-  R acct[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acct[r][i] = 0;
 
   long long f = r0;
   int slot = 0;
@@ -615,24 +657,34 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
       }
       if (NS == 2) {
         if (P.defer) {
-          // keep per-thread sums across tiles; reduced once after the last tile
+          // keep per-thread sums across tiles, reduced once after the last
+          // tile: the pass's own slots in registers, companion slots in this
+          // thread's column of shared memory
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr)
             if (rr == r) {
 #pragma unroll
               for (int i = 0; i < (RB < 4 ? RB : 4); ++i) acct[rr][i] += acc[i * 3];
             }
+          if (P.ncomp) {
+#pragma unroll
+            for (int i = 0; i < (RB < 4 ? RB : 4); ++i) {
+              const int cs = P.rcslot[r][i];
+              if (cs >= 0) sdef[(cs - P.nslots + P.ncomp) * kThreads + threadIdx.x] += acc[i * 3 + 1];
+            }
+          }
         } else {
           for (int k = op0; k < op1; ++k) {
             const TileOp& o = P.ops[k];
             const int i = o.l - lo;
-            for (int q = 0; q < o.np; ++q) {
+            for (int q = 0; q < o.np + (o.ck ? 1 : 0); ++q) {
+              const int qi = q < o.np ? q : 1;
               R val = 0;
 #pragma unroll
               for (int s = 0; s < RB * 3; ++s)
-                if (s == i * 3 + q) val = acc[s];
+                if (s == i * 3 + qi) val = acc[s];
               double v = warp_sum((double)val);
-              if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
+              if (lane == 0) sred[warp * P.nslots + (q < o.np ? o.slot + q : o.cslot)] += v;
             }
           }
         }
@@ -687,6 +739,10 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
           if (lane == 0) sred[warp * P.nslots + sl] += v;
         }
       }
+    for (int s = 0; s < P.ncomp; ++s) {
+      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
+      if (lane == 0) sred[warp * P.nslots + P.nslots - P.ncomp + s] += v;
+    }
   }
   if (NS == 2 && P.nslots > 0) {
     __syncthreads();
@@ -1511,6 +1567,7 @@ size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) {
   size_t s = (size_t)2 * ns * ((size_t)1 << P.t) * 2 * rsize;
   s += (size_t)((P.ncoef + 1) & ~1) * rsize;
   s += (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double);
+  if (ns == 2 && P.defer) s += (size_t)P.ncomp * kThreads * rsize;
   return s;
 }
 

@@ -118,7 +118,7 @@ def _tile_passes(desc):
         if " TILE " not in line:
             continue
         d = dict(re.findall(r"(\w+)=(-?\d+)", line.split("[")[0]))
-        ops = re.findall(r"\[l=(\d+)(,2q)? np=(\d+)\]", line)
+        ops = re.findall(r"\[l=(\d+)(,2q)? np=(\d+)[^\]]*\]", line)
         out.append((line[0], int(d["layer"]), {k: int(v) for k, v in d.items()}, ops))
     return out
 
@@ -181,6 +181,43 @@ def test_fused_zz26_plan_has_no_standalone_ring_or_diag_in_the_forward(q):
     bwd = [l for l in desc.splitlines() if l.startswith("B ")]
     assert sum(" RING " in l for l in bwd) == 1      # the last ring (lambda formed there)
     assert not any("LAMINIT" in l for l in bwd)
+
+
+def test_leading_rotation_layer_folds_into_the_next_backward_layer(q):
+    """RX(x) then RY(theta): the embedding's gradients ride on the RY passes
+    (companion X slots), so the backward never undoes layer 0 and the last RY
+    pass skips its store; without fusion layer 0 gets its own passes."""
+    cfg = W.WORKLOADS["zz26"]
+    desc, _ = _plan(q, 26, cfg["layers"](), batch=8, path=0)
+    bwd = [l for l in desc.splitlines() if l.startswith("B ")]
+    assert not any(l.startswith("B layer=0 ") for l in bwd)
+    l1 = [l for l in bwd if l.startswith("B layer=1 TILE")]
+    assert len(l1) == 3
+    nops = sum(int(re.search(r" ops=(\d+)", l).group(1)) for l in l1)
+    assert nops == 26 and sum(l.count("+X") for l in l1) == 26
+    for l in l1:
+        d = dict(re.findall(r"(\w+)=(-?\d+)", l.split("[")[0]))
+        assert int(d["slots"]) == 2 * int(d["ops"])
+    assert "store=0" in l1[-1] and all("store=1" in l for l in l1[:-1])
+    plain, _ = _plan(q, 26, cfg["layers"](), batch=8, path=0, fuse=0)
+    assert any(l.startswith("B layer=0 TILE") for l in plain.splitlines())
+    assert "+X" not in plain
+    # a parameter-free single-qubit layer carries only companion slots
+    b = W._Builder(14)
+    b.add("RY", "input")
+    b.add("SX")
+    b.add("RZ", "theta")
+    sx, _ = _plan(q, 14, b.layers)
+    for l in sx.splitlines():
+        if l.startswith("B layer=1 TILE"):
+            assert "+Y" in l and " np=1" not in l
+    # not folded when an earlier layer still needs the backward sweep
+    b = W._Builder(14)
+    b.add("RZ", "theta")
+    b.add("RX", "input")
+    b.add("RY", "theta")
+    mid, _ = _plan(q, 14, b.layers)
+    assert "+X" not in mid and any(l.startswith("B layer=1 TILE") for l in mid.splitlines())
 
 
 def test_small_circuits_use_shared_memory_path(q):

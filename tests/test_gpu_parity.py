@@ -114,6 +114,47 @@ def test_every_kind_in_every_position_layer_path():
     compare("c64", n, b.layers, 2, seed=5, path=2)
 
 
+def _fold_circuit(n, name):
+    """Leading RX / RY layer followed by a single-qubit layer: the backward
+    takes the leading layer's gradients on the next layer's passes."""
+    b = W._Builder(n)
+    spec = {
+        "rx_ry": [("RX", "input"), ("RY", "theta"), ("ISINGZZ_RING", "theta"), ("CNOT_RING", "none"),
+                  ("RY", "theta")],
+        "ry_rx": [("RY", "input"), ("RX", "theta"), ("CNOT_RING", "none"), ("RX", "theta")],
+        "rx_sx": [("RX", "input"), ("SX", "none"), ("RZ", "theta"), ("CNOT_RING", "none"), ("RY", "theta")],
+        "ry_gpi2": [("RY", "theta"), ("GPI2", "theta"), ("CNOT_RING", "none"), ("GPI", "theta")],
+        "sx_rx_ry": [("SX", "none"), ("RX", "input"), ("RY", "theta"), ("MS_BRICK", "theta")],
+    }[name]
+    for k, src in spec:
+        b.add(k, src)
+    return b.layers
+
+
+@pytest.mark.parametrize("name", ["rx_ry", "ry_rx", "rx_sx", "ry_gpi2", "sx_rx_ry"])
+@pytest.mark.parametrize("dtype,n", [("c64", 14), ("c128", 13)])
+def test_leading_layer_gradient_folded_into_next_layer(name, dtype, n):
+    compare(dtype, n, _fold_circuit(n, name), 3, seed=11, path=2, fuse=1)
+
+
+def test_folded_gradients_without_deferred_sums():
+    """Two register bits per round: more than four rounds per pass, so the
+    per-round warp reduction carries the companion slots (own process: the
+    knob is read once)."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, '.');"
+            "from tests.test_gpu_parity import compare, _fold_circuit;"
+            "[compare('c64', 14, _fold_circuit(14, k), 2, seed=12, path=2) for k in ('rx_ry', 'ry_rx', 'rx_sx')];"
+            "compare('c128', 13, _fold_circuit(13, 'ry_gpi2'), 2, seed=12, path=2)")
+    import os
+    env = dict(os.environ, QC_RB_BWD="2")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
 def test_empty_circuit_and_batch_one():
     for path in (1, 2):
         got = run_gpu(5, [], np.zeros((1, 0)), np.zeros(0), np.full((1, 5), 0.2), dtype="c128", path=path)
