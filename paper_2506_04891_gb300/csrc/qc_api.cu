@@ -218,6 +218,18 @@ int reg_bits(const qc_circuit* c, int ns) {
   return ns == 2 ? 3 : 4;
 }
 
+// Shared-memory tile buffers of a pass.  Two (one tile in flight while one is
+// processed) measured faster on zz26 than three: the passes are bound by issue
+// and shared-memory latency, not by bytes in flight.  QC_TILE_STAGES=3 takes
+// three where two CTAs per SM still fit.
+int tile_stages(TilePass& P, int ns, int rsize) {
+  static const int k = env_knob("QC_TILE_STAGES");
+  if (k != 3) return 2;
+  P.nstage = 3;
+  const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
+  return 2 * (tile_smem_bytes(P, ns, rsize) + per_cta_reserved) <= per_sm ? 3 : 2;
+}
+
 bool cuts_pair(const LayerInfo& L, int n, int e) {
   // boundary between bits e-1 and e cuts a brick pair (p_lo, p_hi) = (e-1, e)
   if (L.cls != LC_DENSE2 || e <= 0 || e >= n) return false;
@@ -392,6 +404,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     if (!defer)
       for (int r = 0; r < 4; ++r)
         for (int i = 0; i < 4; ++i) P.rslot[r][i] = P.rcslot[r][i] = -1;
+    P.nstage = tile_stages(P, ns, (int)c->rsize);
     out.push_back(P);
     s = e;
     first = false;
@@ -1420,8 +1433,8 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
   auto dump = [&](const char* tag, const std::vector<Step>& v) {
     for (auto& st : v) {
       if (st.type == ST_TILE) {
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d rounds=%d ops=%d slots=%d store=%d src=%d dst=%d",
-                 tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nrounds, st.tp.nops, st.tp.nslots,
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d src=%d dst=%d",
+                 tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nstage, st.tp.nrounds, st.tp.nops, st.tp.nslots,
                  st.tp.store, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {

@@ -77,6 +77,7 @@ struct TilePass {
   int8_t rlo[kMaxRounds];            // round r: register bits [rlo[r], rlo[r] + RB)
   int16_t rop[kMaxRounds + 1];       // ops of round r: [rop[r], rop[r+1])
   int nops;
+  int nstage;                        // shared-memory tile buffers (2 or 3)
   int nslots;                        // gradient slots (bwd)
   int ncomp;                         // companion slots: the last ncomp of the nslots
   int store;                         // 0: gradient only, no store

@@ -516,11 +516,24 @@ __device__ __forceinline__ void tile_bit(const TilePass& P, int r, cx<R>* v0, cx
   }
 }
 
-// Tile-pass shared-memory layout: XOR swizzle of index bits 0..3 by bits
-// 4..7.  It is linear over GF(2), so the address of (base | a << lo) is
-// swz(base) ^ swz(a << lo), and every round's half-warp accesses hit 16
-// distinct 8-byte bank pairs.
-__device__ __forceinline__ int tswz(int i) { return i ^ ((i >> 4) & 15); }
+// Tile-pass shared-memory layout: an XOR swizzle that folds index bits 4..7
+// (complex64: 8-byte elements, 16 per 128-byte wavefront) or 3..6
+// (complex128: 16-byte elements, 8 per wavefront) into the bank bits, with
+// fold columns (15, 10, 12, 8) and (7, 5, 6, 4) packed as nibble tables.
+// With these columns every round's accesses (register bits [lo, lo + RB) for
+// any lo and RB <= 4), the copy loop and the paired complex64 store hit
+// distinct banks; an exhaustive host-side count of wavefronts fixed them (the
+// plain fold of bits 4..7 onto bits 0..3 is 2-way conflicted at lo = 3,
+// RB = 3).  The map is linear over GF(2), so the address of (base | a << lo)
+// is swz(base) ^ swz(a << lo), and it leaves bits >= 8 alone, so
+// swz(i + k * 256) = swz(i) + k * 256.
+template <class R>
+__device__ __forceinline__ int tswz(int i) {
+  if constexpr (sizeof(R) == 4)
+    return i ^ (int)((0x1eb4d278963c5af0ull >> (4 * ((i >> 4) & 15))) & 15);
+  else
+    return i ^ (int)((0x0752613443162570ull >> (4 * ((i >> 3) & 15))) & 15);
+}
 
 template <int BYTES>
 __device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
@@ -537,8 +550,8 @@ __device__ __forceinline__ void cp_async_wait_group() {
 }
 
 // Persistent tile pass.  CTA (b, r) of the cps CTAs of sample b handles tiles
-// f = r, r + cps, ... of that sample; the next tile is copied into the second
-// shared-memory buffer while the current one is processed.
+// f = r, r + cps, ... of that sample through a ring of P.nstage shared-memory
+// buffers: the next nstage - 1 tiles are in flight while one is processed.
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials into part[slot][block]).
 template <class R, int NS, int RB, int KIND>
@@ -551,8 +564,9 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = P.t, n = P.n, c = P.c, h0 = P.h0;
   const int T = 1 << t;
-  C* buf = reinterpret_cast<C*>(smraw);  // [2][NS][T]
-  R* sco = reinterpret_cast<R*>(buf + 2 * NS * T);
+  const int nst = P.nstage;
+  C* buf = reinterpret_cast<C*>(smraw);  // [nst][NS][T]
+  R* sco = reinterpret_cast<R*>(buf + nst * NS * T);
   double* sred = reinterpret_cast<double*>(sco + ((P.ncoef + 1) & ~1));  // [kWarps][nslots]
   R* sdef = reinterpret_cast<R*>(sred + kWarps * (P.nslots > 0 ? P.nslots : 1));  // [ncomp][kThreads]
 
@@ -563,6 +577,7 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
   const int cmask = (1 << c) - 1;
   const long long sb = (long long)b << n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sw_tid = tswz<R>(threadIdx.x), sw_tid2 = tswz<R>(2 * threadIdx.x);
 
   for (int k = 0; k < P.nops; ++k) {
     const TileOp& o = P.ops[k];
@@ -587,32 +602,37 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
   auto issue = [&](long long f, int slot) {
     const long long base = tile_base(f);
     C* d0 = buf + (long long)slot * NS * T;
-    for (int i = threadIdx.x; i < T; i += kThreads) {
+    for (int i = threadIdx.x, si = sw_tid; i < T; i += kThreads, si += kThreads) {
       long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
       if (P.gather) gi = sb + ring_finv(gi - sb, n);
-      cp_async_elem<sizeof(C)>(&d0[tswz(i)], &src0[gi]);
-      if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + tswz(i)], &src1[gi]);
+      cp_async_elem<sizeof(C)>(&d0[si], &src0[gi]);
+      if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + si], &src1[gi]);
     }
   };
 
   long long f = r0;
   int slot = 0;
-  if (f < tps) issue(f, 0);
-  cp_async_commit();
-  for (; f < tps; f += cps) {
-    const long long fn = f + cps;
-    if (fn < tps) issue(fn, slot ^ 1);
+  for (int j = 0; j + 1 < nst; ++j) {
+    if (f + (long long)j * cps < tps) issue(f + (long long)j * cps, j);
     cp_async_commit();
-    cp_async_wait_group<1>();
+  }
+  for (; f < tps; f += cps) {
+    // every iteration commits one group (possibly empty), so the group of
+    // tile f is complete once at most nst - 1 newer groups are pending
+    const long long fn = f + (long long)(nst - 1) * cps;
+    const int sn = slot + nst - 1 < nst ? slot + nst - 1 : slot - 1;
+    if (fn < tps) issue(fn, sn);
+    cp_async_commit();
+    if (nst == 3) cp_async_wait_group<2>();
+    else cp_async_wait_group<1>();
     __syncthreads();
     C* S0 = buf + (long long)slot * NS * T;
     C* S1 = S0 + T;
     if (NS == 1 && P.pre) {
       const long long base = tile_base(f) - sb;
       const R* tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
-      for (int i = threadIdx.x; i < T; i += kThreads) {
+      for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
         const long long k = base + (i & cmask) + ((long long)(i >> c) << h0);
-        const int pi = tswz(i);
         S0[pi] = cmul<R>(diag_phase<R>(tabs, P.pre_tb, ztrans(k, n, P.pre_zmode)), S0[pi]);
       }
       __syncthreads();
@@ -628,9 +648,9 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
       // address of register element a = pb ^ (XOR of basis[j] over set bits j of a)
       int basis[RB];
 #pragma unroll
-      for (int j = 0; j < RB; ++j) basis[j] = tswz(1 << (lo + j));
+      for (int j = 0; j < RB; ++j) basis[j] = tswz<R>(1 << (lo + j));
       for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
-        const int pb = tswz((g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB)));
+        const int pb = tswz<R>((g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB)));
         C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
 #pragma unroll
         for (int a = 0; a < (1 << RB); ++a) {
@@ -696,9 +716,8 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
       const long long base = tile_base(f);
       if (P.post || P.scatter) {
         const R* tabs = coef + P.post_coef + (long long)b * P.post_bstride;
-        for (int i = threadIdx.x; i < T; i += kThreads) {
+        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
           const long long kl = base - sb + (i & cmask) + ((long long)(i >> c) << h0);
-          const int pi = tswz(i);
           C e = S0[pi];
           if (NS == 1 && P.post) e = cmul<R>(diag_phase<R>(tabs, P.post_tb, ztrans(kl, n, P.post_zmode)), e);
           const long long gd = sb + (P.scatter ? ring_finv(kl, n) : kl);
@@ -706,9 +725,8 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
           if (NS == 2) dst1[gd] = S1[pi];
         }
       } else if (sizeof(C) == 8) {
-        for (int i = 2 * threadIdx.x; i < T; i += 2 * kThreads) {
+        for (int i = 2 * threadIdx.x, pi = sw_tid2; i < T; i += 2 * kThreads, pi += 2 * kThreads) {
           const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
-          const int pi = tswz(i);
           C e0 = S0[pi], e1 = S0[pi ^ 1];
           *reinterpret_cast<float4*>(&dst0[gi]) = make_float4(e0.x, e0.y, e1.x, e1.y);
           if (NS == 2) {
@@ -717,15 +735,15 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
           }
         }
       } else {
-        for (int i = threadIdx.x; i < T; i += kThreads) {
+        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
           const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
-          dst0[gi] = S0[tswz(i)];
-          if (NS == 2) dst1[gi] = S1[tswz(i)];
+          dst0[gi] = S0[pi];
+          if (NS == 2) dst1[gi] = S1[pi];
         }
       }
     }
     __syncthreads();
-    slot ^= 1;
+    slot = slot + 1 == nst ? 0 : slot + 1;
   }
   cp_async_wait_group<0>();
   if (NS == 2 && P.defer) {
@@ -1564,7 +1582,7 @@ cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi,
 }
 
 size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) {
-  size_t s = (size_t)2 * ns * ((size_t)1 << P.t) * 2 * rsize;
+  size_t s = (size_t)P.nstage * ns * ((size_t)1 << P.t) * 2 * rsize;
   s += (size_t)((P.ncoef + 1) & ~1) * rsize;
   s += (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double);
   if (ns == 2 && P.defer) s += (size_t)P.ncomp * kThreads * rsize;
