@@ -289,9 +289,10 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
         o.op.real = (int8_t)L.real;
         o.op.gk = (int8_t)(L.kind == QC_L_RX ? 1 : (L.kind == QC_L_RY ? 2 : 0));
         o.op.np = (int16_t)((ns == 2 && L.diff) ? 1 : 0);
-        o.op.coef = L.coef_off + (long long)q * kRec1q;
+        // real ops stage the packed real matrix; complex ones M (+ A backward)
+        o.op.coef = L.coef_off + (long long)q * kRec1q + (L.real ? kRealOff : 0);
         o.op.bstride = L.coef_bstride;
-        o.op.nco = ns == 2 ? kRec1q : 8;
+        o.op.nco = L.real ? 4 : (ns == 2 ? 16 : 8);
         if (o.op.np) o.pidx.push_back(L.offset + q);
         o.cpidx = -1;
         if (ns == 2 && comp) {

@@ -29,7 +29,9 @@ enum LayerClass {
 enum ZMode { Z_IDENT = 0, Z_RINGXOR = 1 };
 
 // Coefficient records, in units of the state's real type R.
-constexpr int kRec1q = 16;    // M (2x2 complex) + A = M^dagger dM (2x2 complex)
+constexpr int kRec1q = 20;    // M (2x2 complex) + A = M^dagger dM (2x2 complex) + the real parts
+                              // of M packed (m00, m01, m10, m11) at kRealOff
+constexpr int kRealOff = 16;
 constexpr int kRec2q = 128;   // M (4x4 complex) + up to three A (4x4 complex)
 
 struct LayerInfo {

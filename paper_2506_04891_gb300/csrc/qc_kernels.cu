@@ -51,6 +51,26 @@ template <class R> __device__ __forceinline__ R im_cdot(cx<R> l, cx<R> v) {  // 
   return l.x * v.y - l.y * v.x;
 }
 template <class R> __device__ __forceinline__ cx<R> ldc(const R* p) { return mk<R>(p[0], p[1]); }
+// Four consecutive R from a 16-byte aligned address (shared-memory staged
+// coefficients): one 16-byte load for float, two for double.
+template <class R>
+__device__ __forceinline__ void ld4(const R* p, R& a, R& b, R& c, R& d) {
+  if constexpr (std::is_same<R, float>::value) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+  } else {
+    const double2 u = *reinterpret_cast<const double2*>(p), v = *reinterpret_cast<const double2*>(p + 2);
+    a = u.x; b = u.y; c = v.x; d = v.y;
+  }
+}
+// Two consecutive complex values (a 2x2 matrix row or column pair).
+template <class R>
+__device__ __forceinline__ void ldc2(const R* p, cx<R>& u, cx<R>& v) {
+  R a, b, c, d;
+  ld4<R>(p, a, b, c, d);
+  u = mk<R>(a, b);
+  v = mk<R>(c, d);
+}
 
 // Real coefficient times complex value, packed over (re, im): one FMUL2 /
 // FFMA2 on sm_100+ for float, two scalar ops for double.
@@ -91,6 +111,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 //   inverse  f^-1(k) = k ^ (k >> 1) ^ (k & 1 ? 3 << (n-2) : 0)
 __device__ __forceinline__ long long ring_finv(long long k, int n) {
   return k ^ (k >> 1) ^ ((k & 1) ? (3LL << (n - 2)) : 0LL);
+}
+// ring_finv for offsets below 2^30 (3 << (n - 2) fits for n <= 30)
+__device__ __forceinline__ int ring_finv32(int k, int n) {
+  return k ^ (k >> 1) ^ ((k & 1) ? (3 << (n - 2)) : 0);
 }
 __device__ __forceinline__ int par64(long long v) { return __popcll((unsigned long long)v) & 1; }
 __device__ __forceinline__ long long ring_f(long long k, int n) {
@@ -158,6 +182,7 @@ __global__ void k_coef(const CoefJob* __restrict__ jobs, int njobs, int n, int b
       for (int i = 0; i < 4; ++i) {
         o[2 * i] = (R)M[i].x; o[2 * i + 1] = (R)M[i].y;
         o[8 + 2 * i] = (R)A[i].x; o[8 + 2 * i + 1] = (R)A[i].y;
+        o[kRealOff + i] = (R)M[i].x;
       }
     }
   } else if (J.cls == LC_DENSE2) {
@@ -294,11 +319,14 @@ __global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* _
 // ---------------------------------------------------------------------------
 
 // forward single-qubit op on register bit I
+// `m` is the staged record: the packed real matrix for a real op, else M
+// (2x2 complex) followed, backward, by A = M^dagger dM.
 template <class R, int RB, int I>
 __device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
   using C = cx<R>;
   if (real) {
-    const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
+    R m00, m01, m10, m11;
+    ld4<R>(m, m00, m01, m10, m11);
 #pragma unroll
     for (int a = 0; a < (1 << RB); ++a)
       if (!(a & (1 << I))) {
@@ -307,7 +335,9 @@ __device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
         v[a | (1 << I)] = rfma<R>(m11, x1, rmul<R>(m10, x0));
       }
   } else {
-    const C m00 = ldc<R>(m), m01 = ldc<R>(m + 2), m10 = ldc<R>(m + 4), m11 = ldc<R>(m + 6);
+    C m00, m01, m10, m11;
+    ldc2<R>(m, m00, m01);
+    ldc2<R>(m + 4, m10, m11);
 #pragma unroll
     for (int a = 0; a < (1 << RB); ++a)
       if (!(a & (1 << I))) {
@@ -335,9 +365,11 @@ template <class R, int RB, int I>
 __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, int ck,
                                     R* acc) {
   using C = cx<R>;
-  if (real && gk == 2) {
-    // RY: undo with M^T; 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
-    const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
+  if (real) {
+    // RY (the only real gate; m is its packed real matrix): undo with M^T;
+    // 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
+    R m00, m01, m10, m11;
+    ld4<R>(m, m00, m01, m10, m11);
     C ga = mk<R>(0, 0), gb = mk<R>(0, 0);
     if (ck == 1) {
       // companion RX: Im(l0* p1 + l1* p0), packed as l * swap(p)
@@ -381,33 +413,14 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
     if (np) acc[I * 3] += (ga.x + ga.y) - (gb.x + gb.y);
     return;
   }
-  if (real) {
-    // M^dagger = M^T for a real M
-    const R m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
-    const R a00 = m[8], a01 = m[10], a10 = m[12], a11 = m[14];
-    R g = 0;
-#pragma unroll
-    for (int a = 0; a < (1 << RB); ++a)
-      if (!(a & (1 << I))) {
-        const int a1 = a | (1 << I);
-        C x0 = p[a], x1 = p[a1];
-        C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
-        C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
-        p[a] = y0; p[a1] = y1;
-        C u0 = l[a], u1 = l[a1];
-        C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
-        C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
-        l[a] = w0; l[a1] = w1;
-        if (np) {
-          g += a00 * re_cdot<R>(w0, y0) + a01 * re_cdot<R>(w0, y1) + a10 * re_cdot<R>(w1, y0) +
-               a11 * re_cdot<R>(w1, y1);
-        }
-        if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
-      }
-    if (np) acc[I * 3] += 2 * g;
-  } else {
-    const C m00 = ldc<R>(m), m01 = ldc<R>(m + 2), m10 = ldc<R>(m + 4), m11 = ldc<R>(m + 6);
-    const C a00 = ldc<R>(m + 8), a01 = ldc<R>(m + 10), a10 = ldc<R>(m + 12), a11 = ldc<R>(m + 14);
+  {
+    C m00, m01, m10, m11, a00, a01, a10, a11;
+    ldc2<R>(m, m00, m01);
+    ldc2<R>(m + 4, m10, m11);
+    if (np && gk != 1) {
+      ldc2<R>(m + 8, a00, a01);
+      ldc2<R>(m + 12, a10, a11);
+    }
     R g = 0;
 #pragma unroll
     for (int a = 0; a < (1 << RB); ++a)
@@ -596,17 +609,25 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
 #pragma unroll
     for (int i = 0; i < 4; ++i) acct[r][i] = 0;
 
-  auto tile_base = [&](long long f) -> long long {
-    return sb + (((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
+  // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
+  // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
+  // bits [0, c) and [h0, h0 + m).
+  const C* s0b = src0 + sb;
+  const C* s1b = NS == 2 ? src1 + sb : nullptr;
+  C* d0b = dst0 + sb;
+  C* d1b = NS == 2 ? dst1 + sb : nullptr;
+  auto tile_base = [&](long long f) -> int {
+    return (int)(((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
   };
+  auto elem_off = [&](int i) -> int { return (i & cmask) | ((i >> c) << h0); };
   auto issue = [&](long long f, int slot) {
-    const long long base = tile_base(f);
-    C* d0 = buf + (long long)slot * NS * T;
+    const int base = tile_base(f);
+    C* d0 = buf + slot * NS * T;
     for (int i = threadIdx.x, si = sw_tid; i < T; i += kThreads, si += kThreads) {
-      long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
-      if (P.gather) gi = sb + ring_finv(gi - sb, n);
-      cp_async_elem<sizeof(C)>(&d0[si], &src0[gi]);
-      if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + si], &src1[gi]);
+      int gi = base | elem_off(i);
+      if (P.gather) gi = ring_finv32(gi, n);
+      cp_async_elem<sizeof(C)>(&d0[si], &s0b[gi]);
+      if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + si], &s1b[gi]);
     }
   };
 
@@ -629,10 +650,10 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
     C* S0 = buf + (long long)slot * NS * T;
     C* S1 = S0 + T;
     if (NS == 1 && P.pre) {
-      const long long base = tile_base(f) - sb;
+      const int base = tile_base(f);
       const R* tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
       for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-        const long long k = base + (i & cmask) + ((long long)(i >> c) << h0);
+        const long long k = base | elem_off(i);
         S0[pi] = cmul<R>(diag_phase<R>(tabs, P.pre_tb, ztrans(k, n, P.pre_zmode)), S0[pi]);
       }
       __syncthreads();
@@ -713,32 +734,32 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
     }
 
     if (P.store) {
-      const long long base = tile_base(f);
+      const int base = tile_base(f);
       if (P.post || P.scatter) {
         const R* tabs = coef + P.post_coef + (long long)b * P.post_bstride;
         for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-          const long long kl = base - sb + (i & cmask) + ((long long)(i >> c) << h0);
+          const int kl = base | elem_off(i);
           C e = S0[pi];
           if (NS == 1 && P.post) e = cmul<R>(diag_phase<R>(tabs, P.post_tb, ztrans(kl, n, P.post_zmode)), e);
-          const long long gd = sb + (P.scatter ? ring_finv(kl, n) : kl);
-          dst0[gd] = e;
-          if (NS == 2) dst1[gd] = S1[pi];
+          const int gd = P.scatter ? ring_finv32(kl, n) : kl;
+          d0b[gd] = e;
+          if (NS == 2) d1b[gd] = S1[pi];
         }
       } else if (sizeof(C) == 8) {
         for (int i = 2 * threadIdx.x, pi = sw_tid2; i < T; i += 2 * kThreads, pi += 2 * kThreads) {
-          const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
+          const int gi = base | elem_off(i);
           C e0 = S0[pi], e1 = S0[pi ^ 1];
-          *reinterpret_cast<float4*>(&dst0[gi]) = make_float4(e0.x, e0.y, e1.x, e1.y);
+          *reinterpret_cast<float4*>(&d0b[gi]) = make_float4(e0.x, e0.y, e1.x, e1.y);
           if (NS == 2) {
             C u0 = S1[pi], u1 = S1[pi ^ 1];
-            *reinterpret_cast<float4*>(&dst1[gi]) = make_float4(u0.x, u0.y, u1.x, u1.y);
+            *reinterpret_cast<float4*>(&d1b[gi]) = make_float4(u0.x, u0.y, u1.x, u1.y);
           }
         }
       } else {
         for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-          const long long gi = base + (i & cmask) + ((long long)(i >> c) << h0);
-          dst0[gi] = S0[pi];
-          if (NS == 2) dst1[gi] = S1[pi];
+          const int gi = base | elem_off(i);
+          d0b[gi] = S0[pi];
+          if (NS == 2) d1b[gi] = S1[pi];
         }
       }
     }
