@@ -495,7 +495,9 @@ __device__ __forceinline__ void bw2(cx<R>* p, cx<R>* l, const R* m, int np, R* a
       }
 #pragma unroll
       for (int s = 0; s < 4; ++s) { p[a | (s << I)] = y[s]; l[a | (s << I)] = w[s]; }
-      for (int k = 0; k < np; ++k) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {  // compile-time acc index (np <= 3)
+        if (k >= np) break;
         const R* A = m + 32 + 32 * k;
         R g = 0;
 #pragma unroll
@@ -662,7 +664,6 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
 #pragma unroll 1
     for (int r = 0; r < P.nrounds; ++r) {
       const int lo = P.rlo[r];
-      const int op0 = P.rop[r], op1 = P.rop[r + 1];
       R acc[RB * 3];
 #pragma unroll
       for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
@@ -715,17 +716,22 @@ __global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB
             }
           }
         } else {
-          for (int k = op0; k < op1; ++k) {
-            const TileOp& o = P.ops[k];
-            const int i = o.l - lo;
-            for (int q = 0; q < o.np + (o.ck ? 1 : 0); ++q) {
-              const int qi = q < o.np ? q : 1;
-              R val = 0;
+          // per op of the round, by its (lower) register bit: every acc index
+          // is a compile-time constant, so acc stays in registers
 #pragma unroll
-              for (int s = 0; s < RB * 3; ++s)
-                if (s == i * 3 + qi) val = acc[s];
-              double v = warp_sum((double)val);
-              if (lane == 0) sred[warp * P.nslots + (q < o.np ? o.slot + q : o.cslot)] += v;
+          for (int i = 0; i < RB; ++i) {
+            const int k = P.rbit[r][i];
+            if (k < 0) continue;
+            const TileOp& o = P.ops[k];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < o.np) {
+                const double v = warp_sum((double)acc[i * 3 + q]);
+                if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
+              }
+            if (o.ck) {
+              const double v = warp_sum((double)acc[i * 3 + 1]);
+              if (lane == 0) sred[warp * P.nslots + o.cslot] += v;
             }
           }
         }
