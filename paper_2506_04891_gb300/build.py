@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libqlayer.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["qc_kernels.cu", "qc_api.cu", "qc_noalloc.cu"]
+SOURCES = ["qc_tile_bwd.cu", "qc_tile_fwd.cu", "qc_kernels.cu", "qc_api.cu", "qc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -576,6 +576,28 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       std::vector<std::vector<int>> pslots;
       int layer;                // layer whose parameters the group differentiates
       int comp = -1;            // layer whose gradients ride along as companions
+      int pre_layer = -1;       // diagonal layer undone in the first pass's round 0
+    };
+    // tile passes of layer tl, folding a leading RX / RY layer before it
+    // (companion gradients; that layer is never undone) or scattering
+    // through a CNOT ring before it
+    auto tile_group = [&](int tl, BGroup& g) {
+      const LayerInfo& Lt = LI[tl];
+      const bool fold = fuse && Lt.cls == LC_ROT1 && tl >= 1 && LI[tl - 1].cls == LC_ROT1 &&
+                        (LI[tl - 1].kind == QC_L_RX || LI[tl - 1].kind == QC_L_RY) &&
+                        LI[tl - 1].diff && LI[tl - 1].nparams > 0 && (tl == 1 || !need[tl - 2]);
+      if (fold) {
+        g.comp = tl - 1;
+        g.steps = tile_steps(Lt, 2, g.pslots, &LI[tl - 1]);
+        g.lo = tl - 1;
+      } else {
+        g.steps = tile_steps(Lt, 2, g.pslots);
+        g.lo = tl;
+        if (fuse && !g.steps.empty() && is_ring(tl - 1) && need[tl - 1]) {
+          g.steps.back().tp.scatter = 1;  // the last (top) pass holds bit n-1
+          g.lo = tl - 1;
+        }
+      }
     };
     std::vector<BGroup> bgroups;
     bool laminit_fused = false;
@@ -586,22 +608,37 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         g.hi = i;
         g.layer = i;
         const LayerInfo& Li = LI[i];
-        // a leading RX / RY layer right before a single-qubit layer: its
-        // gradients come from this layer's passes and it is never undone
-        const bool fold = fuse && Li.cls == LC_ROT1 && i >= 1 && LI[i - 1].cls == LC_ROT1 &&
-                          (LI[i - 1].kind == QC_L_RX || LI[i - 1].kind == QC_L_RY) &&
-                          LI[i - 1].diff && LI[i - 1].nparams > 0 && (i == 1 || !need[i - 2]);
-        if (fold) {
-          g.comp = i - 1;
-          g.steps = tile_steps(Li, 2, g.pslots, &LI[i - 1]);
-          g.lo = i - 1;
-        } else if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
-          g.steps = tile_steps(Li, 2, g.pslots);
-          g.lo = i;
-          if (fuse && !g.steps.empty() && is_ring(i - 1) && need[i - 1]) {
-            g.steps.back().tp.scatter = 1;  // the last (top) pass holds bit n-1
-            g.lo = i - 1;
+        if (fuse && Li.cls == LC_DIAG && i >= 1 && LI[i - 1].cls == LC_ROT1 && need[i - 1]) {
+          // the diagonal layer rides in round 0 of the next layer's contiguous
+          // first pass (register bits 0..RB-1), when that pass has one
+          BGroup h;
+          h.hi = i;
+          h.layer = i - 1;
+          tile_group(i - 1, h);
+          if (!h.steps.empty()) {
+            Step& f0 = h.steps.front();
+            TilePass& tp = f0.tp;
+            // one round-0 group per thread (t - RB <= 8) and lanes whose z bits
+            // never meet the tile's (t >= RB + 6)
+            if (tp.c == tp.t && tp.nrounds > 0 && tp.rlo[0] == 0 && (f0.rb == 3 || f0.rb == 4) &&
+                tp.t >= f0.rb + 6 &&
+                tp.t - f0.rb <= 8 &&
+                (Li.zmode == Z_IDENT || Li.zmode == Z_RINGXOR)) {
+              tp.pre = 1;
+              tp.pre_zmode = Li.zmode;
+              tp.pre_tb = Li.tb;
+              tp.pre_coef = Li.coef_off;
+              tp.pre_bstride = Li.coef_bstride;
+              tp.pre_grad = (Li.diff && Li.nparams > 0) ? 1 : 0;
+              h.pre_layer = i;
+              i = h.lo - 1;
+              bgroups.push_back(std::move(h));
+              continue;
+            }
           }
+        }
+        if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
+          tile_group(i, g);
         } else if (Li.cls == LC_RING) {
           g.steps.push_back(ring_step(2));
           g.lo = i;
@@ -818,6 +855,18 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
             add_job(p, RK_DIRECT, LI[g.comp].source, part_off + nblk * nown, nblk,
                     st.tp.nslots - nown, st.cps, couts);
           part_off += nblk * st.tp.nslots;
+        }
+        if (st.type == ST_TILE && st.tp.pre && st.tp.pre_grad) {
+          // the fused diagonal's marginals [W, M_0 .. M_{n-1}] per CTA
+          const LayerInfo& D = LI[g.pre_layer];
+          const long long nblk = (long long)batch * st.cps;
+          if (st.tp.nslots == 0) st.part_off = part_off;
+          st.tp.pre_moff = part_off - st.part_off;
+          std::vector<OutMap> outs;
+          for (int j = 0; j < D.nparams; ++j)
+            outs.push_back(OutMap{0, diag_zbit(D, n, j), D.offset + j, D.gscale});
+          add_job(p, RK_MARGINAL, D.source, part_off, nblk, n + 1, st.cps, outs);
+          part_off += nblk * (n + 1);
         } else if (st.type == ST_DIAG && Li.diff && Li.nparams > 0) {
           const long long nblk = diag_grid(st.dp, batch);
           st.part_off = part_off;
@@ -1434,9 +1483,9 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
   auto dump = [&](const char* tag, const std::vector<Step>& v) {
     for (auto& st : v) {
       if (st.type == ST_TILE) {
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d src=%d dst=%d",
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d src=%d dst=%d",
                  tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nstage, st.tp.nrounds, st.tp.nops, st.tp.nslots,
-                 st.tp.store, st.s0, st.d0);
+                 st.tp.store, st.tp.pre, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {
           snprintf(line, sizeof line, " [l=%d%s np=%d%s]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "",

@@ -100,8 +100,35 @@ struct TilePass {
   int pre, post;     // 1: multiply by a diagonal phase before / after the gates
   int pre_zmode, post_zmode, pre_tb, post_tb;
   long long pre_coef, pre_bstride, post_coef, post_bstride;
+  // backward pre (contiguous first pass, round 0 at register bits 0..RB-1):
+  // undo a diagonal layer on psi and lambda and write its bit marginals
+  // [W, M_0 .. M_{n-1}] per CTA to part[pre_moff + v * grid + block]
+  int pre_grad;
+  long long pre_moff;
   TileOp ops[kMaxTileOps];
 };
+
+// Shared-memory carve-out of a tile pass, in bytes from the dynamic base, used
+// by the kernel and by the launch size alike: tile buffers, staged
+// coefficients, per-warp gradient sums, per-thread deferred companion sums
+// (backward, deferred), backward pre-diagonal marginals and phase-ratio table,
+// end.  Every block starts on a 16-byte boundary.
+struct TileSmem {
+  size_t buf, sco, sred, sdef, smarg, sratio, end;
+};
+__host__ __device__ inline size_t tsm_align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline TileSmem tile_smem_layout(const TilePass& P, int ns, int rsize) {
+  TileSmem L;
+  L.buf = 0;
+  L.sco = tsm_align16(L.buf + (size_t)P.nstage * ns * ((size_t)1 << P.t) * 2 * rsize);
+  L.sred = tsm_align16(L.sco + (size_t)P.ncoef * rsize);
+  L.sdef = tsm_align16(L.sred + (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double));
+  L.smarg = tsm_align16(L.sdef + (ns == 2 && P.defer ? (size_t)P.ncomp * kThreads * rsize : 0));
+  const bool pre = ns == 2 && P.pre;
+  L.sratio = tsm_align16(L.smarg + (pre ? (size_t)kWarps * (P.n + 1) * sizeof(double) : 0));
+  L.end = tsm_align16(L.sratio + (pre ? (size_t)32 * 2 * rsize : 0));
+  return L;
+}
 
 // Diagonal / complement pass (elementwise).
 struct DiagPass {

@@ -1,156 +1,16 @@
-// CUDA kernels of the layered state-vector simulator (sm_103a).
+// CUDA kernels of the layered state-vector simulator (sm_103a): coefficients,
+// product-state init, diagonal and complement passes, <Z>, the CNOT ring,
+// reductions and the whole-circuit shared-memory kernel.  The tile passes
+// live in qc_tile.cuh (instantiated by qc_tile_fwd.cu / qc_tile_bwd.cu).
 //
 // State: psi[b][k] interleaved complex (float2 / double2), qubit q = bit n-1-q.
 // Every kernel here is bandwidth-shaped: a CTA streams a tile or a contiguous
 // chunk of one sample's state through shared memory or registers once.
-#include <cuda_runtime.h>
-#include <math.h>
-#include <stdint.h>
-
-#include <type_traits>
-
+#include "qc_device.cuh"
 #include "qc_gates.cuh"
-#include "qc_internal.h"
 #include "qc_kernels.h"
 
-// resident CTAs per SM the backward tile pass is compiled for
-#ifndef QC_BWD_MINB
-#define QC_BWD_MINB 2
-#endif
-#ifndef QC_FWD_MINB
-#define QC_FWD_MINB 2
-#endif
-
 namespace qc {
-
-template <class R> struct CT;
-template <> struct CT<float> { using C = float2; };
-template <> struct CT<double> { using C = double2; };
-template <class R> using cx = typename CT<R>::C;
-
-template <class R> __device__ __forceinline__ cx<R> mk(R a, R b) { cx<R> r; r.x = a; r.y = b; return r; }
-template <class R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
-  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// conj(a) * b
-template <class R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b) {
-  return mk<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-// m * v + acc
-template <class R> __device__ __forceinline__ cx<R> cfma(cx<R> m, cx<R> v, cx<R> acc) {
-  return mk<R>(fma(m.x, v.x, fma(-m.y, v.y, acc.x)), fma(m.x, v.y, fma(m.y, v.x, acc.y)));
-}
-// conj(m) * v + acc
-template <class R> __device__ __forceinline__ cx<R> cfmac(cx<R> m, cx<R> v, cx<R> acc) {
-  return mk<R>(fma(m.x, v.x, fma(m.y, v.y, acc.x)), fma(m.x, v.y, fma(-m.y, v.x, acc.y)));
-}
-template <class R> __device__ __forceinline__ R re_cdot(cx<R> l, cx<R> v) {  // Re(conj(l) v)
-  return l.x * v.x + l.y * v.y;
-}
-template <class R> __device__ __forceinline__ R im_cdot(cx<R> l, cx<R> v) {  // Im(conj(l) v)
-  return l.x * v.y - l.y * v.x;
-}
-template <class R> __device__ __forceinline__ cx<R> ldc(const R* p) { return mk<R>(p[0], p[1]); }
-// Four consecutive R from a 16-byte aligned address (shared-memory staged
-// coefficients): one 16-byte load for float, two for double.
-template <class R>
-__device__ __forceinline__ void ld4(const R* p, R& a, R& b, R& c, R& d) {
-  if constexpr (std::is_same<R, float>::value) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    a = v.x; b = v.y; c = v.z; d = v.w;
-  } else {
-    const double2 u = *reinterpret_cast<const double2*>(p), v = *reinterpret_cast<const double2*>(p + 2);
-    a = u.x; b = u.y; c = v.x; d = v.y;
-  }
-}
-// Two consecutive complex values (a 2x2 matrix row or column pair).
-template <class R>
-__device__ __forceinline__ void ldc2(const R* p, cx<R>& u, cx<R>& v) {
-  R a, b, c, d;
-  ld4<R>(p, a, b, c, d);
-  u = mk<R>(a, b);
-  v = mk<R>(c, d);
-}
-
-// Real coefficient times complex value, packed over (re, im): one FMUL2 /
-// FFMA2 on sm_100+ for float, two scalar ops for double.
-template <class R>
-__device__ __forceinline__ cx<R> rmul(R a, cx<R> x) {
-  if constexpr (std::is_same<R, float>::value) return __fmul2_rn(make_float2(a, a), x);
-  else return mk<R>(a * x.x, a * x.y);
-}
-template <class R>
-__device__ __forceinline__ cx<R> rfma(R a, cx<R> x, cx<R> acc) {
-  if constexpr (std::is_same<R, float>::value) return __ffma2_rn(make_float2(a, a), x, acc);
-  else return mk<R>(fma(a, x.x, acc.x), fma(a, x.y, acc.y));
-}
-// componentwise l * v + acc (sum of the components = Re(conj(l) v) contributions)
-template <class R>
-__device__ __forceinline__ cx<R> pfma(cx<R> l, cx<R> v, cx<R> acc) {
-  if constexpr (std::is_same<R, float>::value) return __ffma2_rn(l, v, acc);
-  else return mk<R>(fma(l.x, v.x, acc.x), fma(l.y, v.y, acc.y));
-}
-
-// 16-byte asynchronous global -> shared copy (Ampere+ LDGSTS path)
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Ring = CNOT(q->q+1 mod n) for q = 0..n-1.  With bit p = n-1-q:
-//   forward  f(k):   bit p = parity(k >> p) for p <= n-2, bit n-1 = parity(k mod 2^(n-1))
-//   inverse  f^-1(k) = k ^ (k >> 1) ^ (k & 1 ? 3 << (n-2) : 0)
-__device__ __forceinline__ long long ring_finv(long long k, int n) {
-  return k ^ (k >> 1) ^ ((k & 1) ? (3LL << (n - 2)) : 0LL);
-}
-// ring_finv for offsets below 2^30 (3 << (n - 2) fits for n <= 30)
-__device__ __forceinline__ int ring_finv32(int k, int n) {
-  return k ^ (k >> 1) ^ ((k & 1) ? (3 << (n - 2)) : 0);
-}
-__device__ __forceinline__ int par64(long long v) { return __popcll((unsigned long long)v) & 1; }
-__device__ __forceinline__ long long ring_f(long long k, int n) {
-  // prefix parities from the top: s_p = parity(k >> p)
-  unsigned long long s = (unsigned long long)k;
-  s ^= s >> 1; s ^= s >> 2; s ^= s >> 4; s ^= s >> 8; s ^= s >> 16; s ^= s >> 32;
-  const long long low = (long long)(s & ((1ULL << (n - 1)) - 1));
-  const long long top = (long long)par64(k & ((1LL << (n - 1)) - 1));
-  return low | (top << (n - 1));
-}
-__device__ __forceinline__ int gray_inv(int x) {
-  x ^= x >> 1; x ^= x >> 2; x ^= x >> 4; x ^= x >> 8; x ^= x >> 16;
-  return x;
-}
-
-// compile-time z(j << 8) bits above bit 7 for the marginal accumulators
-template <int ZM>
-__device__ __forceinline__ constexpr int zj_bits(int j) {
-  return ZM == Z_RINGXOR ? ((j << 8) ^ (j << 7)) : (j << 8);
-}
-__device__ __forceinline__ long long ztrans(long long k, int n, int zm) {
-  if (zm == Z_RINGXOR) return k ^ ((k >> 1) | ((k & 1) << (n - 1)));
-  return k;
-}
-
-// phase(z) = T0[z0] T1[z1] T2[z2]
-template <class R>
-__device__ __forceinline__ cx<R> diag_phase(const R* tabs, int tb, long long z) {
-  const long long mask = (1LL << tb) - 1;
-  const long long T = 1LL << tb;
-  cx<R> a = ldc<R>(tabs + 2 * (z & mask));
-  cx<R> b = ldc<R>(tabs + 2 * (T + ((z >> tb) & mask)));
-  cx<R> c = ldc<R>(tabs + 2 * (2 * T + ((z >> (2 * tb)) & mask)));
-  return cmul<R>(cmul<R>(a, b), c);
-}
-
 // ---------------------------------------------------------------------------
 // Coefficients: gate matrices, generators, diagonal phase tables
 // ---------------------------------------------------------------------------
@@ -311,491 +171,6 @@ __global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* _
                        cmul<R>(Tb[i >> la], Ta[i & ma]));
   } else {
     for (int i = threadIdx.x; i < CH; i += blockDim.x) out[i] = cmul<R>(Tb[i >> la], Ta[i & ma]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Tile pass: register-blocked single-qubit and two-qubit gate ops
-// ---------------------------------------------------------------------------
-
-// forward single-qubit op on register bit I
-// `m` is the staged record: the packed real matrix for a real op, else M
-// (2x2 complex) followed, backward, by A = M^dagger dM.
-template <class R, int RB, int I>
-__device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
-  using C = cx<R>;
-  if (real) {
-    R m00, m01, m10, m11;
-    ld4<R>(m, m00, m01, m10, m11);
-#pragma unroll
-    for (int a = 0; a < (1 << RB); ++a)
-      if (!(a & (1 << I))) {
-        C x0 = v[a], x1 = v[a | (1 << I)];
-        v[a] = rfma<R>(m01, x1, rmul<R>(m00, x0));
-        v[a | (1 << I)] = rfma<R>(m11, x1, rmul<R>(m10, x0));
-      }
-  } else {
-    C m00, m01, m10, m11;
-    ldc2<R>(m, m00, m01);
-    ldc2<R>(m + 4, m10, m11);
-#pragma unroll
-    for (int a = 0; a < (1 << RB); ++a)
-      if (!(a & (1 << I))) {
-        C x0 = v[a], x1 = v[a | (1 << I)];
-        v[a] = cfma<R>(m01, x1, cmul<R>(m00, x0));
-        v[a | (1 << I)] = cfma<R>(m11, x1, cmul<R>(m10, x0));
-      }
-  }
-}
-
-// 2 Re <l|(-i/2 G)|p> on one amplitude pair, G = X (ck 1) or Y (ck 2):
-// Im(l0* p1 + l1* p0) and Re(l1* p0) - Re(l0* p1).
-template <class R>
-__device__ __forceinline__ R pauli_grad(int ck, cx<R> w0, cx<R> w1, cx<R> y0, cx<R> y1) {
-  if (ck == 1) return im_cdot<R>(w0, y1) + im_cdot<R>(w1, y0);
-  return re_cdot<R>(w1, y0) - re_cdot<R>(w0, y1);
-}
-
-// backward single-qubit op: undo M on psi and lambda, then accumulate
-// 2 Re <lambda| A |psi> on the gate's input side into acc[3 I].  With a
-// companion generator ck, also the gradient of the preceding layer's RX / RY
-// gate on the same qubit into acc[3 I + 1]: its generator commutes with that
-// gate, so the pair just undone (that layer's output side) gives it.
-template <class R, int RB, int I>
-__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, int ck,
-                                    R* acc) {
-  using C = cx<R>;
-  if (real) {
-    // RY (the only real gate; m is its packed real matrix): undo with M^T;
-    // 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
-    R m00, m01, m10, m11;
-    ld4<R>(m, m00, m01, m10, m11);
-    C ga = mk<R>(0, 0), gb = mk<R>(0, 0);
-    if (ck == 1) {
-      // companion RX: Im(l0* p1 + l1* p0), packed as l * swap(p)
-      C hc = mk<R>(0, 0);
-#pragma unroll
-      for (int a = 0; a < (1 << RB); ++a)
-        if (!(a & (1 << I))) {
-          const int a1 = a | (1 << I);
-          C x0 = p[a], x1 = p[a1];
-          C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
-          C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
-          p[a] = y0; p[a1] = y1;
-          C u0 = l[a], u1 = l[a1];
-          C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
-          C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
-          l[a] = w0; l[a1] = w1;
-          ga = pfma<R>(w1, y0, ga);
-          gb = pfma<R>(w0, y1, gb);
-          hc = pfma<R>(w0, mk<R>(y1.y, y1.x), hc);
-          hc = pfma<R>(w1, mk<R>(y0.y, y0.x), hc);
-        }
-      acc[I * 3 + 1] += hc.x - hc.y;
-    } else {
-#pragma unroll
-      for (int a = 0; a < (1 << RB); ++a)
-        if (!(a & (1 << I))) {
-          const int a1 = a | (1 << I);
-          C x0 = p[a], x1 = p[a1];
-          C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
-          C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
-          p[a] = y0; p[a1] = y1;
-          C u0 = l[a], u1 = l[a1];
-          C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
-          C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
-          l[a] = w0; l[a1] = w1;
-          ga = pfma<R>(w1, y0, ga);
-          gb = pfma<R>(w0, y1, gb);
-          if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
-        }
-    }
-    if (np) acc[I * 3] += (ga.x + ga.y) - (gb.x + gb.y);
-    return;
-  }
-  {
-    C m00, m01, m10, m11, a00, a01, a10, a11;
-    ldc2<R>(m, m00, m01);
-    ldc2<R>(m + 4, m10, m11);
-    if (np && gk != 1) {
-      ldc2<R>(m + 8, a00, a01);
-      ldc2<R>(m + 12, a10, a11);
-    }
-    R g = 0;
-#pragma unroll
-    for (int a = 0; a < (1 << RB); ++a)
-      if (!(a & (1 << I))) {
-        const int a1 = a | (1 << I);
-        C x0 = p[a], x1 = p[a1];
-        // y = M^dagger x: y0 = conj(m00) x0 + conj(m10) x1; y1 = conj(m01) x0 + conj(m11) x1
-        C y0 = cfmac<R>(m10, x1, cfmac<R>(m00, x0, mk<R>(0, 0)));
-        C y1 = cfmac<R>(m11, x1, cfmac<R>(m01, x0, mk<R>(0, 0)));
-        p[a] = y0; p[a1] = y1;
-        C u0 = l[a], u1 = l[a1];
-        C w0 = cfmac<R>(m10, u1, cfmac<R>(m00, u0, mk<R>(0, 0)));
-        C w1 = cfmac<R>(m11, u1, cfmac<R>(m01, u0, mk<R>(0, 0)));
-        l[a] = w0; l[a1] = w1;
-        if (np) {
-          if (gk == 1) {
-            // RX: 2 Re <l|(-i/2 X)|p> = Im(l0* p1 + l1* p0)
-            g += im_cdot<R>(w0, y1) + im_cdot<R>(w1, y0);
-          } else {
-            C t0 = cfma<R>(a01, y1, cmul<R>(a00, y0));
-            C t1 = cfma<R>(a11, y1, cmul<R>(a10, y0));
-            g += 2 * (re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1));
-          }
-        }
-        if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
-      }
-    if (np) acc[I * 3] += g;
-  }
-}
-
-// forward two-qubit op on register bits (I, I+1); 4x4 index = 2*bit(I+1) + bit(I)
-template <class R, int RB, int I>
-__device__ __forceinline__ void ap2(cx<R>* v, const R* m) {
-  using C = cx<R>;
-#pragma unroll
-  for (int a = 0; a < (1 << RB); ++a)
-    if (!(a & (3 << I))) {
-      C x[4], y[4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) x[s] = v[a | (s << I)];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        C t = mk<R>(0, 0);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(m + 2 * (r * 4 + s)), x[s], t);
-        y[r] = t;
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s) v[a | (s << I)] = y[s];
-    }
-}
-
-template <class R, int RB, int I>
-__device__ __forceinline__ void bw2(cx<R>* p, cx<R>* l, const R* m, int np, R* acc) {
-  using C = cx<R>;
-#pragma unroll
-  for (int a = 0; a < (1 << RB); ++a)
-    if (!(a & (3 << I))) {
-      C x[4], u[4], y[4], w[4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) { x[s] = p[a | (s << I)]; u[s] = l[a | (s << I)]; }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        C t = mk<R>(0, 0), z = mk<R>(0, 0);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          C ms = ldc<R>(m + 2 * (s * 4 + r));  // (M^dagger)[r][s] = conj(M[s][r])
-          t = cfmac<R>(ms, x[s], t);
-          z = cfmac<R>(ms, u[s], z);
-        }
-        y[r] = t; w[r] = z;
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s) { p[a | (s << I)] = y[s]; l[a | (s << I)] = w[s]; }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {  // compile-time acc index (np <= 3)
-        if (k >= np) break;
-        const R* A = m + 32 + 32 * k;
-        R g = 0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          C t = mk<R>(0, 0);
-#pragma unroll
-          for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(A + 2 * (r * 4 + s)), y[s], t);
-          g += re_cdot<R>(w[r], t);
-        }
-        acc[I * 3 + k] += 2 * g;
-      }
-    }
-}
-
-// Applies the round's op on register bit I (if any).  KIND is uniform over a
-// pass: 0 complex single-qubit, 1 real single-qubit, 2 two-qubit on (I, I+1).
-template <class R, int NS, int RB, int KIND, int I>
-__device__ __forceinline__ void tile_bit(const TilePass& P, int r, cx<R>* v0, cx<R>* v1,
-                                         const R* sco, R* acc) {
-  if (KIND == 2 && I + 1 >= RB) return;
-  const int k = P.rbit[r][I];
-  if (k < 0) return;
-  const TileOp& o = P.ops[k];
-  const R* mc = sco + o.soff;
-  if (NS == 1) {
-    if (KIND == 2) ap2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, mc);
-    else ap1<R, RB, I>(v0, mc, KIND == 1);
-  } else {
-    if (KIND == 2) bw2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, v1, mc, o.np, acc);
-    else bw1<R, RB, I>(v0, v1, mc, KIND == 1, o.np, o.gk, o.ck, acc);
-  }
-}
-
-// Tile-pass shared-memory layout: an XOR swizzle that folds index bits 4..7
-// (complex64: 8-byte elements, 16 per 128-byte wavefront) or 3..6
-// (complex128: 16-byte elements, 8 per wavefront) into the bank bits, with
-// fold columns (15, 10, 12, 8) and (7, 5, 6, 4) packed as nibble tables.
-// With these columns every round's accesses (register bits [lo, lo + RB) for
-// any lo and RB <= 4), the copy loop and the paired complex64 store hit
-// distinct banks; an exhaustive host-side count of wavefronts fixed them (the
-// plain fold of bits 4..7 onto bits 0..3 is 2-way conflicted at lo = 3,
-// RB = 3).  The map is linear over GF(2), so the address of (base | a << lo)
-// is swz(base) ^ swz(a << lo), and it leaves bits >= 8 alone, so
-// swz(i + k * 256) = swz(i) + k * 256.
-template <class R>
-__device__ __forceinline__ int tswz(int i) {
-  if constexpr (sizeof(R) == 4)
-    return i ^ (int)((0x1eb4d278963c5af0ull >> (4 * ((i >> 4) & 15))) & 15);
-  else
-    return i ^ (int)((0x0752613443162570ull >> (4 * ((i >> 3) & 15))) & 15);
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (BYTES == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// Persistent tile pass.  CTA (b, r) of the cps CTAs of sample b handles tiles
-// f = r, r + cps, ... of that sample through a ring of P.nstage shared-memory
-// buffers: the next nstage - 1 tiles are in flight while one is processed.
-// NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
-// lambda, accumulate gradient partials into part[slot][block]).
-template <class R, int NS, int RB, int KIND>
-__global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB)) k_tile(const __grid_constant__ TilePass P,
-                                                      const R* __restrict__ coef,
-                                                      const cx<R>* src0, cx<R>* dst0,
-                                                      const cx<R>* src1, cx<R>* dst1,
-                                                      double* __restrict__ part, int cps) {
-  using C = cx<R>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int t = P.t, n = P.n, c = P.c, h0 = P.h0;
-  const int T = 1 << t;
-  const int nst = P.nstage;
-  C* buf = reinterpret_cast<C*>(smraw);  // [nst][NS][T]
-  R* sco = reinterpret_cast<R*>(buf + nst * NS * T);
-  double* sred = reinterpret_cast<double*>(sco + ((P.ncoef + 1) & ~1));  // [kWarps][nslots]
-  R* sdef = reinterpret_cast<R*>(sred + kWarps * (P.nslots > 0 ? P.nslots : 1));  // [ncomp][kThreads]
-
-  const long long tps = 1LL << (n - t);
-  const int b = blockIdx.x / cps;
-  const int r0 = blockIdx.x % cps;
-  const int m = t - c, gap = h0 - c;
-  const int cmask = (1 << c) - 1;
-  const long long sb = (long long)b << n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int sw_tid = tswz<R>(threadIdx.x), sw_tid2 = tswz<R>(2 * threadIdx.x);
-
-  for (int k = 0; k < P.nops; ++k) {
-    const TileOp& o = P.ops[k];
-    const R* s = coef + o.coef + (long long)b * o.bstride;
-    for (int i = threadIdx.x; i < o.nco; i += kThreads) sco[o.soff + i] = s[i];
-  }
-  if (NS == 2) {
-    for (int i = threadIdx.x; i < kWarps * P.nslots; i += kThreads) sred[i] = 0;
-    if (P.defer)
-      for (int s = 0; s < P.ncomp; ++s) sdef[s * kThreads + threadIdx.x] = 0;
-  }
-
-  R acct[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acct[r][i] = 0;
-
-  // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
-  // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
-  // bits [0, c) and [h0, h0 + m).
-  const C* s0b = src0 + sb;
-  const C* s1b = NS == 2 ? src1 + sb : nullptr;
-  C* d0b = dst0 + sb;
-  C* d1b = NS == 2 ? dst1 + sb : nullptr;
-  auto tile_base = [&](long long f) -> int {
-    return (int)(((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
-  };
-  auto elem_off = [&](int i) -> int { return (i & cmask) | ((i >> c) << h0); };
-  auto issue = [&](long long f, int slot) {
-    const int base = tile_base(f);
-    C* d0 = buf + slot * NS * T;
-    for (int i = threadIdx.x, si = sw_tid; i < T; i += kThreads, si += kThreads) {
-      int gi = base | elem_off(i);
-      if (P.gather) gi = ring_finv32(gi, n);
-      cp_async_elem<sizeof(C)>(&d0[si], &s0b[gi]);
-      if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + si], &s1b[gi]);
-    }
-  };
-
-  long long f = r0;
-  int slot = 0;
-  for (int j = 0; j + 1 < nst; ++j) {
-    if (f + (long long)j * cps < tps) issue(f + (long long)j * cps, j);
-    cp_async_commit();
-  }
-  for (; f < tps; f += cps) {
-    // every iteration commits one group (possibly empty), so the group of
-    // tile f is complete once at most nst - 1 newer groups are pending
-    const long long fn = f + (long long)(nst - 1) * cps;
-    const int sn = slot + nst - 1 < nst ? slot + nst - 1 : slot - 1;
-    if (fn < tps) issue(fn, sn);
-    cp_async_commit();
-    if (nst == 3) cp_async_wait_group<2>();
-    else cp_async_wait_group<1>();
-    __syncthreads();
-    C* S0 = buf + (long long)slot * NS * T;
-    C* S1 = S0 + T;
-    if (NS == 1 && P.pre) {
-      const int base = tile_base(f);
-      const R* tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
-      for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-        const long long k = base | elem_off(i);
-        S0[pi] = cmul<R>(diag_phase<R>(tabs, P.pre_tb, ztrans(k, n, P.pre_zmode)), S0[pi]);
-      }
-      __syncthreads();
-    }
-
-#pragma unroll 1
-    for (int r = 0; r < P.nrounds; ++r) {
-      const int lo = P.rlo[r];
-      R acc[RB * 3];
-#pragma unroll
-      for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
-      // address of register element a = pb ^ (XOR of basis[j] over set bits j of a)
-      int basis[RB];
-#pragma unroll
-      for (int j = 0; j < RB; ++j) basis[j] = tswz<R>(1 << (lo + j));
-      for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
-        const int pb = tswz<R>((g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB)));
-        C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
-#pragma unroll
-        for (int a = 0; a < (1 << RB); ++a) {
-          int ad = pb;
-#pragma unroll
-          for (int j = 0; j < RB; ++j)
-            if (a & (1 << j)) ad ^= basis[j];
-          v0[a] = S0[ad];
-          if (NS == 2) v1[a] = S1[ad];
-        }
-        tile_bit<R, NS, RB, KIND, 0>(P, r, v0, v1, sco, acc);
-        if (RB > 1) tile_bit<R, NS, RB, KIND, (RB > 1 ? 1 : 0)>(P, r, v0, v1, sco, acc);
-        if (RB > 2) tile_bit<R, NS, RB, KIND, (RB > 2 ? 2 : 0)>(P, r, v0, v1, sco, acc);
-        if (RB > 3) tile_bit<R, NS, RB, KIND, (RB > 3 ? 3 : 0)>(P, r, v0, v1, sco, acc);
-#pragma unroll
-        for (int a = 0; a < (1 << RB); ++a) {
-          int ad = pb;
-#pragma unroll
-          for (int j = 0; j < RB; ++j)
-            if (a & (1 << j)) ad ^= basis[j];
-          S0[ad] = v0[a];
-          if (NS == 2) S1[ad] = v1[a];
-        }
-      }
-      if (NS == 2) {
-        if (P.defer) {
-          // keep per-thread sums across tiles, reduced once after the last
-          // tile: the pass's own slots in registers, companion slots in this
-          // thread's column of shared memory
-#pragma unroll
-          for (int rr = 0; rr < 4; ++rr)
-            if (rr == r) {
-#pragma unroll
-              for (int i = 0; i < (RB < 4 ? RB : 4); ++i) acct[rr][i] += acc[i * 3];
-            }
-          if (P.ncomp) {
-#pragma unroll
-            for (int i = 0; i < (RB < 4 ? RB : 4); ++i) {
-              const int cs = P.rcslot[r][i];
-              if (cs >= 0) sdef[(cs - P.nslots + P.ncomp) * kThreads + threadIdx.x] += acc[i * 3 + 1];
-            }
-          }
-        } else {
-          // per op of the round, by its (lower) register bit: every acc index
-          // is a compile-time constant, so acc stays in registers
-#pragma unroll
-          for (int i = 0; i < RB; ++i) {
-            const int k = P.rbit[r][i];
-            if (k < 0) continue;
-            const TileOp& o = P.ops[k];
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-              if (q < o.np) {
-                const double v = warp_sum((double)acc[i * 3 + q]);
-                if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
-              }
-            if (o.ck) {
-              const double v = warp_sum((double)acc[i * 3 + 1]);
-              if (lane == 0) sred[warp * P.nslots + o.cslot] += v;
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-
-    if (P.store) {
-      const int base = tile_base(f);
-      if (P.post || P.scatter) {
-        const R* tabs = coef + P.post_coef + (long long)b * P.post_bstride;
-        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-          const int kl = base | elem_off(i);
-          C e = S0[pi];
-          if (NS == 1 && P.post) e = cmul<R>(diag_phase<R>(tabs, P.post_tb, ztrans(kl, n, P.post_zmode)), e);
-          const int gd = P.scatter ? ring_finv32(kl, n) : kl;
-          d0b[gd] = e;
-          if (NS == 2) d1b[gd] = S1[pi];
-        }
-      } else if (sizeof(C) == 8) {
-        for (int i = 2 * threadIdx.x, pi = sw_tid2; i < T; i += 2 * kThreads, pi += 2 * kThreads) {
-          const int gi = base | elem_off(i);
-          C e0 = S0[pi], e1 = S0[pi ^ 1];
-          *reinterpret_cast<float4*>(&d0b[gi]) = make_float4(e0.x, e0.y, e1.x, e1.y);
-          if (NS == 2) {
-            C u0 = S1[pi], u1 = S1[pi ^ 1];
-            *reinterpret_cast<float4*>(&d1b[gi]) = make_float4(u0.x, u0.y, u1.x, u1.y);
-          }
-        }
-      } else {
-        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-          const int gi = base | elem_off(i);
-          d0b[gi] = S0[pi];
-          if (NS == 2) d1b[gi] = S1[pi];
-        }
-      }
-    }
-    __syncthreads();
-    slot = slot + 1 == nst ? 0 : slot + 1;
-  }
-  cp_async_wait_group<0>();
-  if (NS == 2 && P.defer) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int sl = P.rslot[r][i];
-        if (sl >= 0) {
-          const double v = warp_sum((double)acct[r][i]);
-          if (lane == 0) sred[warp * P.nslots + sl] += v;
-        }
-      }
-    for (int s = 0; s < P.ncomp; ++s) {
-      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
-      if (lane == 0) sred[warp * P.nslots + P.nslots - P.ncomp + s] += v;
-    }
-  }
-  if (NS == 2 && P.nslots > 0) {
-    __syncthreads();
-    for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
-      double v = 0;
-      for (int w = 0; w < kWarps; ++w) v += sred[w * P.nslots + s];
-      part[(long long)s * gridDim.x + blockIdx.x] = v;
-    }
   }
 }
 
@@ -1608,60 +983,14 @@ cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi,
   return cudaGetLastError();
 }
 
-size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) {
-  size_t s = (size_t)P.nstage * ns * ((size_t)1 << P.t) * 2 * rsize;
-  s += (size_t)((P.ncoef + 1) & ~1) * rsize;
-  s += (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double);
-  if (ns == 2 && P.defer) s += (size_t)P.ncomp * kThreads * rsize;
-  return s;
-}
-
-template <class R, int NS, int RB, int KIND>
-static cudaError_t launch_tile_k(const TilePass& P, int batch, int cps, const void* coef,
-                                 const void* s0, void* d0, const void* s1, void* d1, double* part,
-                                 cudaStream_t st) {
-  size_t smem = tile_smem_bytes(P, NS, sizeof(R));
-  auto kern = k_tile<R, NS, RB, KIND>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  long long grid = (long long)batch * cps;
-  kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const R*)coef, (const cx<R>*)s0, (cx<R>*)d0,
-                                               (const cx<R>*)s1, (cx<R>*)d1, part, cps);
-  return cudaGetLastError();
-}
-
-template <class R, int NS, int RB>
-static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const void* coef,
-                                  const void* s0, void* d0, const void* s1, void* d1, double* part,
-                                  cudaStream_t st) {
-  switch (P.kind) {
-    case 0: return launch_tile_k<R, NS, RB, 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-    case 1: return launch_tile_k<R, NS, RB, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-    case 2: return launch_tile_k<R, NS, RB, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-  }
-  return cudaErrorInvalidValue;
-}
+size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) { return tile_smem_layout(P, ns, rsize).end; }
 
 template <class R>
 cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, const void* coef,
                         const void* s0, void* d0, const void* s1, void* d1, double* part,
                         cudaStream_t st) {
-  if (ns == 1) {
-    switch (rb) {
-      case 1: return launch_tile_rb<R, 1, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-      case 2: return launch_tile_rb<R, 1, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-      case 3: return launch_tile_rb<R, 1, 3>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-      case 4: return launch_tile_rb<R, 1, 4>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-    }
-  } else {
-    switch (rb) {
-      case 1: return launch_tile_rb<R, 2, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-      case 2: return launch_tile_rb<R, 2, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-      case 3: return launch_tile_rb<R, 2, 3>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-      case 4: return launch_tile_rb<R, 2, 4>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-    }
-  }
-  return cudaErrorInvalidValue;
+  if (ns == 1) return launch_tile_fwd<R>(P, rb, batch, cps, coef, s0, d0, s1, d1, part, st);
+  return launch_tile_bwd<R>(P, rb, batch, cps, coef, s0, d0, s1, d1, part, st);
 }
 
 long long diag_grid(const DiagPass& P, int batch) {

@@ -39,6 +39,15 @@ template <class R>
 cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, const void* coef,
                         const void* s0, void* d0, const void* s1, void* d1, double* part,
                         cudaStream_t st);
+// the two sweeps' tile instantiations (qc_tile_fwd.cu, qc_tile_bwd.cu)
+template <class R>
+cudaError_t launch_tile_fwd(const TilePass& P, int rb, int batch, int cps, const void* coef,
+                            const void* s0, void* d0, const void* s1, void* d1, double* part,
+                            cudaStream_t st);
+template <class R>
+cudaError_t launch_tile_bwd(const TilePass& P, int rb, int batch, int cps, const void* coef,
+                            const void* s0, void* d0, const void* s1, void* d1, double* part,
+                            cudaStream_t st);
 template <class R>
 cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, const void* s0,
                         void* d0, const void* s1, void* d1, double* part, cudaStream_t st);

@@ -1,0 +1,687 @@
+// Tile pass: the persistent kernel that applies (forward) or undoes with
+// gradients (backward) the gates of one layer on a tile of 2^t amplitudes
+// staged in shared memory, and its launch templates.  Instantiated by
+// qc_tile_fwd.cu (NS = 1) and qc_tile_bwd.cu (NS = 2).
+#pragma once
+#include "qc_device.cuh"
+#include "qc_kernels.h"
+
+namespace qc {
+
+// ---------------------------------------------------------------------------
+// Tile pass: register-blocked single-qubit and two-qubit gate ops
+// ---------------------------------------------------------------------------
+
+// forward single-qubit op on register bit I
+// `m` is the staged record: the packed real matrix for a real op, else M
+// (2x2 complex) followed, backward, by A = M^dagger dM.
+template <class R, int RB, int I>
+__device__ __forceinline__ void ap1(cx<R>* v, const R* m, int real) {
+  using C = cx<R>;
+  if (real) {
+    R m00, m01, m10, m11;
+    ld4<R>(m, m00, m01, m10, m11);
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        C x0 = v[a], x1 = v[a | (1 << I)];
+        v[a] = rfma<R>(m01, x1, rmul<R>(m00, x0));
+        v[a | (1 << I)] = rfma<R>(m11, x1, rmul<R>(m10, x0));
+      }
+  } else {
+    C m00, m01, m10, m11;
+    ldc2<R>(m, m00, m01);
+    ldc2<R>(m + 4, m10, m11);
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        C x0 = v[a], x1 = v[a | (1 << I)];
+        v[a] = cfma<R>(m01, x1, cmul<R>(m00, x0));
+        v[a | (1 << I)] = cfma<R>(m11, x1, cmul<R>(m10, x0));
+      }
+  }
+}
+
+// 2 Re <l|(-i/2 G)|p> on one amplitude pair, G = X (ck 1) or Y (ck 2):
+// Im(l0* p1 + l1* p0) and Re(l1* p0) - Re(l0* p1).
+template <class R>
+__device__ __forceinline__ R pauli_grad(int ck, cx<R> w0, cx<R> w1, cx<R> y0, cx<R> y1) {
+  if (ck == 1) return im_cdot<R>(w0, y1) + im_cdot<R>(w1, y0);
+  return re_cdot<R>(w1, y0) - re_cdot<R>(w0, y1);
+}
+
+// backward single-qubit op: undo M on psi and lambda, then accumulate
+// 2 Re <lambda| A |psi> on the gate's input side into acc[3 I].  With a
+// companion generator ck, also the gradient of the preceding layer's RX / RY
+// gate on the same qubit into acc[3 I + 1]: its generator commutes with that
+// gate, so the pair just undone (that layer's output side) gives it.
+template <class R, int RB, int I>
+__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, int ck,
+                                    R* acc) {
+  using C = cx<R>;
+  if (real) {
+    // RY (the only real gate; m is its packed real matrix): undo with M^T;
+    // 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
+    R m00, m01, m10, m11;
+    ld4<R>(m, m00, m01, m10, m11);
+    C ga = mk<R>(0, 0), gb = mk<R>(0, 0);
+    if (ck == 1) {
+      // companion RX: Im(l0* p1 + l1* p0), packed as l * swap(p)
+      C hc = mk<R>(0, 0);
+#pragma unroll
+      for (int a = 0; a < (1 << RB); ++a)
+        if (!(a & (1 << I))) {
+          const int a1 = a | (1 << I);
+          C x0 = p[a], x1 = p[a1];
+          C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
+          C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
+          p[a] = y0; p[a1] = y1;
+          C u0 = l[a], u1 = l[a1];
+          C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
+          C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
+          l[a] = w0; l[a1] = w1;
+          ga = pfma<R>(w1, y0, ga);
+          gb = pfma<R>(w0, y1, gb);
+          hc = pfma<R>(w0, mk<R>(y1.y, y1.x), hc);
+          hc = pfma<R>(w1, mk<R>(y0.y, y0.x), hc);
+        }
+      acc[I * 3 + 1] += hc.x - hc.y;
+    } else {
+#pragma unroll
+      for (int a = 0; a < (1 << RB); ++a)
+        if (!(a & (1 << I))) {
+          const int a1 = a | (1 << I);
+          C x0 = p[a], x1 = p[a1];
+          C y0 = rfma<R>(m10, x1, rmul<R>(m00, x0));
+          C y1 = rfma<R>(m11, x1, rmul<R>(m01, x0));
+          p[a] = y0; p[a1] = y1;
+          C u0 = l[a], u1 = l[a1];
+          C w0 = rfma<R>(m10, u1, rmul<R>(m00, u0));
+          C w1 = rfma<R>(m11, u1, rmul<R>(m01, u0));
+          l[a] = w0; l[a1] = w1;
+          ga = pfma<R>(w1, y0, ga);
+          gb = pfma<R>(w0, y1, gb);
+          if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
+        }
+    }
+    if (np) acc[I * 3] += (ga.x + ga.y) - (gb.x + gb.y);
+    return;
+  }
+  {
+    C m00, m01, m10, m11, a00, a01, a10, a11;
+    ldc2<R>(m, m00, m01);
+    ldc2<R>(m + 4, m10, m11);
+    if (np && gk != 1) {
+      ldc2<R>(m + 8, a00, a01);
+      ldc2<R>(m + 12, a10, a11);
+    }
+    R g = 0;
+#pragma unroll
+    for (int a = 0; a < (1 << RB); ++a)
+      if (!(a & (1 << I))) {
+        const int a1 = a | (1 << I);
+        C x0 = p[a], x1 = p[a1];
+        // y = M^dagger x: y0 = conj(m00) x0 + conj(m10) x1; y1 = conj(m01) x0 + conj(m11) x1
+        C y0 = cfmac<R>(m10, x1, cfmac<R>(m00, x0, mk<R>(0, 0)));
+        C y1 = cfmac<R>(m11, x1, cfmac<R>(m01, x0, mk<R>(0, 0)));
+        p[a] = y0; p[a1] = y1;
+        C u0 = l[a], u1 = l[a1];
+        C w0 = cfmac<R>(m10, u1, cfmac<R>(m00, u0, mk<R>(0, 0)));
+        C w1 = cfmac<R>(m11, u1, cfmac<R>(m01, u0, mk<R>(0, 0)));
+        l[a] = w0; l[a1] = w1;
+        if (np) {
+          if (gk == 1) {
+            // RX: 2 Re <l|(-i/2 X)|p> = Im(l0* p1 + l1* p0)
+            g += im_cdot<R>(w0, y1) + im_cdot<R>(w1, y0);
+          } else {
+            C t0 = cfma<R>(a01, y1, cmul<R>(a00, y0));
+            C t1 = cfma<R>(a11, y1, cmul<R>(a10, y0));
+            g += 2 * (re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1));
+          }
+        }
+        if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
+      }
+    if (np) acc[I * 3] += g;
+  }
+}
+
+// forward two-qubit op on register bits (I, I+1); 4x4 index = 2*bit(I+1) + bit(I)
+template <class R, int RB, int I>
+__device__ __forceinline__ void ap2(cx<R>* v, const R* m) {
+  using C = cx<R>;
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (3 << I))) {
+      C x[4], y[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) x[s] = v[a | (s << I)];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        C t = mk<R>(0, 0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(m + 2 * (r * 4 + s)), x[s], t);
+        y[r] = t;
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) v[a | (s << I)] = y[s];
+    }
+}
+
+template <class R, int RB, int I>
+__device__ __forceinline__ void bw2(cx<R>* p, cx<R>* l, const R* m, int np, R* acc) {
+  using C = cx<R>;
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (3 << I))) {
+      C x[4], u[4], y[4], w[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) { x[s] = p[a | (s << I)]; u[s] = l[a | (s << I)]; }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        C t = mk<R>(0, 0), z = mk<R>(0, 0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          C ms = ldc<R>(m + 2 * (s * 4 + r));  // (M^dagger)[r][s] = conj(M[s][r])
+          t = cfmac<R>(ms, x[s], t);
+          z = cfmac<R>(ms, u[s], z);
+        }
+        y[r] = t; w[r] = z;
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) { p[a | (s << I)] = y[s]; l[a | (s << I)] = w[s]; }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {  // compile-time acc index (np <= 3)
+        if (k >= np) break;
+        const R* A = m + 32 + 32 * k;
+        R g = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          C t = mk<R>(0, 0);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(A + 2 * (r * 4 + s)), y[s], t);
+          g += re_cdot<R>(w[r], t);
+        }
+        acc[I * 3 + k] += 2 * g;
+      }
+    }
+}
+
+// Applies the round's op on register bit I (if any).  KIND is uniform over a
+// pass: 0 complex single-qubit, 1 real single-qubit, 2 two-qubit on (I, I+1).
+template <class R, int NS, int RB, int KIND, int I>
+__device__ __forceinline__ void tile_bit(const TilePass& P, int r, cx<R>* v0, cx<R>* v1,
+                                         const R* sco, R* acc) {
+  if (KIND == 2 && I + 1 >= RB) return;
+  const int k = P.rbit[r][I];
+  if (k < 0) return;
+  const TileOp& o = P.ops[k];
+  const R* mc = sco + o.soff;
+  if (NS == 1) {
+    if (KIND == 2) ap2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, mc);
+    else ap1<R, RB, I>(v0, mc, KIND == 1);
+  } else {
+    if (KIND == 2) bw2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, v1, mc, o.np, acc);
+    else bw1<R, RB, I>(v0, v1, mc, KIND == 1, o.np, o.gk, o.ck, acc);
+  }
+}
+
+// Tile-pass shared-memory layout: an XOR swizzle that folds index bits 4..7
+// (8-byte elements: complex64 forward, 16 per 128-byte wavefront) or 3..6
+// (16-byte elements: complex128, or an interleaved complex64 (psi, lambda)
+// pair; 8 per wavefront) into the bank bits, with
+// fold columns (15, 10, 12, 8) and (7, 5, 6, 4) packed as nibble tables.
+// With these columns every round's accesses (register bits [lo, lo + RB) for
+// any lo and RB <= 4), the copy loop and the paired complex64 store hit
+// distinct banks; an exhaustive host-side count of wavefronts fixed them (the
+// plain fold of bits 4..7 onto bits 0..3 is 2-way conflicted at lo = 3,
+// RB = 3).  The map is linear over GF(2), so the address of (base | a << lo)
+// is swz(base) ^ swz(a << lo), and it leaves bits >= 8 alone, so
+// swz(i + k * 256) = swz(i) + k * 256.
+template <int EB>
+__device__ __forceinline__ int tswz(int i) {
+  if constexpr (EB == 8)
+    return i ^ (int)((0x1eb4d278963c5af0ull >> (4 * ((i >> 4) & 15))) & 15);
+  else
+    return i ^ (int)((0x0752613443162570ull >> (4 * ((i >> 3) & 15))) & 15);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Persistent tile pass.  CTA (b, r) of the cps CTAs of sample b handles tiles
+// f = r, r + cps, ... of that sample through a ring of P.nstage shared-memory
+// buffers: the next nstage - 1 tiles are in flight while one is processed.
+// NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
+// lambda, accumulate gradient partials into part[slot][block]).
+// PRE = 1: backward pass with a diagonal layer undone in round 0 (P.pre).
+template <class R, int NS, int RB, int KIND, int PRE>
+__global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB)) k_tile(const __grid_constant__ TilePass P,
+                                                      const R* __restrict__ coef,
+                                                      const cx<R>* src0, cx<R>* dst0,
+                                                      const cx<R>* src1, cx<R>* dst1,
+                                                      double* __restrict__ part, int cps) {
+  using C = cx<R>;
+  // complex64 backward: psi and lambda of one index side by side (one 16-byte
+  // element), so a round moves both with one 16-byte shared access
+  constexpr bool IL = NS == 2 && sizeof(R) == 4;
+  constexpr int EB = (IL || sizeof(C) == 16) ? 16 : 8;  // shared-memory element bytes
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = P.t, n = P.n, c = P.c, h0 = P.h0;
+  const int T = 1 << t;
+  const int nst = P.nstage;
+  const TileSmem lay = tile_smem_layout(P, NS, (int)sizeof(R));
+  C* buf = reinterpret_cast<C*>(smraw + lay.buf);        // [nst][NS][T], or [nst][T][2] interleaved
+  R* sco = reinterpret_cast<R*>(smraw + lay.sco);
+  double* sred = reinterpret_cast<double*>(smraw + lay.sred);  // [kWarps][nslots]
+  R* sdef = reinterpret_cast<R*>(smraw + lay.sdef);            // [ncomp][kThreads]
+  // backward pre-diagonal: [kWarps][n + 1] marginal sums, then the phase
+  // ratio table over the element-varying z bits
+  double* smarg = reinterpret_cast<double*>(smraw + lay.smarg);
+  C* sratio = reinterpret_cast<C*>(smraw + lay.sratio);
+
+  const long long tps = 1LL << (n - t);
+  const int b = blockIdx.x / cps;
+  const int r0 = blockIdx.x % cps;
+  const int m = t - c, gap = h0 - c;
+  const int cmask = (1 << c) - 1;
+  const long long sb = (long long)b << n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sw_tid = tswz<EB>(threadIdx.x), sw_tid2 = tswz<EB>(2 * threadIdx.x);
+
+  for (int k = 0; k < P.nops; ++k) {
+    const TileOp& o = P.ops[k];
+    const R* s = coef + o.coef + (long long)b * o.bstride;
+    for (int i = threadIdx.x; i < o.nco; i += kThreads) sco[o.soff + i] = s[i];
+  }
+  if (NS == 2) {
+    for (int i = threadIdx.x; i < kWarps * P.nslots; i += kThreads) sred[i] = 0;
+    if (P.defer)
+      for (int s = 0; s < P.ncomp; ++s) sdef[s * kThreads + threadIdx.x] = 0;
+  }
+
+  R acct[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acct[r][i] = 0;
+
+  // Backward pre-diagonal (undo D, gradient from bit marginals of
+  // w = Im(conj(lambda) psi), which D leaves unchanged).  Round 0 holds index
+  // bits 0..RB-1 of element a in register a; z is linear over GF(2), so for
+  // k = base | tid << RB | a:  z = z0 ^ zE(a), z0 = ztrans(base) ^ zT,
+  // zT = ztrans(tid << RB).  zE(a) touches the "element" bits 0..RB-1 (and
+  // n-1 for the ring map, via a_0); its pattern pat(a) indexes sratio, the
+  // product of the per-bit phase ratios d_p[1] / d_p[0].
+  constexpr bool pre_b = NS == 2 && PRE == 1;
+  const bool ringz = P.pre_zmode == Z_RINGXOR;
+  const int zT = pre_b ? ztrans32(threadIdx.x << RB, n, P.pre_zmode) : 0;
+  const R* ptabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
+  // element-varying bits: 0..RB-1, plus n-1 for the ring map
+  const int semask = ((1 << RB) - 1) | (ringz ? (1 << (n - 1)) : 0);
+  // tile-varying bits: the union (not the XOR) of the images of tile bits [t, n)
+  int fmask = 0;
+  if (pre_b)
+    for (int q = t; q < n; ++q) fmask |= ztrans32(1 << q, n, P.pre_zmode);
+  // lane p (< n) keeps the sums of tile-only z bit p
+  const bool lane_f = (((fmask & ~semask) >> lane) & 1) != 0;
+  R mW = 0, mA[4] = {0, 0, 0, 0}, mL = 0;  // W, element-bit sums (bits < RB <= 4), ring bit n-1
+  R mF = 0;                                // lane p: tile-only bit p
+  if (pre_b) {
+    if (threadIdx.x < (2 << RB)) {
+      // pattern bits j < RB <-> z bit j; bit RB <-> z bit n-1 (ring map)
+      C v = mk<R>(1, 0);
+      for (int j = 0; j <= RB; ++j) {
+        if (!((threadIdx.x >> j) & 1)) continue;
+        const int p = j < RB ? j : n - 1;
+        const int sblk = p / P.pre_tb, i = p % P.pre_tb;
+        const R* tb = ptabs + 2LL * sblk * (1LL << P.pre_tb);
+        v = cmul<R>(v, cmulc<R>(ldc<R>(tb), ldc<R>(tb + 2 * (1 << i))));  // T[1 << i] conj(T[0])
+      }
+      sratio[threadIdx.x] = v;
+    }
+  }
+
+  // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
+  // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
+  // bits [0, c) and [h0, h0 + m).
+  const C* s0b = src0 + sb;
+  const C* s1b = NS == 2 ? src1 + sb : nullptr;
+  C* d0b = dst0 + sb;
+  C* d1b = NS == 2 ? dst1 + sb : nullptr;
+  auto tile_base = [&](long long f) -> int {
+    return (int)(((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
+  };
+  auto elem_off = [&](int i) -> int { return (i & cmask) | ((i >> c) << h0); };
+  // interleaved copies: each run of 16 threads moves psi then lambda of 8
+  // consecutive indices (16 distinct bank pairs in shared memory, two 64-byte
+  // segments in global memory)
+  const int il_i = ((threadIdx.x >> 4) << 3) | (threadIdx.x & 7);
+  const int il_s = (threadIdx.x >> 3) & 1;
+  const C* il_src = il_s ? s1b : s0b;
+  const int il_si = 2 * tswz<EB>(il_i) + il_s;
+  auto issue = [&](long long f, int slot) {
+    const int base = tile_base(f);
+    C* d0 = buf + slot * NS * T;
+    if constexpr (IL) {
+      for (int i = il_i, si = il_si; i < T; i += kThreads / 2, si += kThreads) {
+        int gi = base | elem_off(i);
+        if (P.gather) gi = ring_finv32(gi, n);
+        cp_async_elem<sizeof(C)>(&d0[si], &il_src[gi]);
+      }
+    } else {
+      for (int i = threadIdx.x, si = sw_tid; i < T; i += kThreads, si += kThreads) {
+        int gi = base | elem_off(i);
+        if (P.gather) gi = ring_finv32(gi, n);
+        cp_async_elem<sizeof(C)>(&d0[si], &s0b[gi]);
+        if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + si], &s1b[gi]);
+      }
+    }
+  };
+
+  long long f = r0;
+  int slot = 0;
+  for (int j = 0; j + 1 < nst; ++j) {
+    if (f + (long long)j * cps < tps) issue(f + (long long)j * cps, j);
+    cp_async_commit();
+  }
+  for (; f < tps; f += cps) {
+    // every iteration commits one group (possibly empty), so the group of
+    // tile f is complete once at most nst - 1 newer groups are pending
+    const long long fn = f + (long long)(nst - 1) * cps;
+    const int sn = slot + nst - 1 < nst ? slot + nst - 1 : slot - 1;
+    if (fn < tps) issue(fn, sn);
+    cp_async_commit();
+    if (nst == 3) cp_async_wait_group<2>();
+    else cp_async_wait_group<1>();
+    __syncthreads();
+    C* S0 = buf + (long long)slot * NS * T;
+    C* S1 = S0 + T;
+    if (NS == 1 && P.pre) {
+      const int base = tile_base(f);
+      const R* tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
+      for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
+        const long long k = base | elem_off(i);
+        S0[pi] = cmul<R>(diag_phase<R>(tabs, P.pre_tb, ztrans(k, n, P.pre_zmode)), S0[pi]);
+      }
+      __syncthreads();
+    }
+
+#pragma unroll 1
+    for (int r = 0; r < P.nrounds; ++r) {
+      const int lo = P.rlo[r];
+      R acc[RB * 3];
+#pragma unroll
+      for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
+      // address of register element a = pb ^ (XOR of basis[j] over set bits j of a)
+      int basis[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) basis[j] = tswz<EB>(1 << (lo + j));
+      for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
+        const int pb = tswz<EB>((g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB)));
+        C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
+#pragma unroll
+        for (int a = 0; a < (1 << RB); ++a) {
+          int ad = pb;
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            if (a & (1 << j)) ad ^= basis[j];
+          if constexpr (IL) {
+            const float4 q = *reinterpret_cast<const float4*>(&S0[2 * ad]);
+            v0[a] = mk<R>(q.x, q.y);
+            v1[a] = mk<R>(q.z, q.w);
+          } else {
+            v0[a] = S0[ad];
+            if (NS == 2) v1[a] = S1[ad];
+          }
+        }
+        if (pre_b && r == 0) {
+          const int z0 = ztrans32(tile_base(f), n, P.pre_zmode) ^ zT;
+          const C p0 = diag_phase32<R>(ptabs, P.pre_tb, z0 & ~semask);
+          const int z0se = (z0 & ((1 << RB) - 1)) | (ringz ? ((z0 >> (n - 1)) & 1) << RB : 0);
+          R Wt = 0, At[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) {
+            // z bits of element a relative to z0: j < RB: a_j (ident) or
+            // a_j ^ a_{j+1} (ring); bit RB: a_0 (ring: z_{n-1})
+            const int pi = a, pr = (a ^ (a >> 1)) | ((a & 1) << RB);
+            const C ph = cmul<R>(p0, sratio[z0se ^ (ringz ? pr : pi)]);
+            const C y = cmulc<R>(ph, v0[a]), u = cmulc<R>(ph, v1[a]);
+            v0[a] = y;
+            v1[a] = u;
+            const R w = im_cdot<R>(u, y);
+            Wt += w;
+            if (ringz) {
+#pragma unroll
+              for (int j = 0; j <= RB; ++j)
+                if ((pr >> j) & 1) At[j] += w;
+            } else {
+#pragma unroll
+              for (int j = 0; j < RB; ++j)
+                if ((pi >> j) & 1) At[j] += w;
+            }
+          }
+          if (P.pre_grad) {
+            mW += Wt;
+#pragma unroll
+            for (int j = 0; j < RB && j < 4; ++j) mA[j] += At[j];
+            if (ringz) mL += ((z0 >> (n - 1)) & 1) ? Wt - At[RB] : At[RB];
+            // tile-only bits: uniform over the warp; lane p keeps bit p
+            const R sw = warp_sum_r<R>(Wt);
+            if (lane_f && ((z0 >> lane) & 1)) mF += sw;
+          }
+        }
+        tile_bit<R, NS, RB, KIND, 0>(P, r, v0, v1, sco, acc);
+        if (RB > 1) tile_bit<R, NS, RB, KIND, (RB > 1 ? 1 : 0)>(P, r, v0, v1, sco, acc);
+        if (RB > 2) tile_bit<R, NS, RB, KIND, (RB > 2 ? 2 : 0)>(P, r, v0, v1, sco, acc);
+        if (RB > 3) tile_bit<R, NS, RB, KIND, (RB > 3 ? 3 : 0)>(P, r, v0, v1, sco, acc);
+#pragma unroll
+        for (int a = 0; a < (1 << RB); ++a) {
+          int ad = pb;
+#pragma unroll
+          for (int j = 0; j < RB; ++j)
+            if (a & (1 << j)) ad ^= basis[j];
+          if constexpr (IL) {
+            *reinterpret_cast<float4*>(&S0[2 * ad]) = make_float4(v0[a].x, v0[a].y, v1[a].x, v1[a].y);
+          } else {
+            S0[ad] = v0[a];
+            if (NS == 2) S1[ad] = v1[a];
+          }
+        }
+      }
+      if (NS == 2) {
+        if (P.defer) {
+          // keep per-thread sums across tiles, reduced once after the last
+          // tile: the pass's own slots in registers, companion slots in this
+          // thread's column of shared memory
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr)
+            if (rr == r) {
+#pragma unroll
+              for (int i = 0; i < (RB < 4 ? RB : 4); ++i) acct[rr][i] += acc[i * 3];
+            }
+          if (P.ncomp) {
+#pragma unroll
+            for (int i = 0; i < (RB < 4 ? RB : 4); ++i) {
+              const int cs = P.rcslot[r][i];
+              if (cs >= 0) sdef[(cs - P.nslots + P.ncomp) * kThreads + threadIdx.x] += acc[i * 3 + 1];
+            }
+          }
+        } else {
+          // per op of the round, by its (lower) register bit: every acc index
+          // is a compile-time constant, so acc stays in registers
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            const int k = P.rbit[r][i];
+            if (k < 0) continue;
+            const TileOp& o = P.ops[k];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < o.np) {
+                const double v = warp_sum((double)acc[i * 3 + q]);
+                if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
+              }
+            if (o.ck) {
+              const double v = warp_sum((double)acc[i * 3 + 1]);
+              if (lane == 0) sred[warp * P.nslots + o.cslot] += v;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    if (P.store) {
+      const int base = tile_base(f);
+      if (P.post || P.scatter) {
+        const R* tabs = coef + P.post_coef + (long long)b * P.post_bstride;
+        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
+          const int kl = base | elem_off(i);
+          C e = S0[pi];
+          if (NS == 1 && P.post) e = cmul<R>(diag_phase<R>(tabs, P.post_tb, ztrans(kl, n, P.post_zmode)), e);
+          const int gd = P.scatter ? ring_finv32(kl, n) : kl;
+          if constexpr (IL) {
+            d0b[gd] = S0[2 * pi];
+            d1b[gd] = S0[2 * pi + 1];
+          } else {
+            d0b[gd] = e;
+            if (NS == 2) d1b[gd] = S1[pi];
+          }
+        }
+      } else if (sizeof(C) == 8) {
+        for (int i = 2 * threadIdx.x, pi = sw_tid2; i < T; i += 2 * kThreads, pi += 2 * kThreads) {
+          const int gi = base | elem_off(i);
+          if constexpr (IL) {
+            const float4 q0 = *reinterpret_cast<const float4*>(&S0[2 * pi]);
+            const float4 q1 = *reinterpret_cast<const float4*>(&S0[2 * (pi ^ 1)]);
+            *reinterpret_cast<float4*>(&d0b[gi]) = make_float4(q0.x, q0.y, q1.x, q1.y);
+            *reinterpret_cast<float4*>(&d1b[gi]) = make_float4(q0.z, q0.w, q1.z, q1.w);
+          } else {
+            C e0 = S0[pi], e1 = S0[pi ^ 1];
+            *reinterpret_cast<float4*>(&d0b[gi]) = make_float4(e0.x, e0.y, e1.x, e1.y);
+            if (NS == 2) {
+              C u0 = S1[pi], u1 = S1[pi ^ 1];
+              *reinterpret_cast<float4*>(&d1b[gi]) = make_float4(u0.x, u0.y, u1.x, u1.y);
+            }
+          }
+        }
+      } else {
+        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
+          const int gi = base | elem_off(i);
+          d0b[gi] = S0[pi];
+          if (NS == 2) d1b[gi] = S1[pi];
+        }
+      }
+    }
+    __syncthreads();
+    slot = slot + 1 == nst ? 0 : slot + 1;
+  }
+  cp_async_wait_group<0>();
+  if (NS == 2 && P.defer) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int sl = P.rslot[r][i];
+        if (sl >= 0) {
+          const double v = warp_sum((double)acct[r][i]);
+          if (lane == 0) sred[warp * P.nslots + sl] += v;
+        }
+      }
+    for (int s = 0; s < P.ncomp; ++s) {
+      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
+      if (lane == 0) sred[warp * P.nslots + P.nslots - P.ncomp + s] += v;
+    }
+  }
+  if (NS == 2 && P.nslots > 0) {
+    __syncthreads();
+    for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
+      double v = 0;
+      for (int w = 0; w < kWarps; ++w) v += sred[w * P.nslots + s];
+      part[(long long)s * gridDim.x + blockIdx.x] = v;
+    }
+  }
+  if (pre_b && P.pre_grad) {
+    // per thread u_p = sum over its elements of w * z_p; the element bits and
+    // thread-constant bits from the tile-invariant sums, n-1 (ring) from mL,
+    // tile-only bits from the lane accumulators
+    const double wsum = warp_sum((double)mW);
+    if (lane == 0) smarg[warp * (n + 1)] = wsum;
+    for (int p = 0; p < n; ++p) {
+      R u;
+      const int zt = (zT >> p) & 1;
+      if (p < RB) {
+        R ap = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j == p) ap = mA[j];  // compile-time index: mA stays in registers
+        u = zt ? mW - ap : ap;
+      } else if (ringz && p == n - 1) {
+        u = mL;
+      } else if ((fmask >> p) & 1) {
+        u = 0;
+      } else {
+        u = zt ? mW : (R)0;
+      }
+      double v = warp_sum((double)u);
+      v += (double)__shfl_sync(0xffffffffu, mF, p);
+      if (lane == 0) smarg[warp * (n + 1) + 1 + p] = v;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v <= n; v += kThreads) {
+      double s = 0;
+      for (int w = 0; w < kWarps; ++w) s += smarg[w * (n + 1) + v];
+      part[P.pre_moff + (long long)v * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+template <class R, int NS, int RB, int KIND, int PRE>
+static cudaError_t launch_tile_k(const TilePass& P, int batch, int cps, const void* coef,
+                                 const void* s0, void* d0, const void* s1, void* d1, double* part,
+                                 cudaStream_t st) {
+  size_t smem = tile_smem_bytes(P, NS, sizeof(R));
+  auto kern = k_tile<R, NS, RB, KIND, PRE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  long long grid = (long long)batch * cps;
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const R*)coef, (const cx<R>*)s0, (cx<R>*)d0,
+                                               (const cx<R>*)s1, (cx<R>*)d1, part, cps);
+  return cudaGetLastError();
+}
+
+template <class R, int NS, int RB>
+static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const void* coef,
+                                  const void* s0, void* d0, const void* s1, void* d1, double* part,
+                                  cudaStream_t st) {
+  // the pre-diagonal variant exists for backward single-qubit passes with
+  // RB = 3 or 4 (the planner only fuses those)
+  // (a forward pass's P.pre is the plain phase multiply inside PRE = 0)
+  constexpr bool kPre = NS == 2 && (RB == 3 || RB == 4);
+  if (NS == 2 && P.pre) {
+    if (!kPre || P.kind == 2) return cudaErrorInvalidValue;
+    switch (P.kind) {
+      case 0: return launch_tile_k<R, NS, RB, 0, kPre ? 1 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 1: return launch_tile_k<R, NS, RB, 1, kPre ? 1 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+  switch (P.kind) {
+    case 0: return launch_tile_k<R, NS, RB, 0, 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+    case 1: return launch_tile_k<R, NS, RB, 1, 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+    case 2: return launch_tile_k<R, NS, RB, 2, 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace qc

@@ -220,6 +220,24 @@ def test_leading_rotation_layer_folds_into_the_next_backward_layer(q):
     assert "+X" not in mid and any(l.startswith("B layer=1 TILE") for l in mid.splitlines())
 
 
+def test_backward_diagonal_layers_ride_in_the_next_tile_pass(q):
+    """zz26 backward: each IsingZZ ring layer is undone (and differentiated)
+    in round 0 of the next RY layer's contiguous pass, so no standalone
+    diagonal pass is left; without fusion every one is its own pass."""
+    cfg = W.WORKLOADS["zz26"]
+    desc, _ = _plan(q, 26, cfg["layers"](), batch=8, path=0)
+    bwd = [l for l in desc.splitlines() if l.startswith("B ")]
+    assert not any(" DIAG " in l for l in bwd)
+    pre = [l for l in bwd if "pre=1" in l]
+    assert len(pre) == 12
+    for l in pre:
+        d = dict(re.findall(r"(\w+)=(-?\d+)", l.split("[")[0]))
+        assert d["c"] == d["t"] and int(d["t"]) - int(d["rb"]) <= 8
+    plain, _ = _plan(q, 26, cfg["layers"](), batch=8, path=0, fuse=0)
+    assert sum(" DIAG " in l for l in plain.splitlines() if l.startswith("B ")) == 12
+    assert "pre=1" not in plain
+
+
 def test_small_circuits_use_shared_memory_path(q):
     for name in ("hea4", "hea12", "hea12_c128"):
         cfg = W.WORKLOADS[name]
