@@ -199,13 +199,22 @@ int sm_count() {
   return cached;
 }
 
-// CTAs per sample of a persistent tile pass: two resident CTAs per SM.
-int tile_cps(int batch, int n, int t) {
+// CTAs per sample of a persistent tile pass: as many as the SMs hold at the
+// pass's residency (its compiled CTAs per SM, fewer if its shared memory does
+// not fit that many).
+int tile_cps(int batch, int n, int t, int resident) {
   const long long tps = 1LL << (n - t);
-  long long c = (2LL * sm_count() + batch - 1) / batch;
+  long long c = ((long long)resident * sm_count() + batch - 1) / batch;
   if (c > tps) c = tps;
   if (c < 1) c = 1;
   return (int)c;
+}
+int pass_cps(const qc_circuit* c, int batch, const TilePass& tp, int ns) {
+  const int rs = (int)c->rsize;
+  int res = tile_resident(rs, tp.kind, ns, ns == 2 && tp.pre);
+  const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
+  while (res > 1 && (size_t)res * (tile_smem_bytes(tp, ns, rs) + per_cta_reserved) > per_sm) --res;
+  return tile_cps(batch, c->n, tp.t, res);
 }
 int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 // Register bits per round: the backward holds two states, so it takes one
@@ -540,7 +549,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       for (auto& tp : plan_tile_layer(c, Li, ns, pslots, comp)) {
         Step st;
         st.type = ST_TILE; st.ns = ns; st.tp = tp; st.rb = std::min(reg_bits(c, ns), tp.t);
-        st.cps = tile_cps(batch, n, tp.t);
+        st.cps = pass_cps(c, batch, tp, ns);
         v.push_back(st);
       }
       return v;
@@ -630,6 +639,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
               tp.pre_coef = Li.coef_off;
               tp.pre_bstride = Li.coef_bstride;
               tp.pre_grad = (Li.diff && Li.nparams > 0) ? 1 : 0;
+              f0.cps = pass_cps(c, batch, tp, 2);  // the pre variant holds fewer CTAs
               h.pre_layer = i;
               i = h.lo - 1;
               bgroups.push_back(std::move(h));

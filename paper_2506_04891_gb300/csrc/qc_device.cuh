@@ -10,12 +10,17 @@
 
 #include "qc_internal.h"
 
-// resident CTAs per SM the tile passes are compiled for
+// resident CTAs per SM the tile passes are compiled for: the complex64
+// forward pass of real single-qubit gates (RY) fits three (80 registers, no
+// spills), the others two (a three-CTA backward spills and measured slower)
 #ifndef QC_BWD_MINB
 #define QC_BWD_MINB 2
 #endif
 #ifndef QC_FWD_MINB
 #define QC_FWD_MINB 2
+#endif
+#ifndef QC_REAL_MINB
+#define QC_REAL_MINB 3
 #endif
 
 namespace qc {

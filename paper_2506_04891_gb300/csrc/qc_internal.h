@@ -108,6 +108,12 @@ struct TilePass {
   TileOp ops[kMaxTileOps];
 };
 
+// Resident CTAs per SM a tile pass is compiled for (see the launch bounds of
+// the tile kernel): the complex64 real-gate forward pass 3, others 2.
+inline int tile_resident(int rsize, int kind, int ns, int pre) {
+  return (rsize == 4 && kind == 1 && ns == 1 && !pre) ? 3 : 2;
+}
+
 // Shared-memory carve-out of a tile pass, in bytes from the dynamic base, used
 // by the kernel and by the launch size alike: tile buffers, staged
 // coefficients, per-warp gradient sums, per-thread deferred companion sums

@@ -265,8 +265,11 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials into part[slot][block]).
 // PRE = 1: backward pass with a diagonal layer undone in round 0 (P.pre).
+constexpr int tile_minb(int rsize, int ns, int kind, int pre) {
+  return (rsize == 4 && kind == 1 && ns == 1 && pre == 0) ? QC_REAL_MINB : (ns == 2 ? QC_BWD_MINB : QC_FWD_MINB);
+}
 template <class R, int NS, int RB, int KIND, int PRE>
-__global__ void __launch_bounds__(kThreads, (NS == 2 ? QC_BWD_MINB : QC_FWD_MINB)) k_tile(const __grid_constant__ TilePass P,
+__global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE)) k_tile(const __grid_constant__ TilePass P,
                                                       const R* __restrict__ coef,
                                                       const cx<R>* src0, cx<R>* dst0,
                                                       const cx<R>* src1, cx<R>* dst1,
