@@ -86,7 +86,15 @@ typedef enum {
   QC_L_GPI = 7,           /* anti-diagonal (Sec. 2.4.1, GPI mapping) */
   QC_L_GPI2 = 8,          /* IonQ native single-qubit gate */
   QC_L_MS_BRICK = 9,      /* IonQ native two-qubit gate on a brick pattern */
-  QC_L_ECR_BRICK = 10     /* IBM native two-qubit gate on a brick pattern */
+  QC_L_ECR_BRICK = 10,    /* IBM native two-qubit gate on a brick pattern */
+  QC_L_Z = 11,            /* diagonal constants on every qubit (Appendix A, (anti)diagonal) */
+  QC_L_S = 12,
+  QC_L_H = 13,            /* fixed gate (Appendix A, fixed gates) */
+  QC_L_CZ_BRICK = 14,     /* diagonal two-qubit constant on a brick pattern */
+  QC_L_SWAP_BRICK = 15,   /* permutation two-qubit constant on a brick pattern */
+  QC_L_ROT = 16           /* Rot(theta, phi, lambda) as printed in Appendix A: three
+                             parameters per qubit, qubit j reads offset + 3j + {0, 1, 2};
+                             run as e^{i(phi+lambda)/2} RZ(phi) RY(theta) RZ(lambda) */
 } qc_layer_kind;
 
 typedef enum { QC_SRC_NONE = 0, QC_SRC_THETA = 1, QC_SRC_INPUT = 2 } qc_source;

@@ -28,11 +28,14 @@ Layer description (shared plain structure, no arithmetic): a tuple
 
 Parameters per layer:
 * RX, RY, RZ, GPI, GPI2: n (parameter j acts on qubit j);
+* ROT: 3n, qubit j reads (theta, phi, lambda) = parameters 3j, 3j+1, 3j+2 of the
+  matrix Rot(theta, phi, lambda) printed in Appendix A;
 * ISINGZZ_RING: n (parameter j acts on the pair (j, (j+1) mod n), Sec. 2.4.1
   formula for K_Rzz; for n = 2 this is the same pair twice);
 * MS_BRICK: 3 per gate (phi0, phi1, theta), gate i on qubits
   (parity + 2i, parity + 2i + 1), no wrap-around;
-* CNOT_RING, X, SX, ECR_BRICK: none.
+* CNOT_RING, X, SX, ECR_BRICK, Z, S, H, CZ_BRICK, SWAP_BRICK: none (Z, S, H
+  on every qubit; CZ and SWAP on the brick pairs).
 CNOT_RING applies CNOT(q -> q+1 mod n) for q = 0, 1, ..., n-1 in that order.
 
 Angles of GPI, GPI2 and MS are in turns, as printed in Appendix A
@@ -45,6 +48,7 @@ import numpy as np
 LAYER_KINDS = (
     "RX", "RY", "RZ", "ISINGZZ_RING", "CNOT_RING", "X", "SX",
     "GPI", "GPI2", "MS_BRICK", "ECR_BRICK",
+    "Z", "S", "H", "CZ_BRICK", "SWAP_BRICK", "ROT",
 )
 
 # ---------------------------------------------------------------------------
@@ -102,6 +106,13 @@ def gpi2(phi):
                      [-1j * np.exp(2j * np.pi * phi), 1]], dtype=np.complex128) / np.sqrt(2.0)
 
 
+def rot(theta, phi, lam):
+    """Rot(theta, phi, lambda) as printed in Appendix A ("Other gates")."""
+    c, s = np.cos(theta / 2), np.sin(theta / 2)
+    return np.array([[c, -np.exp(1j * lam) * s],
+                     [np.exp(1j * phi) * s, np.exp(1j * (phi + lam)) * c]], dtype=np.complex128)
+
+
 def ms(phi0, phi1, theta):
     """Molmer-Sorensen gate (Appendix A, "Other gates").
 
@@ -152,6 +163,16 @@ def d_gpi2(phi):
                      [-1j * w * np.exp(w * phi), 0]], dtype=np.complex128) / np.sqrt(2.0)
 
 
+def d_rot(theta, phi, lam):
+    """Partial derivatives (d/dtheta, d/dphi, d/dlambda) of ``rot``."""
+    c, s = np.cos(theta / 2), np.sin(theta / 2)
+    el, ep, epl = np.exp(1j * lam), np.exp(1j * phi), np.exp(1j * (phi + lam))
+    dth = 0.5 * np.array([[-s, -el * c], [ep * c, -epl * s]], dtype=np.complex128)
+    dph = np.array([[0, 0], [1j * ep * s, 1j * epl * c]], dtype=np.complex128)
+    dla = np.array([[0, -1j * el * s], [0, 1j * epl * c]], dtype=np.complex128)
+    return dth, dph, dla
+
+
 def d_ms(phi0, phi1, theta):
     """Partial derivatives (d/dphi0, d/dphi1, d/dtheta) of ``ms``."""
     c, s = np.cos(np.pi * theta), np.sin(np.pi * theta)
@@ -193,6 +214,8 @@ def layer_num_params(n, kind):
     """Number of parameters a layer of ``kind`` on n qubits reads."""
     if kind in ("RX", "RY", "RZ", "GPI", "GPI2", "ISINGZZ_RING"):
         return n
+    if kind == "ROT":
+        return 3 * n
     if kind == "MS_BRICK":
         raise ValueError("MS_BRICK parameter count depends on parity; use brick_pairs")
     return 0
@@ -263,6 +286,26 @@ def layer_gates(n, layer, x_b, theta):
     elif kind == "ECR_BRICK":
         for pair in brick_pairs(n, parity):
             gates.append((pair, ECR, []))
+    elif kind in ("Z", "S", "H"):
+        U = {"Z": Z, "S": S, "H": H}[kind]
+        for q in range(n):
+            gates.append(((q,), U, []))
+    elif kind in ("CZ_BRICK", "SWAP_BRICK"):
+        U = CZ if kind == "CZ_BRICK" else SWAP
+        for pair in brick_pairs(n, parity):
+            gates.append((pair, U, []))
+    elif kind == "ROT":
+        for q in range(n):
+            th = _param_value(layer, 3 * q + 0, x_b, theta)
+            ph = _param_value(layer, 3 * q + 1, x_b, theta)
+            la = _param_value(layer, 3 * q + 2, x_b, theta)
+            derivs = []
+            if diff:
+                dth, dph, dla = d_rot(th, ph, la)
+                derivs = [(source, offset + 3 * q + 0, dth),
+                          (source, offset + 3 * q + 1, dph),
+                          (source, offset + 3 * q + 2, dla)]
+            gates.append(((q,), rot(th, ph, la), derivs))
     elif kind == "MS_BRICK":
         for i, pair in enumerate(brick_pairs(n, parity)):
             p0 = _param_value(layer, 3 * i + 0, x_b, theta)
@@ -448,6 +491,9 @@ SHIFT_RULES = {
     "ISINGZZ_RING": (np.pi / 2, 0.5),
     "GPI": (0.125, 2 * np.pi),
     "MS_THETA": (0.25, np.pi),
+    # Rot: theta enters as RY(theta); phi and lambda through a phase e^{i a}
+    # on one basis state, a generator with eigenvalues 0 and 1
+    "ROT": (np.pi / 2, 0.5),
 }
 
 

@@ -302,11 +302,11 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
         o.op.coef = L.coef_off + (long long)q * kRec1q + (L.real ? kRealOff : 0);
         o.op.bstride = L.coef_bstride;
         o.op.nco = L.real ? 4 : (ns == 2 ? 16 : 8);
-        if (o.op.np) o.pidx.push_back(L.offset + q);
+        if (o.op.np) o.pidx.push_back(L.offset + L.pstride * q);
         o.cpidx = -1;
         if (ns == 2 && comp) {
           o.op.ck = (int8_t)(comp->kind == QC_L_RX ? 1 : 2);
-          o.cpidx = comp->offset + q;
+          o.cpidx = comp->offset + comp->pstride * q;
         }
         ops.push_back(o);
       }
@@ -477,6 +477,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
     J.cls = Li.cls; J.kind = Li.kind; J.source = Li.source; J.offset = Li.offset;
     J.parity = Li.parity; J.ngates = Li.ngates; J.per_sample = Li.per_sample;
     J.has_phase = Li.has_phase; J.tb = Li.tb;
+    J.pstride = Li.pstride; J.rot_phase = Li.rot_phase;
     J.coef_off = (long long)ce;
     J.bstride = Li.per_sample ? (long long)sz : 0;
     ce += Li.per_sample ? sz * batch : sz;
@@ -524,7 +525,8 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       if (Li.diff && Li.nparams > 0) {
         S.slot = slot;
         std::vector<OutMap> outs;
-        for (int j = 0; j < Li.nparams; ++j) outs.push_back(OutMap{0, j, Li.offset + j, 1.0});
+        for (int j = 0; j < Li.nparams; ++j)
+          outs.push_back(OutMap{0, j, Li.offset + (Li.cls == LC_DENSE2 ? j : Li.pstride * j), 1.0});
         add_job(p, RK_DIRECT, Li.source, (long long)slot * batch, batch, Li.nparams, 1, outs);
         slot += Li.nparams;
       }
@@ -669,7 +671,8 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
     if (fuse) {
       while (lead < L && lead < kMaxLeading) {
         const LayerInfo& Li = LI[lead];
-        const bool single = Li.cls == LC_ROT1 || (Li.cls == LC_DIAG && Li.kind == QC_L_RZ) ||
+        const bool single = Li.cls == LC_ROT1 ||
+                            (Li.cls == LC_DIAG && (Li.kind == QC_L_RZ || Li.kind == QC_L_Z || Li.kind == QC_L_S)) ||
                             Li.cls == LC_XCOMP;
         if (!single) break;
         ++lead;
@@ -681,6 +684,8 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       p.pv.kind[l] = LI[l].kind;
       p.pv.source[l] = LI[l].source;
       p.pv.offset[l] = LI[l].offset;
+      p.pv.pstride[l] = LI[l].pstride;
+      p.pv.rot_phase[l] = LI[l].rot_phase;
     }
     struct FGroup {
       int hi;
@@ -874,7 +879,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
           st.tp.pre_moff = part_off - st.part_off;
           std::vector<OutMap> outs;
           for (int j = 0; j < D.nparams; ++j)
-            outs.push_back(OutMap{0, diag_zbit(D, n, j), D.offset + j, D.gscale});
+            outs.push_back(OutMap{0, diag_zbit(D, n, j), D.offset + D.pstride * j, D.gscale});
           add_job(p, RK_MARGINAL, D.source, part_off, nblk, n + 1, st.cps, outs);
           part_off += nblk * (n + 1);
         } else if (st.type == ST_DIAG && Li.diff && Li.nparams > 0) {
@@ -882,7 +887,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
           st.part_off = part_off;
           std::vector<OutMap> outs;
           for (int j = 0; j < Li.nparams; ++j)
-            outs.push_back(OutMap{0, diag_zbit(Li, n, j), Li.offset + j, Li.gscale});
+            outs.push_back(OutMap{0, diag_zbit(Li, n, j), Li.offset + Li.pstride * j, Li.gscale});
           add_job(p, RK_MARGINAL, Li.source, part_off, nblk, n + 1, nblk / batch, outs);
           part_off += nblk * (n + 1);
         } else if (st.type == ST_DIAG) {
@@ -1180,11 +1185,11 @@ qc_status backward_impl(qc_circuit* c, int batch, const double* x, const double*
 
 int layer_class(int kind) {
   switch (kind) {
-    case QC_L_RX: case QC_L_RY: case QC_L_SX: case QC_L_GPI2: return LC_ROT1;
-    case QC_L_RZ: case QC_L_ISINGZZ_RING: return LC_DIAG;
+    case QC_L_RX: case QC_L_RY: case QC_L_SX: case QC_L_GPI2: case QC_L_H: return LC_ROT1;
+    case QC_L_RZ: case QC_L_ISINGZZ_RING: case QC_L_Z: case QC_L_S: return LC_DIAG;
     case QC_L_CNOT_RING: return LC_RING;
     case QC_L_X: case QC_L_GPI: return LC_XCOMP;
-    case QC_L_MS_BRICK: case QC_L_ECR_BRICK: return LC_DENSE2;
+    case QC_L_MS_BRICK: case QC_L_ECR_BRICK: case QC_L_CZ_BRICK: case QC_L_SWAP_BRICK: return LC_DENSE2;
   }
   return -1;
 }
@@ -1235,21 +1240,44 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
   c->opt = o;
   if (o.path == 1 && !smem_fits(c.get()))
     return fail(QC_ERR_UNSUPPORTED, "whole-circuit shared-memory path needs n <= 13 (c64) / 12 (c128)");
+  // a Rot layer runs as three layers RZ(lambda), RY(theta), RZ(phi) (the
+  // last carrying the global phase e^{i(phi+lambda)/2}) on strided parameters
+  struct Sub { qc_layer in; int pstride, rot_phase, user; };
+  std::vector<Sub> subs;
   for (int l = 0; l < n_layers; ++l) {
     const qc_layer& in = layers[l];
+    if (in.kind == QC_L_ROT) {
+      if (in.source < QC_SRC_NONE || in.source > QC_SRC_INPUT)
+        return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unknown source");
+      if (in.source != QC_SRC_NONE && in.offset < 0)
+        return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": negative offset");
+      if (in.source == QC_SRC_THETA) c->n_theta = std::max(c->n_theta, in.offset + 3 * n);
+      if (in.source == QC_SRC_INPUT) c->n_in = std::max(c->n_in, in.offset + 3 * n);
+      subs.push_back(Sub{qc_layer{QC_L_RZ, in.source, in.offset + 2, 0}, 3, 0, l});
+      subs.push_back(Sub{qc_layer{QC_L_RY, in.source, in.offset + 0, 0}, 3, 0, l});
+      subs.push_back(Sub{qc_layer{QC_L_RZ, in.source, in.offset + 1, 0}, 3, 1, l});
+    } else {
+      subs.push_back(Sub{in, 1, 0, l});
+    }
+  }
+  for (const Sub& sub : subs) {
+    const qc_layer& in = sub.in;
+    const int l = sub.user;
     LayerInfo L;
     memset(&L, 0, sizeof(L));
     L.kind = in.kind;
     L.source = in.source;
     L.offset = in.offset;
     L.parity = in.parity;
+    L.pstride = sub.pstride;
+    L.rot_phase = sub.rot_phase;
     L.cls = layer_class(in.kind);
     if (L.cls < 0) return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unknown kind");
     if (in.source < QC_SRC_NONE || in.source > QC_SRC_INPUT)
       return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unknown source");
     if ((in.kind == QC_L_CNOT_RING || in.kind == QC_L_ISINGZZ_RING) && n < 2)
       return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": ring layers need n >= 2");
-    if (in.kind == QC_L_MS_BRICK || in.kind == QC_L_ECR_BRICK) {
+    if (L.cls == LC_DENSE2) {
       if (in.parity != 0 && in.parity != 1)
         return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": brick parity must be 0 or 1");
       L.ngates = std::max(0, (n - in.parity) / 2);
@@ -1265,7 +1293,8 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
       default: L.nparams = 0;
     }
     const bool never_param = in.kind == QC_L_CNOT_RING || in.kind == QC_L_X || in.kind == QC_L_SX ||
-                             in.kind == QC_L_ECR_BRICK;
+                             in.kind == QC_L_ECR_BRICK || in.kind == QC_L_Z || in.kind == QC_L_S ||
+                             in.kind == QC_L_H || in.kind == QC_L_CZ_BRICK || in.kind == QC_L_SWAP_BRICK;
     if (never_param && in.source != QC_SRC_NONE)
       return fail(QC_ERR_INVALID, "layer " + std::to_string(l) + ": unparametrised kind needs source NONE");
     if (in.source != QC_SRC_NONE && in.offset < 0)
@@ -1278,8 +1307,10 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
     L.gscale = in.kind == QC_L_GPI ? -4.0 * 3.14159265358979323846 : 1.0;
     L.tb = (n + kDiagTables - 1) / kDiagTables;
     if (L.tb < 1) L.tb = 1;
-    if (in.source == QC_SRC_THETA) c->n_theta = std::max(c->n_theta, in.offset + L.nparams);
-    if (in.source == QC_SRC_INPUT) c->n_in = std::max(c->n_in, in.offset + L.nparams);
+    if (sub.pstride == 1) {  // (Rot's bound was taken above)
+      if (in.source == QC_SRC_THETA) c->n_theta = std::max(c->n_theta, in.offset + L.nparams);
+      if (in.source == QC_SRC_INPUT) c->n_in = std::max(c->n_in, in.offset + L.nparams);
+    }
     c->layers.push_back(L);
   }
   *out = c.release();

@@ -66,6 +66,15 @@ __device__ inline void gate1q(int kind, double t, dc M[4]) {
     case QC_L_X:
       M[0] = dmk(0, 0); M[1] = dmk(1, 0); M[2] = dmk(1, 0); M[3] = dmk(0, 0);
       break;
+    case QC_L_Z:
+      M[0] = dmk(1, 0); M[1] = dmk(0, 0); M[2] = dmk(0, 0); M[3] = dmk(-1, 0);
+      break;
+    case QC_L_S:
+      M[0] = dmk(1, 0); M[1] = dmk(0, 0); M[2] = dmk(0, 0); M[3] = dmk(0, 1);
+      break;
+    case QC_L_H:
+      M[0] = dmk(kInvSqrt2, 0); M[1] = dmk(kInvSqrt2, 0); M[2] = dmk(kInvSqrt2, 0); M[3] = dmk(-kInvSqrt2, 0);
+      break;
     default:
       M[0] = dmk(1, 0); M[1] = dmk(0, 0); M[2] = dmk(0, 0); M[3] = dmk(1, 0);
   }
@@ -157,6 +166,16 @@ __device__ inline void dgate_ms(double p0, double p1, double th, int which, dc D
   D[6] = dmul(dmul(mis, e12), dmk(0, k12));
   D[9] = dmul(dmul(mis, e21), dmk(0, k21));
   D[12] = dmul(dmul(mis, e30), dmk(0, k30));
+}
+
+// CZ = diag(1, 1, 1, -1); SWAP exchanges |01> and |10> (Appendix A).
+__device__ inline void gate_cz(dc M[16]) {
+  for (int i = 0; i < 16; ++i) M[i] = dmk(0, 0);
+  M[0] = dmk(1, 0); M[5] = dmk(1, 0); M[10] = dmk(1, 0); M[15] = dmk(-1, 0);
+}
+__device__ inline void gate_swap(dc M[16]) {
+  for (int i = 0; i < 16; ++i) M[i] = dmk(0, 0);
+  M[0 * 4 + 0] = dmk(1, 0); M[1 * 4 + 2] = dmk(1, 0); M[2 * 4 + 1] = dmk(1, 0); M[3 * 4 + 3] = dmk(1, 0);
 }
 
 // ECR = (I (x) X - X (x) Y) / sqrt(2), first qubit the left factor.

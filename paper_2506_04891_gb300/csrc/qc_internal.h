@@ -49,6 +49,10 @@ struct LayerInfo {
   long long coef_off;
   long long coef_bstride;   // per-sample stride (0 when shared)
   int tb;                   // DIAG/XCOMP: bits per table (tables of 2^tb complex)
+  int pstride;              // parameter j of the layer is offset + pstride * j (1, or 3 for
+                            // the layers a Rot layer expands into)
+  int rot_phase;            // RZ part of a Rot: the phase tables carry e^{i(phi+lambda)/2},
+                            // lambda = parameter offset + pstride * j + 1
 };
 
 // One gate op inside a tile pass.

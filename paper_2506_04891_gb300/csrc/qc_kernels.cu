@@ -17,8 +17,9 @@ namespace qc {
 
 __device__ __forceinline__ double param_of(const CoefJob& J, int b, int j, const double* x,
                                            const double* theta, int n_in) {
-  if (J.source == QC_SRC_THETA) return theta[J.offset + j];
-  if (J.source == QC_SRC_INPUT) return x[(long long)b * n_in + J.offset + j];
+  const int idx = J.offset + J.pstride * j;
+  if (J.source == QC_SRC_THETA) return theta[idx];
+  if (J.source == QC_SRC_INPUT) return x[(long long)b * n_in + idx];
   return 0.0;
 }
 
@@ -63,6 +64,10 @@ __global__ void k_coef(const CoefJob* __restrict__ jobs, int njobs, int n, int b
             o[32 + 32 * w + 2 * i + 1] = (R)A[i].y;
           }
         }
+      } else if (J.kind == QC_L_CZ_BRICK) {
+        gate_cz(M);
+      } else if (J.kind == QC_L_SWAP_BRICK) {
+        gate_swap(M);
       } else {
         gate_ecr(M);
       }
@@ -79,9 +84,23 @@ __global__ void k_coef(const CoefJob* __restrict__ jobs, int njobs, int n, int b
       if (J.kind == QC_L_GPI) {
         dvec[p][0] = dexpi(2.0 * kPi * t);
         dvec[p][1] = dexpi(-2.0 * kPi * t);
+      } else if (J.kind == QC_L_Z) {
+        dvec[p][0] = dmk(1, 0);
+        dvec[p][1] = dmk(-1, 0);
+      } else if (J.kind == QC_L_S) {
+        dvec[p][0] = dmk(1, 0);
+        dvec[p][1] = dmk(0, 1);
       } else {  // RZ, IsingZZ: exp(-i t/2 * (+1 / -1))
         dvec[p][0] = dexpi(-0.5 * t);
         dvec[p][1] = dexpi(0.5 * t);
+        if (J.rot_phase) {
+          // RZ(phi) part of Rot(theta, phi, lambda): times e^{i (phi + lambda) / 2}
+          CoefJob Jl = J;
+          Jl.offset += 1;
+          const dc g = dexpi(0.5 * (t + param_of(Jl, b, j, x, theta, n_in)));
+          dvec[p][0] = dmul(dvec[p][0], g);
+          dvec[p][1] = dmul(dvec[p][1], g);
+        }
       }
     }
     __syncthreads();
@@ -113,9 +132,15 @@ __global__ void k_prodvec(ProdVecJob P, int n, int batch, int n_in, const double
     CoefJob J;
     J.source = P.source[l];
     J.offset = P.offset[l];
+    J.pstride = P.pstride[l];
     double t = param_of(J, b, q, x, theta, n_in);
     dc M[4];
     gate1q(P.kind[l], t, M);
+    if (P.rot_phase[l]) {  // RZ(phi) part of a Rot: times e^{i (phi + lambda) / 2}
+      J.offset += 1;
+      const dc g = dexpi(0.5 * (t + param_of(J, b, q, x, theta, n_in)));
+      for (int i = 0; i < 4; ++i) M[i] = dmul(M[i], g);
+    }
     dc a = dadd(dmul(M[0], v0), dmul(M[1], v1));
     dc c = dadd(dmul(M[2], v0), dmul(M[3], v1));
     v0 = a; v1 = c;

@@ -15,6 +15,8 @@ struct CoefJob {
   int per_sample;
   int has_phase;
   int tb;
+  int pstride;    // parameter j at offset + pstride * j
+  int rot_phase;  // RZ part of a Rot (see LayerInfo)
   long long coef_off;
   long long bstride;
 };
@@ -23,6 +25,7 @@ constexpr int kMaxLeading = 32;
 struct ProdVecJob {
   int nl;
   int kind[kMaxLeading], source[kMaxLeading], offset[kMaxLeading];
+  int pstride[kMaxLeading], rot_phase[kMaxLeading];
 };
 
 template <class R>

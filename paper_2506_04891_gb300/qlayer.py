@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libqlayer.so")
 KINDS = {
     "RX": 0, "RY": 1, "RZ": 2, "ISINGZZ_RING": 3, "CNOT_RING": 4, "X": 5, "SX": 6,
     "GPI": 7, "GPI2": 8, "MS_BRICK": 9, "ECR_BRICK": 10,
+    "Z": 11, "S": 12, "H": 13, "CZ_BRICK": 14, "SWAP_BRICK": 15, "ROT": 16,
 }
 SOURCES = {"none": 0, "theta": 1, "input": 2}
 DTYPES = {"c64": 0, "c128": 1}

@@ -44,6 +44,8 @@ def layer_param_count(n: int, layer) -> int:
         return n
     if kind == "MS_BRICK":
         return 3 * brick_gate_count(n, parity)
+    if kind == "ROT":
+        return 3 * n
     return 0
 
 
@@ -75,6 +77,20 @@ def hea_circuit(n: int, depth: int, block=("RZ", "RY", "RZ"), embed="RX"):
     for _ in range(depth):
         for k in block:
             b.add(k, "theta")
+        b.add("CNOT_RING")
+    return b.layers
+
+
+def qdi_circuit(n: int, depth: int):
+    """Quantum Depth Infused layer (Sec. 3): the data x re-enters in every RZ
+    layer (the same n inputs each block), between trainable RY / RZ layers and a
+    CNOT ring."""
+    b = _Builder(n)
+    for _ in range(depth):
+        b.layers.append(("RZ", "input", 0, 0))
+        b.n_in = max(b.n_in, n)
+        b.add("RY", "theta")
+        b.add("RZ", "theta")
         b.add("CNOT_RING")
     return b.layers
 

@@ -91,6 +91,21 @@ def test_create_rejects_invalid(q, bad, err):
     assert q.qc_last_error()
 
 
+def test_rot_counts_three_parameters_per_qubit_and_constants_take_no_source(q):
+    n = 6
+    h = q.qc_create(n, "c64", [("ROT", "theta", 4, 0), ("H", "none", 0, 0), ("ROT", "input", 1, 0)])
+    try:
+        assert q.qc_num_params(h) == (4 + 3 * n, 1 + 3 * n)
+        assert q.qc_num_params(h) == W.circuit_params(n, [("ROT", "theta", 4, 0), ("ROT", "input", 1, 0)])
+    finally:
+        q.qc_destroy(h)
+    for kind in ("Z", "S", "H", "CZ_BRICK", "SWAP_BRICK"):
+        with pytest.raises(q.QCError):
+            q.qc_create(n, "c64", [(kind, "theta", 0, 0)])
+    with pytest.raises(q.QCError):
+        q.qc_create(n, "c64", [("SWAP_BRICK", "none", 0, 2)])
+
+
 def test_unknown_kind_rejected(q):
     import ctypes
     arr = (q.qc_layer * 1)()

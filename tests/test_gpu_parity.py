@@ -100,10 +100,11 @@ def test_tiny_n(n, path):
 def test_every_kind_in_every_position_layer_path():
     n = 14
     kinds = ["RX", "RY", "RZ", "ISINGZZ_RING", "CNOT_RING", "X", "SX", "GPI", "GPI2",
-             "MS_BRICK", "ECR_BRICK"]
+             "MS_BRICK", "ECR_BRICK", "Z", "S", "H", "CZ_BRICK", "SWAP_BRICK", "ROT"]
+    fixed = ("CNOT_RING", "X", "SX", "ECR_BRICK", "Z", "S", "H", "CZ_BRICK", "SWAP_BRICK")
     layers, off = [], 0
     for i, k in enumerate(kinds + kinds[::-1]):
-        src = "none" if k in ("CNOT_RING", "X", "SX", "ECR_BRICK") else ("input" if i % 5 == 0 else "theta")
+        src = "none" if k in fixed else ("input" if i % 5 == 0 else "theta")
         par = i % 2
         cnt = W.layer_param_count(n, (k, src, 0, par))
         layers.append((k, src, 0, par))
@@ -153,6 +154,27 @@ def test_folded_gradients_without_deferred_sums():
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("dtype,n", [("c64", 9), ("c128", 8)])
+def test_constant_gates_and_rot_both_paths(path, dtype, n):
+    """Z, S, H, CZ and SWAP bricks (both parities) and Rot (theta and input
+    sourced) around the other kinds (Appendix A matrices)."""
+    b = W._Builder(n)
+    for k, src, par in [("ROT", "input", 0), ("H", "none", 0), ("CZ_BRICK", "none", 0),
+                        ("S", "none", 0), ("RY", "theta", 0), ("SWAP_BRICK", "none", 1),
+                        ("Z", "none", 0), ("ROT", "theta", 0), ("CNOT_RING", "none", 0),
+                        ("CZ_BRICK", "none", 1), ("SWAP_BRICK", "none", 0), ("ROT", "theta", 0)]:
+        b.add(k, src, par)
+    compare(dtype, n, b.layers, 3, seed=13, path=path)
+
+
+@pytest.mark.parametrize("dtype,n,path", [("c64", 14, 2), ("c128", 13, 2), ("c64", 10, 1)])
+def test_qdi_reupload_matches_oracle(dtype, n, path):
+    """QDI (Sec. 3): the same x re-enters every RZ layer, so several layers add
+    into each dx entry."""
+    compare(dtype, n, W.qdi_circuit(n, 3), 3, seed=14, path=path)
 
 
 def test_empty_circuit_and_batch_one():

@@ -95,6 +95,7 @@ def _all_gate_mats():
         "RX": O.rx(t[0]), "RY": O.ry(t[0]), "RZ": O.rz(t[0]), "ZZ": O.isingzz(t[1]),
         "GPI": O.gpi(t[2]), "GPI2": O.gpi2(t[2]), "MS": O.ms(*t), "SX": O.SX,
         "ECR": O.ECR, "X": O.X, "CNOT": O.CNOT, "H": O.H,
+        "Z": O.Z, "S": O.S, "CZ": O.CZ, "SWAP": O.SWAP, "ROT": O.rot(*t),
     }
 
 
@@ -113,6 +114,42 @@ def test_fixed_gate_identities():
     p0, p1, th = 0.21, 0.05, 0.33
     K = (np.cos(np.pi * th) * np.eye(4) - O.ms(p0, p1, th)) / (1j * np.sin(np.pi * th))
     assert np.allclose(K, K.conj().T) and np.allclose(K @ K, np.eye(4))
+
+
+def test_constant_gate_identities():
+    # H, S, Z, CZ, SWAP (Appendix A): H^2 = I, S^2 = Z, H Z H = X, CZ = diag with one
+    # sign flip, SWAP exchanges the two factors of a product state
+    assert np.allclose(O.H @ O.H, np.eye(2), atol=1e-15)
+    assert np.allclose(O.S @ O.S, O.Z, atol=1e-15)
+    assert np.allclose(O.H @ O.Z @ O.H, O.X, atol=1e-15)
+    assert np.allclose(O.CZ, np.diag([1, 1, 1, -1]))
+    a, b = RNG.normal(size=2) + 1j * RNG.normal(size=2), RNG.normal(size=2) + 1j * RNG.normal(size=2)
+    assert np.allclose(O.SWAP @ np.kron(a, b), np.kron(b, a), atol=1e-15)
+    # CZ is symmetric in its qubits: SWAP CZ SWAP = CZ
+    assert np.allclose(O.SWAP @ O.CZ @ O.SWAP, O.CZ)
+
+
+def test_rot_is_rz_ry_rz_up_to_the_printed_phase():
+    # Rot(th, ph, la) = e^{i (ph + la) / 2} Rz(ph) Ry(th) Rz(la); Rot(th, 0, 0) = Ry(th)
+    for th, ph, la in [(0.37, 1.21, -0.6), (2.9, -0.4, 0.85)]:
+        dec = np.exp(0.5j * (ph + la)) * O.rz(ph) @ O.ry(th) @ O.rz(la)
+        assert np.allclose(O.rot(th, ph, la), dec, atol=1e-15)
+    assert np.allclose(O.rot(0.8, 0.0, 0.0), O.ry(0.8), atol=1e-15)
+    # first row of the printed matrix: (cos(th/2), -e^{i la} sin(th/2))
+    th, ph, la = 0.5, 0.2, 0.9
+    assert np.isclose(O.rot(th, ph, la)[0, 0], np.cos(th / 2))
+    assert np.isclose(O.rot(th, ph, la)[0, 1], -np.exp(1j * la) * np.sin(th / 2))
+
+
+def test_rot_derivatives_match_difference_quotient():
+    p = np.array([0.71, -0.33, 1.4])
+    h = 1e-6
+    d = O.d_rot(*p)
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        num = (O.rot(*(p + e)) - O.rot(*(p - e))) / (2 * h)
+        assert np.allclose(d[i], num, atol=1e-8)
 
 
 def test_h_rz_expansion_identities():
@@ -153,7 +190,7 @@ def test_ms_derivatives_match_difference_quotient():
 # ---------------------------------------------------------------------------
 
 ALL_KINDS = ["RX", "RY", "RZ", "ISINGZZ_RING", "CNOT_RING", "X", "SX", "GPI", "GPI2",
-             "MS_BRICK", "ECR_BRICK"]
+             "MS_BRICK", "ECR_BRICK", "Z", "S", "H", "CZ_BRICK", "SWAP_BRICK", "ROT"]
 
 
 def _random_layer_inputs(n, layer):
@@ -385,9 +422,10 @@ def test_parameter_shift_covers_every_exact_kind():
     n = 3
     layers = [("RX", "input", 0, 0), ("RY", "theta", 0, 0), ("RZ", "theta", 3, 0),
               ("ISINGZZ_RING", "theta", 6, 0), ("GPI", "theta", 9, 0),
-              ("MS_BRICK", "theta", 12, 0), ("CNOT_RING", "none", 0, 0)]
+              ("MS_BRICK", "theta", 12, 0), ("CNOT_RING", "none", 0, 0),
+              ("ROT", "theta", 15, 0), ("H", "none", 0, 0), ("CZ_BRICK", "none", 0, 0)]
     x, theta, _ = W.draw_inputs(n, layers, 1, seed=2)
-    theta = np.random.default_rng(3).uniform(0, 1, size=15)
+    theta = np.random.default_rng(3).uniform(0, 1, size=24)
     g = W.draw_upstream(1, n, seed=2)
     _, _, dth_s, dx = O.adjoint(n, layers, x, theta, g)
     ps = O.param_shift_sample(n, layers, x[0], theta, g[0])
@@ -416,6 +454,8 @@ def _pins_pass():
             test_adjoint_matches_param_shift_and_finite_differences(name)
         test_h_rz_expansion_identities()
         test_ms_matches_printed_except_corrected_entry()
+        test_rot_is_rz_ry_rz_up_to_the_printed_phase()
+        test_constant_gate_identities()
     except AssertionError:
         return False
     return True
@@ -430,7 +470,7 @@ _orig_apply = O.apply_local
 
 @pytest.mark.parametrize("mutation", [
     "ry_sign", "rz_sign", "apply_transposed", "dry_dropped_term", "ring_reversed",
-    "expect_wrong_bit", "adjoint_no_conj", "ms_unconjugated",
+    "expect_wrong_bit", "adjoint_no_conj", "ms_unconjugated", "rot_phases_swapped",
 ])
 def test_planted_mistakes_are_caught(monkeypatch, mutation):
     if mutation == "ry_sign":
@@ -464,4 +504,7 @@ def test_planted_mistakes_are_caught(monkeypatch, mutation):
             m[3, 0] = m[0, 3]
             return m
         monkeypatch.setattr(O, "ms", bad)
+    elif mutation == "rot_phases_swapped":
+        orig_rot = O.rot
+        monkeypatch.setattr(O, "rot", lambda th, ph, la: orig_rot(th, la, ph))
     assert not _pins_pass(), mutation
