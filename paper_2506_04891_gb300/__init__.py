@@ -7,7 +7,7 @@ __all__ = ["qlayer", "workloads"]
 
 
 def __getattr__(name):
-    if name in ("qlayer", "workloads", "serving", "torch_fn"):
+    if name in ("qlayer", "workloads", "serving", "torch_fn", "tune", "dist"):
         import importlib
         return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -118,6 +118,7 @@ struct OutMap {
 struct Plan {
   int batch = 0;
   bool smem = false;
+  bool unplaced = false;  // a gate found no round (invalid geometry): the plan is refused
   std::vector<Step> fwd, bwd;
   std::vector<CoefJob> coef_jobs;
   ProdVecJob pv{};
@@ -168,8 +169,10 @@ struct qc_circuit {
 
 namespace {
 
-// Tuning knobs for benchmarks (environment, read once): QC_TMAX_FWD, QC_TMAX_BWD
-// (tile bits), QC_RB_FWD, QC_RB_BWD (register bits per round).  0 = default.
+// Tile geometry: the circuit's options first, then the process-wide
+// environment knobs QC_TMAX_FWD, QC_TMAX_BWD (tile bits), QC_RB_FWD,
+// QC_RB_BWD (register bits per round), QC_TILE_STAGES (read once), then the
+// defaults.  0 = unset.
 int env_knob(const char* name) {
   const char* v = getenv(name);
   return v ? atoi(v) : 0;
@@ -178,6 +181,8 @@ int env_knob(const char* name) {
 // Largest tile (log2 amplitudes): two buffers of ns states must leave room
 // for two CTAs per SM.
 int tile_tmax(const qc_circuit* c, int ns) {
+  if (ns == 1 && c->opt.tile_bits_fwd > 0) return c->opt.tile_bits_fwd;
+  if (ns == 2 && c->opt.tile_bits_bwd > 0) return c->opt.tile_bits_bwd;
   static const int kf = env_knob("QC_TMAX_FWD"), kb = env_knob("QC_TMAX_BWD");
   if (ns == 1 && kf > 0) return kf;
   if (ns == 2 && kb > 0) return kb;
@@ -220,7 +225,8 @@ int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 // Register bits per round: the backward holds two states, so it takes one
 // bit fewer (every thread of a 2^11-amplitude tile then has work).
 int reg_bits(const qc_circuit* c, int ns) {
-  (void)c;
+  if (ns == 1 && c->opt.reg_bits_fwd > 0) return c->opt.reg_bits_fwd;
+  if (ns == 2 && c->opt.reg_bits_bwd > 0) return c->opt.reg_bits_bwd;
   static const int kf = env_knob("QC_RB_FWD"), kb = env_knob("QC_RB_BWD");
   if (ns == 1 && kf > 0) return kf;
   if (ns == 2 && kb > 0) return kb;
@@ -231,12 +237,25 @@ int reg_bits(const qc_circuit* c, int ns) {
 // processed) measured faster on zz26 than three: the passes are bound by issue
 // and shared-memory latency, not by bytes in flight.  QC_TILE_STAGES=3 takes
 // three where two CTAs per SM still fit.
-int tile_stages(TilePass& P, int ns, int rsize) {
-  static const int k = env_knob("QC_TILE_STAGES");
+int tile_stages(const qc_circuit* c, TilePass& P, int ns, int rsize) {
+  static const int ke = env_knob("QC_TILE_STAGES");
+  const int k = c->opt.stages > 0 ? c->opt.stages : ke;
   if (k != 3) return 2;
   P.nstage = 3;
   const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
   return 2 * (tile_smem_bytes(P, ns, rsize) + per_cta_reserved) <= per_sm ? 3 : 2;
+}
+
+// set by plan_tile_layer when a gate found no round; read by build_plan
+thread_local bool g_plan_unplaced = false;
+
+// Register bits per round of a pass of tile size t: a two-qubit op needs both
+// of its bits in the same round, so brick layers take at least two, and a pass
+// has at most kMaxRounds rounds.
+int pass_rb(const qc_circuit* c, const LayerInfo& L, int ns, int t) {
+  int rb = std::max(reg_bits(c, ns), L.cls == LC_DENSE2 ? 2 : 1);
+  rb = std::max(rb, (t + kMaxRounds - 1) / kMaxRounds);
+  return std::min(rb, t);
 }
 
 bool cuts_pair(const LayerInfo& L, int n, int e) {
@@ -335,7 +354,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
       continue;
     }
     // rounds of RB register bits
-    const int RB = std::min(reg_bits(c, ns), P.t);
+    const int RB = pass_rb(c, L, ns, P.t);
     std::vector<int> assigned(ops.size(), 0);
     int nass = 0, nr = 0;
     std::vector<TileOp> ordered;
@@ -361,11 +380,12 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
           ordered_cpidx.push_back(ops[k].cpidx);
         }
       }
-      if (!got || nr >= kMaxRounds) break;  // cannot happen for valid geometry
+      if (!got || nr >= kMaxRounds) break;  // the check below turns this into an error
       P.rlo[nr] = (int8_t)lo;
       ++nr;
       P.rop[nr] = (int16_t)ordered.size();
     }
+    if (nass < (int)ops.size()) g_plan_unplaced = true;
     P.nrounds = nr;
     P.nops = (int)ordered.size();
     int soff = 0, slot = 0;
@@ -414,7 +434,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     if (!defer)
       for (int r = 0; r < 4; ++r)
         for (int i = 0; i < 4; ++i) P.rslot[r][i] = P.rcslot[r][i] = -1;
-    P.nstage = tile_stages(P, ns, (int)c->rsize);
+    P.nstage = tile_stages(c, P, ns, (int)c->rsize);
     out.push_back(P);
     s = e;
     first = false;
@@ -455,6 +475,7 @@ void add_job(Plan& P, int kind, int source, long long part_off, long long nblk, 
 }
 
 std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
+  g_plan_unplaced = false;
   auto P = std::make_unique<Plan>();
   Plan& p = *P;
   p.batch = batch;
@@ -550,7 +571,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       std::vector<Step> v;
       for (auto& tp : plan_tile_layer(c, Li, ns, pslots, comp)) {
         Step st;
-        st.type = ST_TILE; st.ns = ns; st.tp = tp; st.rb = std::min(reg_bits(c, ns), tp.t);
+        st.type = ST_TILE; st.ns = ns; st.tp = tp; st.rb = pass_rb(c, Li, ns, tp.t);
         st.cps = pass_cps(c, batch, tp, ns);
         v.push_back(st);
       }
@@ -950,6 +971,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       }
     }
   }
+  P->unplaced = g_plan_unplaced;
   return P;
 }
 
@@ -1000,6 +1022,7 @@ qc_status get_plan(qc_circuit* c, int batch, Plan** out) {
   auto it = c->plans.find(batch);
   if (it == c->plans.end()) {
     auto P = build_plan(c, batch);
+    if (P->unplaced) return fail(QC_ERR_UNSUPPORTED, "planner: a gate found no round in its tile pass");
     it = c->plans.emplace(batch, std::move(P)).first;
   }
   *out = it->second.get();
@@ -1209,14 +1232,16 @@ qc_status set_error(qc_status s, const char* msg) { return fail(s, msg); }
 // ===========================================================================
 extern "C" {
 
-QC_API int qc_version(void) { return 100; }
+QC_API int qc_version(void) { return 101; }
 
 QC_API void qc_default_options(qc_options* opt) {
   if (!opt) return;
   opt->ckpt_every = -1;
   opt->path = 0;
   opt->fuse = 1;
-  opt->reserved = 0;
+  opt->tile_bits_fwd = opt->tile_bits_bwd = 0;
+  opt->reg_bits_fwd = opt->reg_bits_bwd = 0;
+  opt->stages = 0;
 }
 
 QC_API const char* qc_last_error(void) { return g_last_error.c_str(); }
@@ -1233,6 +1258,17 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
   if (opt) o = *opt;
   if (o.path < 0 || o.path > 2) return fail(QC_ERR_INVALID, "options.path must be 0, 1 or 2");
   if (o.ckpt_every < -1) return fail(QC_ERR_INVALID, "options.ckpt_every must be >= -1");
+  {
+    const int fmax = dtype == QC_C64 ? 13 : 12, bmax = dtype == QC_C64 ? 12 : 11;
+    if (o.tile_bits_fwd != 0 && (o.tile_bits_fwd < 6 || o.tile_bits_fwd > fmax))
+      return fail(QC_ERR_INVALID, "options.tile_bits_fwd out of range");
+    if (o.tile_bits_bwd != 0 && (o.tile_bits_bwd < 6 || o.tile_bits_bwd > bmax))
+      return fail(QC_ERR_INVALID, "options.tile_bits_bwd out of range");
+    if (o.reg_bits_fwd < 0 || o.reg_bits_fwd > 4 || o.reg_bits_bwd < 0 || o.reg_bits_bwd > 4)
+      return fail(QC_ERR_INVALID, "options.reg_bits_* must be in 0 .. 4");
+    if (o.stages != 0 && o.stages != 2 && o.stages != 3)
+      return fail(QC_ERR_INVALID, "options.stages must be 0, 2 or 3");
+  }
   auto c = std::make_unique<qc_circuit>();
   c->n = n;
   c->dtype = dtype;
@@ -1514,7 +1550,8 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
   qc_status s = check_common(c, batch);
   if (s != QC_OK) return s;
   Plan* p;
-  get_plan(c, batch, &p);
+  s = get_plan(c, batch, &p);
+  if (s != QC_OK) return s;
   std::string o;
   char line[512];
   snprintf(line, sizeof line, "path=%s nlead=%d nckpt=%d ws_fwd=%zu ws_bwd=%zu jobs=%zu outs=%zu overlap=%d\n",

@@ -46,7 +46,11 @@ class qc_layer(ctypes.Structure):
 
 class qc_options(ctypes.Structure):
     _fields_ = [("ckpt_every", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("fuse", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fuse", ctypes.c_int32), ("tile_bits_fwd", ctypes.c_int32),
+                ("tile_bits_bwd", ctypes.c_int32), ("reg_bits_fwd", ctypes.c_int32),
+                ("reg_bits_bwd", ctypes.c_int32), ("stages", ctypes.c_int32)]
+
+TUNING_FIELDS = ("tile_bits_fwd", "tile_bits_bwd", "reg_bits_fwd", "reg_bits_bwd", "stages")
 
 
 class QCError(RuntimeError):
@@ -225,7 +229,7 @@ class Circuit:
     """
 
     def __init__(self, n: int, layers, dtype: str = "c64", ckpt_every: int = -1, path: int = 0,
-                 fuse: int = 1):
+                 fuse: int = 1, tuning: dict | None = None):
         self.n = int(n)
         self.layers = list(layers)
         self.dtype = dtype
@@ -233,6 +237,11 @@ class Circuit:
         opt.ckpt_every = ckpt_every
         opt.path = path
         opt.fuse = fuse
+        self.tuning = dict(tuning or {})
+        for k, v in self.tuning.items():
+            if k not in TUNING_FIELDS:
+                raise ValueError(f"unknown tuning field {k!r}")
+            setattr(opt, k, int(v))
         self.handle = qc_create(self.n, dtype, self.layers, opt)
         self.n_theta, self.n_in = qc_num_params(self.handle)
         self._ws = {}

@@ -47,7 +47,7 @@ def test_nm_exports_are_extern_c(q):
 
 
 def test_version_and_defaults(q):
-    assert q.qc_version() == 100
+    assert q.qc_version() == 101
     o = q.qc_default_options()
     assert (o.ckpt_every, o.path, o.fuse) == (-1, 0, 1)
 
@@ -106,6 +106,40 @@ def test_rot_counts_three_parameters_per_qubit_and_constants_take_no_source(q):
         q.qc_create(n, "c64", [("SWAP_BRICK", "none", 0, 2)])
 
 
+def test_tuning_options_shape_the_plan_and_are_validated(q):
+    layers = W.zz_circuit(16, 2)
+    base = q.Circuit(16, layers, path=2).describe(2)
+    tuned = q.Circuit(16, layers, path=2, tuning=dict(tile_bits_fwd=10, tile_bits_bwd=9,
+                                                      reg_bits_fwd=3, reg_bits_bwd=2)).describe(2)
+    def geo(desc, tag):
+        return {(int(d["t"]), int(d["rb"])) for d in
+                (dict(re.findall(r"(\w+)=(-?\d+)", l.split("[")[0])) for l in desc.splitlines()
+                 if l.startswith(tag) and " TILE " in l)}
+    assert geo(base, "F ") == {(12, 4)} and geo(base, "B ") == {(11, 3)}
+    assert geo(tuned, "F ") == {(10, 3)} and geo(tuned, "B ") == {(9, 2)}
+    for bad in (dict(tile_bits_fwd=14), dict(tile_bits_bwd=13), dict(tile_bits_fwd=5),
+                dict(reg_bits_bwd=5), dict(stages=4)):
+        with pytest.raises(q.QCError):
+            q.Circuit(16, layers, tuning=bad)
+    with pytest.raises(q.QCError):
+        q.Circuit(16, layers, dtype="c128", tuning=dict(tile_bits_bwd=12))
+    with pytest.raises(ValueError):
+        q.Circuit(16, layers, tuning=dict(tiles=3))
+
+
+def test_tuner_candidates_stay_in_range():
+    from paper_2506_04891_gb300 import tune
+    for dtype in ("c64", "c128"):
+        fwd, bwd = tune.candidates(26, dtype)
+        fm, bm = tune.MAX_TILE[dtype]
+        assert fwd and bwd
+        assert all(6 <= c["tile_bits_fwd"] <= fm and c["reg_bits_fwd"] in (3, 4) for c in fwd)
+        assert all(6 <= c["tile_bits_bwd"] <= bm and 1 <= c["reg_bits_bwd"] <= 4 for c in bwd)
+        assert tune.DEFAULT_TILE[dtype][0] in {c["tile_bits_fwd"] for c in fwd}
+    fwd, _ = tune.candidates(9, "c64")
+    assert all(c["tile_bits_fwd"] <= 9 for c in fwd)
+
+
 def test_unknown_kind_rejected(q):
     import ctypes
     arr = (q.qc_layer * 1)()
@@ -115,11 +149,13 @@ def test_unknown_kind_rejected(q):
     assert h.value is None
 
 
-def _plan(q, n, layers, dtype="c64", batch=4, path=2, ckpt=-1, fuse=1):
+def _plan(q, n, layers, dtype="c64", batch=4, path=2, ckpt=-1, fuse=1, **tuning):
     opt = q.qc_default_options()
     opt.path = path
     opt.ckpt_every = ckpt
     opt.fuse = fuse
+    for k, v in tuning.items():
+        setattr(opt, k, v)
     h = q.qc_create(n, dtype, layers, opt)
     try:
         return q.qc_describe_plan(h, batch), q.qc_workspace_bytes(h, batch)
@@ -140,10 +176,11 @@ def _tile_passes(desc):
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("n", [5, 11, 12, 13, 14, 17, 20, 23, 26])
-def test_tile_passes_cover_every_qubit_once(q, n, dtype):
+@pytest.mark.parametrize("rb", [0, 1, 2, 4])
+def test_tile_passes_cover_every_qubit_once(q, n, dtype, rb):
     layers = [("RY", "theta", 0, 0), ("MS_BRICK", "theta", n, 0), ("ECR_BRICK", "none", 0, 1),
               ("RX", "theta", 0, 0)]
-    desc, _ = _plan(q, n, layers, dtype=dtype, fuse=0)
+    desc, _ = _plan(q, n, layers, dtype=dtype, fuse=0, reg_bits_fwd=rb, reg_bits_bwd=rb)
     tmax = 12 if dtype == "c64" else 11
     for tag in "FB":
         covered = {}

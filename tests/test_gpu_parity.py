@@ -177,6 +177,32 @@ def test_qdi_reupload_matches_oracle(dtype, n, path):
     compare(dtype, n, W.qdi_circuit(n, 3), 3, seed=14, path=path)
 
 
+def test_autotune_picks_a_candidate_and_its_plan_matches_the_oracle():
+    from paper_2506_04891_gb300 import tune
+    n = 16
+    layers = W.ibm_circuit(n, 2)
+    r = tune.autotune(n, layers, 2, fwd_candidates=[dict(tile_bits_fwd=12, reg_bits_fwd=4),
+                                                    dict(tile_bits_fwd=10, reg_bits_fwd=3)],
+                      bwd_candidates=[dict(tile_bits_bwd=11, reg_bits_bwd=3),
+                                      dict(tile_bits_bwd=9, reg_bits_bwd=2)])
+    assert len(r["timings"]) == 4 and all(ms > 0 for _, _, ms in r["timings"])
+    assert r["tuning"]["tile_bits_fwd"] in (10, 12) and r["tuning"]["tile_bits_bwd"] in (9, 11)
+    x, theta, g = W.draw_inputs(n, layers, 2, seed=3)
+    ref = oracle_all(n, layers, x, theta, g)
+    for tuning in ({}, r["tuning"], dict(tile_bits_fwd=9, tile_bits_bwd=8, reg_bits_fwd=2,
+                                         reg_bits_bwd=1, stages=3)):
+        import torch
+        from paper_2506_04891_gb300 import qlayer as Q
+        c = Q.Circuit(n, layers, path=2, tuning=tuning)
+        xt = torch.tensor(x, device="cuda")
+        tt = torch.tensor(theta, device="cuda")
+        ps, ez = c.forward(xt, tt, batch=2)
+        dth, dx = c.backward(xt, tt, ps, torch.tensor(g, device="cuda"))
+        check("c64", "ez", ez.cpu().numpy(), ref["ez"])
+        check("c64", "dx", dx.cpu().numpy(), ref["dx"])
+        check("c64", "dtheta", dth.cpu().numpy(), ref["dth"], batch_sum=2)
+
+
 def test_empty_circuit_and_batch_one():
     for path in (1, 2):
         got = run_gpu(5, [], np.zeros((1, 0)), np.zeros(0), np.full((1, 5), 0.2), dtype="c128", path=path)
