@@ -264,7 +264,8 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // buffers: the next nstage - 1 tiles are in flight while one is processed.
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials into part[slot][block]).
-// PRE = 1: backward pass with a diagonal layer undone in round 0 (P.pre).
+// PRE = 1 / 2: backward pass with a diagonal layer (identity / ring z map)
+// undone in round 0 (P.pre).
 constexpr int tile_minb(int rsize, int ns, int kind, int pre) {
   return (rsize == 4 && kind == 1 && ns == 1 && pre == 0) ? QC_REAL_MINB : (ns == 2 ? QC_BWD_MINB : QC_FWD_MINB);
 }
@@ -326,16 +327,17 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   // zT = ztrans(tid << RB).  zE(a) touches the "element" bits 0..RB-1 (and
   // n-1 for the ring map, via a_0); its pattern pat(a) indexes sratio, the
   // product of the per-bit phase ratios d_p[1] / d_p[0].
-  constexpr bool pre_b = NS == 2 && PRE == 1;
-  const bool ringz = P.pre_zmode == Z_RINGXOR;
-  const int zT = pre_b ? ztrans32(threadIdx.x << RB, n, P.pre_zmode) : 0;
+  // PRE: 1 = identity z map (RZ, Z, S), 2 = ring map z = k ^ rotr(k, 1) (IsingZZ)
+  constexpr bool pre_b = NS == 2 && PRE >= 1;
+  constexpr bool ringz = PRE == 2;
+  const int zT = pre_b ? ztrans32(threadIdx.x << RB, n, ringz ? Z_RINGXOR : Z_IDENT) : 0;
   const R* ptabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
   // element-varying bits: 0..RB-1, plus n-1 for the ring map
   const int semask = ((1 << RB) - 1) | (ringz ? (1 << (n - 1)) : 0);
   // tile-varying bits: the union (not the XOR) of the images of tile bits [t, n)
   int fmask = 0;
   if (pre_b)
-    for (int q = t; q < n; ++q) fmask |= ztrans32(1 << q, n, P.pre_zmode);
+    for (int q = t; q < n; ++q) fmask |= ztrans32(1 << q, n, ringz ? Z_RINGXOR : Z_IDENT);
   // lane p (< n) keeps the sums of tile-only z bit p
   const bool lane_f = (((fmask & ~semask) >> lane) & 1) != 0;
   R mW = 0, mA[4] = {0, 0, 0, 0}, mL = 0;  // W, element-bit sums (bits < RB <= 4), ring bit n-1
@@ -366,6 +368,16 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     return (int)(((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
   };
   auto elem_off = [&](int i) -> int { return (i & cmask) | ((i >> c) << h0); };
+  // elem_off(i0 + k * step) = elem_off(i0) + k * lin_step(step) when the step
+  // keeps clear of the split between the contiguous and the high bits (c >= t,
+  // or step a multiple of 2^c); -1 otherwise.  The loops below then advance
+  // the offset by one add per element instead of re-deriving it.
+  auto lin_step = [&](int step) -> int {
+    if (c >= t) return step;
+    return (step & cmask) == 0 ? ((step >> c) << h0) : -1;
+  };
+  const int ds_half = lin_step(kThreads / 2), ds_full = lin_step(kThreads),
+            ds_pair = lin_step(2 * kThreads);
   // interleaved copies: each run of 16 threads moves psi then lambda of 8
   // consecutive indices (16 distinct bank pairs in shared memory, two 64-byte
   // segments in global memory)
@@ -377,10 +389,23 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     const int base = tile_base(f);
     C* d0 = buf + slot * NS * T;
     if constexpr (IL) {
-      for (int i = il_i, si = il_si; i < T; i += kThreads / 2, si += kThreads) {
-        int gi = base | elem_off(i);
-        if (P.gather) gi = ring_finv32(gi, n);
-        cp_async_elem<sizeof(C)>(&d0[si], &il_src[gi]);
+      if (ds_half >= 0) {
+        int gi = base | elem_off(il_i);
+        for (int i = il_i, si = il_si; i < T; i += kThreads / 2, si += kThreads, gi += ds_half)
+          cp_async_elem<sizeof(C)>(&d0[si], &il_src[P.gather ? ring_finv32(gi, n) : gi]);
+      } else {
+        for (int i = il_i, si = il_si; i < T; i += kThreads / 2, si += kThreads) {
+          int gi = base | elem_off(i);
+          if (P.gather) gi = ring_finv32(gi, n);
+          cp_async_elem<sizeof(C)>(&d0[si], &il_src[gi]);
+        }
+      }
+    } else if (ds_full >= 0) {
+      int gi = base | elem_off(threadIdx.x);
+      for (int i = threadIdx.x, si = sw_tid; i < T; i += kThreads, si += kThreads, gi += ds_full) {
+        const int g2 = P.gather ? ring_finv32(gi, n) : gi;
+        cp_async_elem<sizeof(C)>(&d0[si], &s0b[g2]);
+        if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + si], &s1b[g2]);
       }
     } else {
       for (int i = threadIdx.x, si = sw_tid; i < T; i += kThreads, si += kThreads) {
@@ -449,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           }
         }
         if (pre_b && r == 0) {
-          const int z0 = ztrans32(tile_base(f), n, P.pre_zmode) ^ zT;
+          const int z0 = ztrans32(tile_base(f), n, ringz ? Z_RINGXOR : Z_IDENT) ^ zT;
           const C p0 = diag_phase32<R>(ptabs, P.pre_tb, z0 & ~semask);
           const int z0se = (z0 & ((1 << RB) - 1)) | (ringz ? ((z0 >> (n - 1)) & 1) << RB : 0);
           R Wt = 0, At[5] = {0, 0, 0, 0, 0};
@@ -458,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
             // z bits of element a relative to z0: j < RB: a_j (ident) or
             // a_j ^ a_{j+1} (ring); bit RB: a_0 (ring: z_{n-1})
             const int pi = a, pr = (a ^ (a >> 1)) | ((a & 1) << RB);
-            const C ph = cmul<R>(p0, sratio[z0se ^ (ringz ? pr : pi)]);
+            const C ph = cmul<R>(p0, sratio[z0se ^ (ringz ? pr : pi)]);  // ringz: compile time
             const C y = cmulc<R>(ph, v0[a]), u = cmulc<R>(ph, v1[a]);
             v0[a] = y;
             v1[a] = u;
@@ -562,8 +587,12 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           }
         }
       } else if (sizeof(C) == 8) {
-        for (int i = 2 * threadIdx.x, pi = sw_tid2; i < T; i += 2 * kThreads, pi += 2 * kThreads) {
-          const int gi = base | elem_off(i);
+        // paired 16-byte stores: i = 2 tid + k * 2 kThreads (c >= 1 here, so the
+        // pair never straddles the contiguous segment)
+        int gi_step = base | elem_off(2 * threadIdx.x);
+        for (int i = 2 * threadIdx.x, pi = sw_tid2; i < T;
+             i += 2 * kThreads, pi += 2 * kThreads, gi_step += (ds_pair >= 0 ? ds_pair : 0)) {
+          const int gi = ds_pair >= 0 ? gi_step : (base | elem_off(i));
           if constexpr (IL) {
             const float4 q0 = *reinterpret_cast<const float4*>(&S0[2 * pi]);
             const float4 q1 = *reinterpret_cast<const float4*>(&S0[2 * (pi ^ 1)]);
@@ -579,8 +608,10 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           }
         }
       } else {
-        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-          const int gi = base | elem_off(i);
+        int gi_step = base | elem_off(threadIdx.x);
+        for (int i = threadIdx.x, pi = sw_tid; i < T;
+             i += kThreads, pi += kThreads, gi_step += (ds_full >= 0 ? ds_full : 0)) {
+          const int gi = ds_full >= 0 ? gi_step : (base | elem_off(i));
           d0b[gi] = S0[pi];
           if (NS == 2) d1b[gi] = S1[pi];
         }
@@ -674,8 +705,14 @@ static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const v
   if (NS == 2 && P.pre) {
     if (!kPre || P.kind == 2) return cudaErrorInvalidValue;
     switch (P.kind) {
-      case 0: return launch_tile_k<R, NS, RB, 0, kPre ? 1 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
-      case 1: return launch_tile_k<R, NS, RB, 1, kPre ? 1 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 0:
+        if (P.pre_zmode == Z_RINGXOR)
+          return launch_tile_k<R, NS, RB, 0, kPre ? 2 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+        return launch_tile_k<R, NS, RB, 0, kPre ? 1 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      case 1:
+        if (P.pre_zmode == Z_RINGXOR)
+          return launch_tile_k<R, NS, RB, 1, kPre ? 2 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+        return launch_tile_k<R, NS, RB, 1, kPre ? 1 : 0>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
     }
     return cudaErrorInvalidValue;
   }
