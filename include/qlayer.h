@@ -122,23 +122,28 @@ typedef struct {
   int32_t fuse;
   /* Layer-path tile geometry (0 = the planner's default).  tile_bits_*: log2
    * amplitudes per shared-memory tile (forward default 12 for QC_C64, 11 for
-   * QC_C128; backward 11 / 10; allowed 6 .. 13 / 12 forward, 6 .. 12 / 11
+   * QC_C128; backward 12 / 10; allowed 6 .. 13 / 12 forward, 6 .. 12 / 11
    * backward).  reg_bits_*: index bits held in registers per round (1 .. 4;
-   * defaults 4 forward, 3 backward).  stages: shared-memory tile buffers
-   * (2 or 3; 3 only where two CTAs per SM still fit).  A tuner may try
+   * defaults 4, except 3 for the QC_C128 backward; the planner raises it where a pass needs
+   * more: two for brick layers, and at most eight rounds per pass).
+   * stages_*: shared-memory tile buffers per CTA (1, 2 or 3; default 2, 1 for
+   * the QC_C64 backward; 3 only
+   * where two CTAs per SM still fit; with 1 the CTAs of an SM overlap each
+   * other's copies instead of their own).  A tuner may try
    * several (paper_2506_04891_gb300.tune); results never depend on them
    * beyond rounding. */
   int32_t tile_bits_fwd;
   int32_t tile_bits_bwd;
   int32_t reg_bits_fwd;
   int32_t reg_bits_bwd;
-  int32_t stages;
+  int32_t stages_fwd;
+  int32_t stages_bwd;
 } qc_options;
 
 /* Version of this ABI (major * 100 + minor). */
 QC_API int qc_version(void);
 
-/* Fills *opt with the defaults {-1, 0, 1, 0, 0, 0, 0, 0}. */
+/* Fills *opt with the defaults {-1, 0, 1, 0, 0, 0, 0, 0, 0}. */
 QC_API void qc_default_options(qc_options* opt);
 
 /* Validates a layer list and builds a circuit for n qubits (1 <= n <= 30).

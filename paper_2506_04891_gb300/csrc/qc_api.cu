@@ -186,7 +186,9 @@ int tile_tmax(const qc_circuit* c, int ns) {
   static const int kf = env_knob("QC_TMAX_FWD"), kb = env_knob("QC_TMAX_BWD");
   if (ns == 1 && kf > 0) return kf;
   if (ns == 2 && kb > 0) return kb;
-  if (c->dtype == QC_C64) return ns == 2 ? 11 : 12;
+  // complex64 backward: 2^12 amplitudes of psi and lambda in one buffer (64 KB),
+  // two CTAs per SM overlapping each other's copies (see tile_stages)
+  if (c->dtype == QC_C64) return 12;
   return ns == 2 ? 10 : 11;
 }
 
@@ -222,24 +224,31 @@ int pass_cps(const qc_circuit* c, int batch, const TilePass& tp, int ns) {
   return tile_cps(batch, c->n, tp.t, res);
 }
 int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
-// Register bits per round: the backward holds two states, so it takes one
-// bit fewer (every thread of a 2^11-amplitude tile then has work).
+// Register bits per round: 4, except the complex128 backward (two states of
+// 16-byte amplitudes) takes 3.  With 2^12-amplitude tiles every thread of a
+// 256-thread CTA has work at 4 bits.
 int reg_bits(const qc_circuit* c, int ns) {
   if (ns == 1 && c->opt.reg_bits_fwd > 0) return c->opt.reg_bits_fwd;
   if (ns == 2 && c->opt.reg_bits_bwd > 0) return c->opt.reg_bits_bwd;
   static const int kf = env_knob("QC_RB_FWD"), kb = env_knob("QC_RB_BWD");
   if (ns == 1 && kf > 0) return kf;
   if (ns == 2 && kb > 0) return kb;
-  return ns == 2 ? 3 : 4;
+  return (ns == 2 && c->dtype == QC_C128) ? 3 : 4;
 }
 
-// Shared-memory tile buffers of a pass.  Two (one tile in flight while one is
-// processed) measured faster on zz26 than three: the passes are bound by issue
-// and shared-memory latency, not by bytes in flight.  QC_TILE_STAGES=3 takes
-// three where two CTAs per SM still fit.
+// Shared-memory tile buffers of a pass.  Forward: two (one tile in flight
+// while one is processed) measured faster on zz26 than three: the passes are
+// bound by issue and shared-memory traffic, not by bytes in flight.  Complex64
+// backward: one buffer of 2^12 amplitudes per CTA; the two CTAs of an SM
+// overlap each other's copies, and the larger tile takes 7 instead of 10
+// shared-memory rounds per 26-qubit layer (measured 6% faster on zz26 than
+// 2^11 tiles with two buffers).  Three buffers only where two CTAs still fit.
 int tile_stages(const qc_circuit* c, TilePass& P, int ns, int rsize) {
   static const int ke = env_knob("QC_TILE_STAGES");
-  const int k = c->opt.stages > 0 ? c->opt.stages : ke;
+  const int ko = ns == 1 ? c->opt.stages_fwd : c->opt.stages_bwd;
+  int k = ko > 0 ? ko : ke;
+  if (k == 0 && ns == 2 && c->dtype == QC_C64) k = 1;
+  if (k == 1) return 1;
   if (k != 3) return 2;
   P.nstage = 3;
   const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
@@ -1241,7 +1250,7 @@ QC_API void qc_default_options(qc_options* opt) {
   opt->fuse = 1;
   opt->tile_bits_fwd = opt->tile_bits_bwd = 0;
   opt->reg_bits_fwd = opt->reg_bits_bwd = 0;
-  opt->stages = 0;
+  opt->stages_fwd = opt->stages_bwd = 0;
 }
 
 QC_API const char* qc_last_error(void) { return g_last_error.c_str(); }
@@ -1266,8 +1275,8 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
       return fail(QC_ERR_INVALID, "options.tile_bits_bwd out of range");
     if (o.reg_bits_fwd < 0 || o.reg_bits_fwd > 4 || o.reg_bits_bwd < 0 || o.reg_bits_bwd > 4)
       return fail(QC_ERR_INVALID, "options.reg_bits_* must be in 0 .. 4");
-    if (o.stages != 0 && o.stages != 2 && o.stages != 3)
-      return fail(QC_ERR_INVALID, "options.stages must be 0, 2 or 3");
+    if (o.stages_fwd < 0 || o.stages_fwd > 3 || o.stages_bwd < 0 || o.stages_bwd > 3)
+      return fail(QC_ERR_INVALID, "options.stages_* must be in 0 .. 3");
   }
   auto c = std::make_unique<qc_circuit>();
   c->n = n;

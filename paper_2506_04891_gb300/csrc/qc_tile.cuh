@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     if (fn < tps) issue(fn, sn);
     cp_async_commit();
     if (nst == 3) cp_async_wait_group<2>();
-    else cp_async_wait_group<1>();
+    else if (nst == 2) cp_async_wait_group<1>();
+    else cp_async_wait_group<0>();  // one buffer: the tile just issued
     __syncthreads();
     C* S0 = buf + (long long)slot * NS * T;
     C* S1 = S0 + T;

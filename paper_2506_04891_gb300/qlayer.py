@@ -48,9 +48,11 @@ class qc_options(ctypes.Structure):
     _fields_ = [("ckpt_every", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("fuse", ctypes.c_int32), ("tile_bits_fwd", ctypes.c_int32),
                 ("tile_bits_bwd", ctypes.c_int32), ("reg_bits_fwd", ctypes.c_int32),
-                ("reg_bits_bwd", ctypes.c_int32), ("stages", ctypes.c_int32)]
+                ("reg_bits_bwd", ctypes.c_int32), ("stages_fwd", ctypes.c_int32),
+                ("stages_bwd", ctypes.c_int32)]
 
-TUNING_FIELDS = ("tile_bits_fwd", "tile_bits_bwd", "reg_bits_fwd", "reg_bits_bwd", "stages")
+TUNING_FIELDS = ("tile_bits_fwd", "tile_bits_bwd", "reg_bits_fwd", "reg_bits_bwd", "stages_fwd",
+                 "stages_bwd")
 
 
 class QCError(RuntimeError):

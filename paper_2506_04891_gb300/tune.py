@@ -19,7 +19,7 @@ import itertools
 from . import qlayer as Q
 from . import workloads as W
 
-DEFAULT_TILE = {"c64": (12, 11), "c128": (11, 10)}  # (forward, backward) tile bits
+DEFAULT_TILE = {"c64": (12, 12), "c128": (11, 10)}  # (forward, backward) tile bits
 MAX_TILE = {"c64": (13, 12), "c128": (12, 11)}
 
 
@@ -27,11 +27,12 @@ def candidates(n: int, dtype: str):
     """Forward and backward candidate lists around the defaults."""
     f0, b0 = DEFAULT_TILE[dtype]
     fm, bm = MAX_TILE[dtype]
-    fwd = [dict(tile_bits_fwd=t, reg_bits_fwd=r, stages=s)
-           for t, r, s in itertools.product([f0 - 1, f0, min(f0 + 1, fm)], [3, 4], [2, 3])
+    fwd = [dict(tile_bits_fwd=t, reg_bits_fwd=r, stages_fwd=s)
+           for t, r, s in itertools.product([f0 - 1, f0, min(f0 + 1, fm)], [3, 4], [1, 2, 3])
            if t <= n]
-    bwd = [dict(tile_bits_bwd=t, reg_bits_bwd=r)
-           for t, r in itertools.product([b0 - 1, b0, min(b0 + 1, bm)], [2, 3, 4]) if t <= n]
+    bwd = [dict(tile_bits_bwd=t, reg_bits_bwd=r, stages_bwd=s)
+           for t, r, s in itertools.product([b0 - 1, b0, min(b0 + 1, bm)], [2, 3, 4], [1, 2])
+           if t <= n]
     # drop duplicates that clamping produced
     dedup = lambda xs: [dict(t) for t in {tuple(sorted(d.items())) for d in xs}]
     return sorted(dedup(fwd), key=lambda d: sorted(d.items())), sorted(dedup(bwd), key=lambda d: sorted(d.items()))

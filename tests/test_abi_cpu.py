@@ -115,10 +115,10 @@ def test_tuning_options_shape_the_plan_and_are_validated(q):
         return {(int(d["t"]), int(d["rb"])) for d in
                 (dict(re.findall(r"(\w+)=(-?\d+)", l.split("[")[0])) for l in desc.splitlines()
                  if l.startswith(tag) and " TILE " in l)}
-    assert geo(base, "F ") == {(12, 4)} and geo(base, "B ") == {(11, 3)}
+    assert geo(base, "F ") == {(12, 4)} and geo(base, "B ") == {(12, 4)}
     assert geo(tuned, "F ") == {(10, 3)} and geo(tuned, "B ") == {(9, 2)}
     for bad in (dict(tile_bits_fwd=14), dict(tile_bits_bwd=13), dict(tile_bits_fwd=5),
-                dict(reg_bits_bwd=5), dict(stages=4)):
+                dict(reg_bits_bwd=5), dict(stages_fwd=4), dict(stages_bwd=-1)):
         with pytest.raises(q.QCError):
             q.Circuit(16, layers, tuning=bad)
     with pytest.raises(q.QCError):

@@ -190,7 +190,7 @@ def test_autotune_picks_a_candidate_and_its_plan_matches_the_oracle():
     x, theta, g = W.draw_inputs(n, layers, 2, seed=3)
     ref = oracle_all(n, layers, x, theta, g)
     for tuning in ({}, r["tuning"], dict(tile_bits_fwd=9, tile_bits_bwd=8, reg_bits_fwd=2,
-                                         reg_bits_bwd=1, stages=3)):
+                                         reg_bits_bwd=1, stages_fwd=3, stages_bwd=1)):
         import torch
         from paper_2506_04891_gb300 import qlayer as Q
         c = Q.Circuit(n, layers, path=2, tuning=tuning)
