@@ -124,8 +124,21 @@ inline int tile_resident(int rsize, int kind, int ns, int pre) {
 // (backward, deferred), backward pre-diagonal marginals and phase-ratio table,
 // end.  Every block starts on a 16-byte boundary.
 struct TileSmem {
-  size_t buf, sco, sred, sdef, smarg, sratio, end;
+  size_t buf, sco, sred, sdef, smarg, sratio, fph, end;
 };
+// Forward pre/post phase block (one per diagonal the pass multiplies in):
+// element-varying z bits, the compressed pattern of each per-thread element,
+// and the product of the per-bit phase ratios for every pattern.
+constexpr int kFphMaxSE = 8;
+struct FwdPhaseMeta {
+  int ok;      // 0: the tile has more than 16 elements per thread or 8 such bits
+  int nse, semask;
+  int sepos[kFphMaxSE];
+  int patk[16];
+};
+constexpr size_t kFphBytes(int rsize) {
+  return ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15) + (size_t)(1 << kFphMaxSE) * 2 * rsize;
+}
 __host__ __device__ inline size_t tsm_align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline TileSmem tile_smem_layout(const TilePass& P, int ns, int rsize) {
   TileSmem L;
@@ -136,7 +149,9 @@ __host__ __device__ inline TileSmem tile_smem_layout(const TilePass& P, int ns, 
   L.smarg = tsm_align16(L.sdef + (ns == 2 && P.defer ? (size_t)P.ncomp * kThreads * rsize : 0));
   const bool pre = ns == 2 && P.pre;
   L.sratio = tsm_align16(L.smarg + (pre ? (size_t)kWarps * (P.n + 1) * sizeof(double) : 0));
-  L.end = tsm_align16(L.sratio + (pre ? (size_t)32 * 2 * rsize : 0));
+  L.fph = tsm_align16(L.sratio + (pre ? (size_t)32 * 2 * rsize : 0));
+  const size_t nfph = ns == 1 ? (size_t)(P.pre ? 1 : 0) + (P.post ? 1 : 0) : 0;
+  L.end = tsm_align16(L.fph + nfph * kFphBytes(rsize));
   return L;
 }
 

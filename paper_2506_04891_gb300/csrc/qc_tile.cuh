@@ -264,6 +264,82 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // buffers: the next nstage - 1 tiles are in flight while one is processed.
 // NS = 1: forward (apply M to psi).  NS = 2: backward (undo M on psi and
 // lambda, accumulate gradient partials into part[slot][block]).
+// Forward diagonal phase multiplied into a tile (pre: after the load, post:
+// at the store).  Thread tid handles the elements i = tid + 256 k; with
+// off() the tile's element-to-index map (linear over GF(2)) and z linear,
+// z(base | off(i)) = z0 ^ zK(k), z0 = z(base | off(tid)), zK(k) = z(off(256 k)).
+// zK touches a few "element" bits SE, so phase(z) = phase(z0 without SE) *
+// ratio[pattern of z on SE], ratio[] the products of the per-bit phase ratios
+// d_p[1] / d_p[0] (from the factored tables), set up once per CTA.
+template <class R>
+__device__ void fph_setup(unsigned char* blk, const R* tabs, int tb, int zm, int n, int t, int c,
+                          int h0) {
+  FwdPhaseMeta* M = reinterpret_cast<FwdPhaseMeta*>(blk);
+  cx<R>* ratio = reinterpret_cast<cx<R>*>(blk + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
+  const int KB = t > 8 ? t - 8 : 0;
+  if (threadIdx.x == 0) {
+    const int cm = (1 << c) - 1;
+    auto eoff = [&](int i) { return (i & cm) | ((i >> c) << h0); };
+    int zk[4] = {0, 0, 0, 0}, se = 0;
+    M->ok = KB <= 4;
+    if (M->ok) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < KB) {
+          zk[j] = ztrans32(eoff(256 << j), n, zm);
+          se |= zk[j];
+        }
+      M->ok = __popc(se) <= kFphMaxSE;
+    }
+    if (M->ok) {
+      int nse = 0;
+      for (int p = 0; p < n; ++p)
+        if ((se >> p) & 1) M->sepos[nse++] = p;
+      M->nse = nse;
+      M->semask = se;
+      for (int k = 0; k < (1 << KB); ++k) {
+        int z = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < KB && ((k >> j) & 1)) z ^= zk[j];
+        int pat = 0;
+        for (int j = 0; j < nse; ++j)
+          if ((z >> M->sepos[j]) & 1) pat |= 1 << j;
+        M->patk[k] = pat;
+      }
+    }
+  }
+  __syncthreads();
+  if (!M->ok) return;
+  const int nse = M->nse;
+  for (int e = threadIdx.x; e < (1 << nse); e += kThreads) {
+    cx<R> v = mk<R>(1, 0);
+    for (int j = 0; j < nse; ++j) {
+      if (!((e >> j) & 1)) continue;
+      const int p = M->sepos[j];
+      const int sblk = p / tb, i = p % tb;
+      const R* tt = tabs + 2LL * sblk * (1LL << tb);
+      v = cmul<R>(v, cmulc<R>(ldc<R>(tt), ldc<R>(tt + 2 * (1 << i))));  // T[1 << i] conj(T[0])
+    }
+    ratio[e] = v;
+  }
+}
+// per (thread, tile): the base phase and the element-bit pattern of z0
+template <class R>
+__device__ __forceinline__ void fph_tile(const unsigned char* blk, const R* tabs, int tb, int z0,
+                                         cx<R>& p0, int& z0se) {
+  const FwdPhaseMeta* M = reinterpret_cast<const FwdPhaseMeta*>(blk);
+  z0se = 0;
+  for (int j = 0; j < M->nse; ++j) z0se |= ((z0 >> M->sepos[j]) & 1) << j;
+  p0 = diag_phase32<R>(tabs, tb, z0 & ~M->semask);
+}
+template <class R>
+__device__ __forceinline__ cx<R> fph_elem(const unsigned char* blk, cx<R> p0, int z0se, int k) {
+  const FwdPhaseMeta* M = reinterpret_cast<const FwdPhaseMeta*>(blk);
+  const cx<R>* ratio = reinterpret_cast<const cx<R>*>(blk + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
+  return cmul<R>(p0, ratio[z0se ^ M->patk[k]]);
+}
+
 // PRE = 1 / 2: backward pass with a diagonal layer (identity / ring z map)
 // undone in round 0 (P.pre).
 constexpr int tile_minb(int rsize, int ns, int kind, int pre) {
@@ -293,6 +369,9 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   // ratio table over the element-varying z bits
   double* smarg = reinterpret_cast<double*>(smraw + lay.smarg);
   C* sratio = reinterpret_cast<C*>(smraw + lay.sratio);
+  // forward pre / post phase blocks
+  unsigned char* fph_pre = smraw + lay.fph;
+  unsigned char* fph_post = smraw + lay.fph + (P.pre ? kFphBytes((int)sizeof(R)) : 0);
 
   const long long tps = 1LL << (n - t);
   const int b = blockIdx.x / cps;
@@ -356,6 +435,13 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
       sratio[threadIdx.x] = v;
     }
   }
+
+  const R* fpre_tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
+  const R* fpost_tabs = coef + P.post_coef + (long long)b * P.post_bstride;
+  if (NS == 1 && P.pre) fph_setup<R>(fph_pre, fpre_tabs, P.pre_tb, P.pre_zmode, n, t, c, h0);
+  if (NS == 1 && P.post) fph_setup<R>(fph_post, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0);
+  const bool fpre_ok = NS == 1 && P.pre && reinterpret_cast<const FwdPhaseMeta*>(fph_pre)->ok;
+  const bool fpost_ok = NS == 1 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
 
   // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
   // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
@@ -438,10 +524,20 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     C* S1 = S0 + T;
     if (NS == 1 && P.pre) {
       const int base = tile_base(f);
-      const R* tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
-      for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
-        const long long k = base | elem_off(i);
-        S0[pi] = cmul<R>(diag_phase<R>(tabs, P.pre_tb, ztrans(k, n, P.pre_zmode)), S0[pi]);
+      if (fpre_ok) {
+        if (threadIdx.x < T) {
+          C p0;
+          int z0se;
+          fph_tile<R>(fph_pre, fpre_tabs, P.pre_tb, ztrans32(base | elem_off(threadIdx.x), n, P.pre_zmode),
+                      p0, z0se);
+          for (int i = threadIdx.x, pi = sw_tid, k = 0; i < T; i += kThreads, pi += kThreads, ++k)
+            S0[pi] = cmul<R>(fph_elem<R>(fph_pre, p0, z0se, k), S0[pi]);
+        }
+      } else {
+        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
+          const int k = base | elem_off(i);
+          S0[pi] = cmul<R>(diag_phase32<R>(fpre_tabs, P.pre_tb, ztrans32(k, n, P.pre_zmode)), S0[pi]);
+        }
       }
       __syncthreads();
     }
@@ -573,11 +669,18 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     if (P.store) {
       const int base = tile_base(f);
       if (P.post || P.scatter) {
-        const R* tabs = coef + P.post_coef + (long long)b * P.post_bstride;
-        for (int i = threadIdx.x, pi = sw_tid; i < T; i += kThreads, pi += kThreads) {
+        C p0 = mk<R>(1, 0);
+        int z0se = 0;
+        if (fpost_ok && threadIdx.x < T)
+          fph_tile<R>(fph_post, fpost_tabs, P.post_tb, ztrans32(base | elem_off(threadIdx.x), n, P.post_zmode),
+                      p0, z0se);
+        for (int i = threadIdx.x, pi = sw_tid, k = 0; i < T; i += kThreads, pi += kThreads, ++k) {
           const int kl = base | elem_off(i);
           C e = S0[pi];
-          if (NS == 1 && P.post) e = cmul<R>(diag_phase<R>(tabs, P.post_tb, ztrans(kl, n, P.post_zmode)), e);
+          if (NS == 1 && P.post)
+            e = cmul<R>(fpost_ok ? fph_elem<R>(fph_post, p0, z0se, k)
+                                 : diag_phase32<R>(fpost_tabs, P.post_tb, ztrans32(kl, n, P.post_zmode)),
+                        e);
           const int gd = P.scatter ? ring_finv32(kl, n) : kl;
           if constexpr (IL) {
             d0b[gd] = S0[2 * pi];
