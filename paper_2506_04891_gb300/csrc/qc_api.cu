@@ -427,7 +427,8 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     // deferred reduction when every gradient op is single-qubit and rounds fit
     for (int r = 0; r < 4; ++r)
       for (int i = 0; i < 4; ++i) P.rslot[r][i] = P.rcslot[r][i] = -1;
-    bool defer = P.nrounds <= 4 && slot > 0;
+    // the kernel keeps deferred sums for 4 rounds (3 at 4 register bits)
+    bool defer = P.nrounds <= (RB == 4 ? 3 : 4) && slot > 0;
     for (int k = 0; k < P.nops && defer; ++k) {
       const TileOp& o = P.ops[k];
       if (o.np == 0 && !o.ck) continue;
@@ -659,11 +660,9 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
           if (!h.steps.empty()) {
             Step& f0 = h.steps.front();
             TilePass& tp = f0.tp;
-            // one round-0 group per thread (t - RB <= 8) and lanes whose z bits
-            // never meet the tile's (t >= RB + 6)
-            if (tp.c == tp.t && tp.nrounds > 0 && tp.rlo[0] == 0 && (f0.rb == 3 || f0.rb == 4) &&
-                tp.t >= f0.rb + 6 &&
-                tp.t - f0.rb <= 8 &&
+            // a contiguous pass of 2^9 .. 2^12 amplitudes (2 .. 16 per thread);
+            // the kernel's pre variant is built for 3 and 4 register bits
+            if (tp.c == tp.t && tp.nrounds > 0 && tp.t >= 9 && tp.t <= 12 && (f0.rb == 3 || f0.rb == 4) &&
                 (Li.zmode == Z_IDENT || Li.zmode == Z_RINGXOR)) {
               tp.pre = 1;
               tp.pre_zmode = Li.zmode;
@@ -671,7 +670,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
               tp.pre_coef = Li.coef_off;
               tp.pre_bstride = Li.coef_bstride;
               tp.pre_grad = (Li.diff && Li.nparams > 0) ? 1 : 0;
-              f0.cps = pass_cps(c, batch, tp, 2);  // the pre variant holds fewer CTAs
+              f0.cps = pass_cps(c, batch, tp, 2);
               h.pre_layer = i;
               i = h.lo - 1;
               bgroups.push_back(std::move(h));

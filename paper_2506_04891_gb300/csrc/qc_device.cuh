@@ -22,6 +22,9 @@
 #ifndef QC_REAL_MINB
 #define QC_REAL_MINB 3
 #endif
+#ifndef QC_PRE_MINB
+#define QC_PRE_MINB 2
+#endif
 
 namespace qc {
 

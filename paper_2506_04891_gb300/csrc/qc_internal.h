@@ -113,9 +113,12 @@ struct TilePass {
 };
 
 // Resident CTAs per SM a tile pass is compiled for (see the launch bounds of
-// the tile kernel): the complex64 real-gate forward pass 3, others 2.
+// the tile kernel): the complex64 real-gate forward pass 3, others 2 (a
+// fused-diagonal backward pass at one CTA per SM without spills measured
+// slower than two with some).
 inline int tile_resident(int rsize, int kind, int ns, int pre) {
-  return (rsize == 4 && kind == 1 && ns == 1 && !pre) ? 3 : 2;
+  (void)pre;
+  return (rsize == 4 && kind == 1 && ns == 1) ? 3 : 2;
 }
 
 // Shared-memory carve-out of a tile pass, in bytes from the dynamic base, used
@@ -124,8 +127,12 @@ inline int tile_resident(int rsize, int kind, int ns, int pre) {
 // (backward, deferred), backward pre-diagonal marginals and phase-ratio table,
 // end.  Every block starts on a 16-byte boundary.
 struct TileSmem {
-  size_t buf, sco, sred, sdef, smarg, sratio, fph, end;
+  size_t buf, sco, sred, sdef, smarg, sratio, smacc, fph, end;
 };
+// backward pre-diagonal: per-thread running marginal sums kept in shared
+// memory (W, up to 8 element-bit sums, up to 2 tile-and-lane bits, the lane's
+// tile-only bit)
+constexpr int kPreAcc = 12;
 // Forward pre/post phase block (one per diagonal the pass multiplies in):
 // element-varying z bits, the compressed pattern of each per-thread element,
 // and the product of the per-bit phase ratios for every pattern.
@@ -149,8 +156,9 @@ __host__ __device__ inline TileSmem tile_smem_layout(const TilePass& P, int ns, 
   L.smarg = tsm_align16(L.sdef + (ns == 2 && P.defer ? (size_t)P.ncomp * kThreads * rsize : 0));
   const bool pre = ns == 2 && P.pre;
   L.sratio = tsm_align16(L.smarg + (pre ? (size_t)kWarps * (P.n + 1) * sizeof(double) : 0));
-  L.fph = tsm_align16(L.sratio + (pre ? (size_t)32 * 2 * rsize : 0));
-  const size_t nfph = ns == 1 ? (size_t)(P.pre ? 1 : 0) + (P.post ? 1 : 0) : 0;
+  L.smacc = L.sratio;
+  L.fph = tsm_align16(L.smacc + (pre ? (size_t)kPreAcc * kThreads * rsize : 0));
+  const size_t nfph = ns == 1 ? (size_t)(P.pre ? 1 : 0) + (P.post ? 1 : 0) : (pre ? 1 : 0);
   L.end = tsm_align16(L.fph + nfph * kFphBytes(rsize));
   return L;
 }

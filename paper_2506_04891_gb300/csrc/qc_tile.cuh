@@ -343,7 +343,9 @@ __device__ __forceinline__ cx<R> fph_elem(const unsigned char* blk, cx<R> p0, in
 // PRE = 1 / 2: backward pass with a diagonal layer (identity / ring z map)
 // undone in round 0 (P.pre).
 constexpr int tile_minb(int rsize, int ns, int kind, int pre) {
-  return (rsize == 4 && kind == 1 && ns == 1 && pre == 0) ? QC_REAL_MINB : (ns == 2 ? QC_BWD_MINB : QC_FWD_MINB);
+  return (rsize == 4 && kind == 1 && ns == 1 && pre == 0) ? QC_REAL_MINB
+         : (ns == 2 && pre > 0) ? QC_PRE_MINB
+         : (ns == 2 ? QC_BWD_MINB : QC_FWD_MINB);
 }
 template <class R, int NS, int RB, int KIND, int PRE>
 __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE)) k_tile(const __grid_constant__ TilePass P,
@@ -368,7 +370,6 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   // backward pre-diagonal: [kWarps][n + 1] marginal sums, then the phase
   // ratio table over the element-varying z bits
   double* smarg = reinterpret_cast<double*>(smraw + lay.smarg);
-  C* sratio = reinterpret_cast<C*>(smraw + lay.sratio);
   // forward pre / post phase blocks
   unsigned char* fph_pre = smraw + lay.fph;
   unsigned char* fph_post = smraw + lay.fph + (P.pre ? kFphBytes((int)sizeof(R)) : 0);
@@ -393,47 +394,48 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
       for (int s = 0; s < P.ncomp; ++s) sdef[s * kThreads + threadIdx.x] = 0;
   }
 
-  R acct[4][4];
+  constexpr int kAR = RB == 4 ? 3 : 4;  // deferred rounds (the planner matches)
+  R acct[kAR][4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < kAR; ++r)
 #pragma unroll
     for (int i = 0; i < 4; ++i) acct[r][i] = 0;
 
-  // Backward pre-diagonal (undo D, gradient from bit marginals of
-  // w = Im(conj(lambda) psi), which D leaves unchanged).  Round 0 holds index
-  // bits 0..RB-1 of element a in register a; z is linear over GF(2), so for
-  // k = base | tid << RB | a:  z = z0 ^ zE(a), z0 = ztrans(base) ^ zT,
-  // zT = ztrans(tid << RB).  zE(a) touches the "element" bits 0..RB-1 (and
-  // n-1 for the ring map, via a_0); its pattern pat(a) indexes sratio, the
-  // product of the per-bit phase ratios d_p[1] / d_p[0].
-  // PRE: 1 = identity z map (RZ, Z, S), 2 = ring map z = k ^ rotr(k, 1) (IsingZZ)
+  // Backward pre-diagonal (PRE = 1 identity, 2 ring z map): before round 0 a
+  // sweep over the tile undoes a diagonal layer D on psi and lambda and sums
+  // the bit marginals of w = Im(conj(lambda) psi), which D leaves unchanged.
+  // The pass is contiguous (c = t), thread tid holds elements i = tid + 256 k,
+  // and z is linear over GF(2): z(base | i) = z0 ^ zK(k), z0 = z(base | tid).
+  // The phase comes from the forward helper (base phase x per-bit ratios).
+  // Marginals: the element bits SE (those zK touches) add each element's
+  // exact bit; bits that vary with both the tile and the lane (the ring map's
+  // n-1) are summed per thread and tile; tile-only bits are warp-uniform and
+  // lane p keeps bit p after one warp sum per tile; every other bit follows
+  // from the thread's total W at the end.  Running sums sit in this thread's
+  // shared-memory columns: [0] W, [1 .. 8] SE bits, [9 .. 10] tile-and-lane
+  // bits, [11] the lane's tile-only bit.
   constexpr bool pre_b = NS == 2 && PRE >= 1;
-  constexpr bool ringz = PRE == 2;
-  const int zT = pre_b ? ztrans32(threadIdx.x << RB, n, ringz ? Z_RINGXOR : Z_IDENT) : 0;
+  constexpr int zmc = PRE == 2 ? Z_RINGXOR : Z_IDENT;
   const R* ptabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
-  // element-varying bits: 0..RB-1, plus n-1 for the ring map
-  const int semask = ((1 << RB) - 1) | (ringz ? (1 << (n - 1)) : 0);
-  // tile-varying bits: the union (not the XOR) of the images of tile bits [t, n)
-  int fmask = 0;
-  if (pre_b)
-    for (int q = t; q < n; ++q) fmask |= ztrans32(1 << q, n, ringz ? Z_RINGXOR : Z_IDENT);
-  // lane p (< n) keeps the sums of tile-only z bit p
-  const bool lane_f = (((fmask & ~semask) >> lane) & 1) != 0;
-  R mW = 0, mA[4] = {0, 0, 0, 0}, mL = 0;  // W, element-bit sums (bits < RB <= 4), ring bit n-1
-  R mF = 0;                                // lane p: tile-only bit p
+  unsigned char* fph_bpre = smraw + lay.fph;
+  R* macc = reinterpret_cast<R*>(smraw + lay.smacc) + threadIdx.x;
+  int zT = 0, fmask = 0, flmask = 0, flpos0 = -1, flpos1 = -1;
+  bool lane_f = false;
   if (pre_b) {
-    if (threadIdx.x < (2 << RB)) {
-      // pattern bits j < RB <-> z bit j; bit RB <-> z bit n-1 (ring map)
-      C v = mk<R>(1, 0);
-      for (int j = 0; j <= RB; ++j) {
-        if (!((threadIdx.x >> j) & 1)) continue;
-        const int p = j < RB ? j : n - 1;
-        const int sblk = p / P.pre_tb, i = p % P.pre_tb;
-        const R* tb = ptabs + 2LL * sblk * (1LL << P.pre_tb);
-        v = cmul<R>(v, cmulc<R>(ldc<R>(tb), ldc<R>(tb + 2 * (1 << i))));  // T[1 << i] conj(T[0])
+    fph_setup<R>(fph_bpre, ptabs, P.pre_tb, zmc, n, t, c, h0);
+    zT = ztrans32(threadIdx.x, n, zmc);
+    int lmask = 0;
+    for (int q = t; q < n; ++q) fmask |= ztrans32(1 << q, n, zmc);
+    for (int q = 0; q < 5; ++q) lmask |= ztrans32(1 << q, n, zmc);
+    const int sem = reinterpret_cast<const FwdPhaseMeta*>(fph_bpre)->semask;
+    flmask = fmask & lmask & ~sem;  // one bit (n-1) for the ring map, none for the identity
+    for (int p = 0; p < n; ++p)
+      if ((flmask >> p) & 1) {
+        if (flpos0 < 0) flpos0 = p;
+        else flpos1 = p;
       }
-      sratio[threadIdx.x] = v;
-    }
+    lane_f = (((fmask & ~lmask & ~sem) >> lane) & 1) != 0;
+    for (int j = 0; j < kPreAcc; ++j) macc[j * kThreads] = 0;
   }
 
   const R* fpre_tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
@@ -541,6 +543,79 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
       }
       __syncthreads();
     }
+    if (pre_b) {
+      const int base = tile_base(f);
+      const FwdPhaseMeta* pm = reinterpret_cast<const FwdPhaseMeta*>(fph_bpre);
+      const int nse = pm->nse;
+      const int z0 = ztrans32(base | threadIdx.x, n, zmc);  // c = t: elem_off(i) = i
+      // Contiguous pass: element k is index bits 8 .. t-1, so the element z
+      // bits are 7 .. t-1 (ring: z_p = k_p ^ k_{p+1}) or 8 .. t-1 (identity)
+      // and the pattern of element k is k ^ (k << 1) or k -- compile-time
+      // constants in the unrolled loop below (the per-CTA table's bit order).
+      constexpr int zlo = PRE == 2 ? 7 : 8;
+      const int z0se = (z0 >> zlo) & ((1 << nse) - 1);  // nse = t - 7 (ring) or t - 8
+      const C p0 = diag_phase32<R>(ptabs, P.pre_tb, z0 & ~pm->semask);
+      const C* ratio = reinterpret_cast<const C*>(fph_bpre + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
+      R Wt = 0, Ase[5] = {0, 0, 0, 0, 0};
+      auto load = [&](int si, C& x, C& l) {
+        if constexpr (IL) {
+          const float4 q = *reinterpret_cast<const float4*>(&S0[2 * si]);
+          x = mk<R>(q.x, q.y);
+          l = mk<R>(q.z, q.w);
+        } else {
+          x = S0[si];
+          l = S1[si];
+        }
+      };
+      auto store = [&](int si, C y, C u) {
+        if constexpr (IL) {
+          *reinterpret_cast<float4*>(&S0[2 * si]) = make_float4(y.x, y.y, u.x, u.y);
+        } else {
+          S0[si] = y;
+          S1[si] = u;
+        }
+      };
+      const int ne = T >> 8;  // 2 .. 16 elements per thread
+#pragma unroll
+      for (int k = 0; k < 16; k += 2) {
+        if (k < ne) {
+          const int si = sw_tid + k * kThreads;  // the swizzle only folds bits below 8
+          C x0, l0, x1, l1;
+          load(si, x0, l0);
+          load(si + kThreads, x1, l1);
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int kk = k + e;
+            const int pat = PRE == 2 ? (kk ^ (kk << 1)) : kk;
+            const C ph = cmul<R>(p0, ratio[z0se ^ pat]);
+            const C y = cmulc<R>(ph, e ? x1 : x0), u = cmulc<R>(ph, e ? l1 : l0);
+            store(si + e * kThreads, y, u);
+            const R w = im_cdot<R>(u, y);
+            Wt += w;
+            // the element bit j of z is z0se_j ^ pat_j: sum w where pat_j is
+            // set, and fold z0se in when the tile is done
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+              if ((pat >> j) & 1) Ase[j] += w;
+          }
+        }
+      }
+      // Ase[j] so far sums w over pat_j = 1; z_j = z0se_j ^ pat_j
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if ((z0se >> j) & 1) Ase[j] = Wt - Ase[j];
+      if (P.pre_grad) {
+        macc[0] += Wt;
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+          if (j < nse) macc[(1 + j) * kThreads] += Ase[j];
+        if (flpos0 >= 0 && ((z0 >> flpos0) & 1)) macc[9 * kThreads] += Wt;
+        if (flpos1 >= 0 && ((z0 >> flpos1) & 1)) macc[10 * kThreads] += Wt;
+        const R sw = warp_sum_r<R>(Wt);
+        if (lane_f && ((z0 >> lane) & 1)) macc[11 * kThreads] += sw;
+      }
+      __syncthreads();
+    }
 
 #pragma unroll 1
     for (int r = 0; r < P.nrounds; ++r) {
@@ -570,42 +645,6 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
             if (NS == 2) v1[a] = S1[ad];
           }
         }
-        if (pre_b && r == 0) {
-          const int z0 = ztrans32(tile_base(f), n, ringz ? Z_RINGXOR : Z_IDENT) ^ zT;
-          const C p0 = diag_phase32<R>(ptabs, P.pre_tb, z0 & ~semask);
-          const int z0se = (z0 & ((1 << RB) - 1)) | (ringz ? ((z0 >> (n - 1)) & 1) << RB : 0);
-          R Wt = 0, At[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-          for (int a = 0; a < (1 << RB); ++a) {
-            // z bits of element a relative to z0: j < RB: a_j (ident) or
-            // a_j ^ a_{j+1} (ring); bit RB: a_0 (ring: z_{n-1})
-            const int pi = a, pr = (a ^ (a >> 1)) | ((a & 1) << RB);
-            const C ph = cmul<R>(p0, sratio[z0se ^ (ringz ? pr : pi)]);  // ringz: compile time
-            const C y = cmulc<R>(ph, v0[a]), u = cmulc<R>(ph, v1[a]);
-            v0[a] = y;
-            v1[a] = u;
-            const R w = im_cdot<R>(u, y);
-            Wt += w;
-            if (ringz) {
-#pragma unroll
-              for (int j = 0; j <= RB; ++j)
-                if ((pr >> j) & 1) At[j] += w;
-            } else {
-#pragma unroll
-              for (int j = 0; j < RB; ++j)
-                if ((pi >> j) & 1) At[j] += w;
-            }
-          }
-          if (P.pre_grad) {
-            mW += Wt;
-#pragma unroll
-            for (int j = 0; j < RB && j < 4; ++j) mA[j] += At[j];
-            if (ringz) mL += ((z0 >> (n - 1)) & 1) ? Wt - At[RB] : At[RB];
-            // tile-only bits: uniform over the warp; lane p keeps bit p
-            const R sw = warp_sum_r<R>(Wt);
-            if (lane_f && ((z0 >> lane) & 1)) mF += sw;
-          }
-        }
         tile_bit<R, NS, RB, KIND, 0>(P, r, v0, v1, sco, acc);
         if (RB > 1) tile_bit<R, NS, RB, KIND, (RB > 1 ? 1 : 0)>(P, r, v0, v1, sco, acc);
         if (RB > 2) tile_bit<R, NS, RB, KIND, (RB > 2 ? 2 : 0)>(P, r, v0, v1, sco, acc);
@@ -630,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           // tile: the pass's own slots in registers, companion slots in this
           // thread's column of shared memory
 #pragma unroll
-          for (int rr = 0; rr < 4; ++rr)
+          for (int rr = 0; rr < kAR; ++rr)
             if (rr == r) {
 #pragma unroll
               for (int i = 0; i < (RB < 4 ? RB : 4); ++i) acct[rr][i] += acc[i * 3];
@@ -727,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   cp_async_wait_group<0>();
   if (NS == 2 && P.defer) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < kAR; ++r)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int sl = P.rslot[r][i];
@@ -750,27 +789,21 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     }
   }
   if (pre_b && P.pre_grad) {
-    // per thread u_p = sum over its elements of w * z_p; the element bits and
-    // thread-constant bits from the tile-invariant sums, n-1 (ring) from mL,
-    // tile-only bits from the lane accumulators
+    // per thread u_p = sum over its elements of w * z_p (see the sweep)
+    const FwdPhaseMeta* pm = reinterpret_cast<const FwdPhaseMeta*>(fph_bpre);
+    const R mW = macc[0], mF = macc[11 * kThreads];
     const double wsum = warp_sum((double)mW);
     if (lane == 0) smarg[warp * (n + 1)] = wsum;
     for (int p = 0; p < n; ++p) {
       R u;
-      const int zt = (zT >> p) & 1;
-      if (p < RB) {
-        R ap = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (j == p) ap = mA[j];  // compile-time index: mA stays in registers
-        u = zt ? mW - ap : ap;
-      } else if (ringz && p == n - 1) {
-        u = mL;
-      } else if ((fmask >> p) & 1) {
-        u = 0;
-      } else {
-        u = zt ? mW : (R)0;
-      }
+      int js = -1;
+      for (int j = 0; j < pm->nse; ++j)
+        if (pm->sepos[j] == p) js = j;
+      if (js >= 0) u = macc[(1 + js) * kThreads];
+      else if (p == flpos0) u = macc[9 * kThreads];
+      else if (p == flpos1) u = macc[10 * kThreads];
+      else if ((fmask >> p) & 1) u = 0;  // lane p's term below
+      else u = ((zT >> p) & 1) ? mW : (R)0;
       double v = warp_sum((double)u);
       v += (double)__shfl_sync(0xffffffffu, mF, p);
       if (lane == 0) smarg[warp * (n + 1) + 1 + p] = v;
