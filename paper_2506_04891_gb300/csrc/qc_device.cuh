@@ -11,8 +11,10 @@
 #include "qc_internal.h"
 
 // resident CTAs per SM the tile passes are compiled for: the complex64
-// forward pass of real single-qubit gates (RY) fits three (80 registers, no
-// spills), the others two (a three-CTA backward spills and measured slower)
+// forward passes of real single-qubit gates (RY; also the variant that
+// multiplies a following diagonal in its last round) fit three (80
+// registers, no spills), the others two (a three-CTA backward spills and
+// measured slower)
 #ifndef QC_BWD_MINB
 #define QC_BWD_MINB 2
 #endif

@@ -271,12 +271,14 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // zK touches a few "element" bits SE, so phase(z) = phase(z0 without SE) *
 // ratio[pattern of z on SE], ratio[] the products of the per-bit phase ratios
 // d_p[1] / d_p[0] (from the factored tables), set up once per CTA.
+// ebit0 / KB: the element index bits are ebit0 .. ebit0 + KB - 1 of the tile's
+// local index (the store loop: 8 .. t-1; a register round: lo .. lo + RB - 1).
 template <class R>
 __device__ void fph_setup(unsigned char* blk, const R* tabs, int tb, int zm, int n, int t, int c,
-                          int h0) {
+                          int h0, int ebit0 = 8, int KB = -1) {
   FwdPhaseMeta* M = reinterpret_cast<FwdPhaseMeta*>(blk);
   cx<R>* ratio = reinterpret_cast<cx<R>*>(blk + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
-  const int KB = t > 8 ? t - 8 : 0;
+  if (KB < 0) KB = t > 8 ? t - 8 : 0;
   if (threadIdx.x == 0) {
     const int cm = (1 << c) - 1;
     auto eoff = [&](int i) { return (i & cm) | ((i >> c) << h0); };
@@ -286,7 +288,7 @@ __device__ void fph_setup(unsigned char* blk, const R* tabs, int tb, int zm, int
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (j < KB) {
-          zk[j] = ztrans32(eoff(256 << j), n, zm);
+          zk[j] = ztrans32(eoff(1 << (ebit0 + j)), n, zm);
           se |= zk[j];
         }
       M->ok = __popc(se) <= kFphMaxSE;
@@ -343,7 +345,7 @@ __device__ __forceinline__ cx<R> fph_elem(const unsigned char* blk, cx<R> p0, in
 // PRE = 1 / 2: backward pass with a diagonal layer (identity / ring z map)
 // undone in round 0 (P.pre).
 constexpr int tile_minb(int rsize, int ns, int kind, int pre) {
-  return (rsize == 4 && kind == 1 && ns == 1 && pre == 0) ? QC_REAL_MINB
+  return (rsize == 4 && kind == 1 && ns == 1) ? QC_REAL_MINB
          : (ns == 2 && pre > 0) ? QC_PRE_MINB
          : (ns == 2 ? QC_BWD_MINB : QC_FWD_MINB);
 }
@@ -441,9 +443,15 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   const R* fpre_tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
   const R* fpost_tabs = coef + P.post_coef + (long long)b * P.post_bstride;
   if (NS == 1 && P.pre) fph_setup<R>(fph_pre, fpre_tabs, P.pre_tb, P.pre_zmode, n, t, c, h0);
-  if (NS == 1 && P.post) fph_setup<R>(fph_post, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0);
+  // the post phase is applied in the last round, on its RB register bits
+  const int rlast = P.nrounds - 1;
+  if (NS == 1 && P.post) {
+    if (PRE == 1) fph_setup<R>(fph_post, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0, P.rlo[rlast], RB);
+    else fph_setup<R>(fph_post, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0);
+  }
   const bool fpre_ok = NS == 1 && P.pre && reinterpret_cast<const FwdPhaseMeta*>(fph_pre)->ok;
-  const bool fpost_ok = NS == 1 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
+  // forward: the PRE = 1 variant multiplies the post phase in the last round
+  const bool fpost_ok = NS == 1 && PRE == 1 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
 
   // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
   // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
@@ -649,6 +657,18 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
         if (RB > 1) tile_bit<R, NS, RB, KIND, (RB > 1 ? 1 : 0)>(P, r, v0, v1, sco, acc);
         if (RB > 2) tile_bit<R, NS, RB, KIND, (RB > 2 ? 2 : 0)>(P, r, v0, v1, sco, acc);
         if (RB > 3) tile_bit<R, NS, RB, KIND, (RB > 3 ? 3 : 0)>(P, r, v0, v1, sco, acc);
+        if (NS == 1 && PRE == 1 && fpost_ok && r == rlast) {
+          // the layer's gates are all applied to these elements: multiply in
+          // the following diagonal layer's phase (element a = local index
+          // bits lo .. lo + RB - 1 of this group)
+          const int lidx = (g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB));
+          C p0;
+          int z0se;
+          fph_tile<R>(fph_post, fpost_tabs, P.post_tb,
+                      ztrans32(tile_base(f) | elem_off(lidx), n, P.post_zmode), p0, z0se);
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) v0[a] = cmul<R>(fph_elem<R>(fph_post, p0, z0se, a), v0[a]);
+        }
 #pragma unroll
         for (int a = 0; a < (1 << RB); ++a) {
           int ad = pb;
@@ -707,18 +727,21 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
 
     if (P.store) {
       const int base = tile_base(f);
-      if (P.post || P.scatter) {
+      if ((NS == 1 && P.post && !(PRE == 1 && fpost_ok)) || P.scatter) {
+        // forward post not applied in the round: the store-loop decomposition
+        const bool loop_ok = NS == 1 && P.post && PRE == 0 &&
+                             reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
         C p0 = mk<R>(1, 0);
         int z0se = 0;
-        if (fpost_ok && threadIdx.x < T)
+        if (loop_ok && threadIdx.x < T)
           fph_tile<R>(fph_post, fpost_tabs, P.post_tb, ztrans32(base | elem_off(threadIdx.x), n, P.post_zmode),
                       p0, z0se);
         for (int i = threadIdx.x, pi = sw_tid, k = 0; i < T; i += kThreads, pi += kThreads, ++k) {
           const int kl = base | elem_off(i);
           C e = S0[pi];
           if (NS == 1 && P.post)
-            e = cmul<R>(fpost_ok ? fph_elem<R>(fph_post, p0, z0se, k)
-                                 : diag_phase32<R>(fpost_tabs, P.post_tb, ztrans32(kl, n, P.post_zmode)),
+            e = cmul<R>(loop_ok ? fph_elem<R>(fph_post, p0, z0se, k)
+                                : diag_phase32<R>(fpost_tabs, P.post_tb, ztrans32(kl, n, P.post_zmode)),
                         e);
           const int gd = P.scatter ? ring_finv32(kl, n) : kl;
           if constexpr (IL) {
@@ -835,6 +858,14 @@ template <class R, int NS, int RB>
 static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const void* coef,
                                   const void* s0, void* d0, const void* s1, void* d1, double* part,
                                   cudaStream_t st) {
+  // forward: passes with a post phase and single-qubit gates at RB = 3 or 4
+  // run the variant that applies it in the last round
+  if constexpr (NS == 1 && (RB == 3 || RB == 4)) {
+    if (P.post && P.kind != 2) {
+      if (P.kind == 1) return launch_tile_k<R, NS, RB, 1, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+      return launch_tile_k<R, NS, RB, 0, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+    }
+  }
   // the pre-diagonal variant exists for backward single-qubit passes with
   // RB = 3 or 4 (the planner only fuses those)
   // (a forward pass's P.pre is the plain phase multiply inside PRE = 0)
