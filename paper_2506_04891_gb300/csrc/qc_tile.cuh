@@ -254,6 +254,11 @@ __device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Bulk prefetch of a global segment into L2 (address 16-byte aligned, size a
+// multiple of 16); no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* gmem, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
@@ -529,6 +534,19 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     if (nst == 3) cp_async_wait_group<2>();
     else if (nst == 2) cp_async_wait_group<1>();
     else cp_async_wait_group<0>();  // one buffer: the tile just issued
+    // one buffer: while this tile is processed, pull the next one into L2 so
+    // its copies do not wait on DRAM (one bulk prefetch per contiguous
+    // segment of 2^c amplitudes and state; not for gathered loads)
+    if (nst == 1 && !P.gather && f + cps < tps) {
+      const int nb = tile_base(f + cps);
+      const int nseg = 1 << m;                      // rows of the tile
+      const unsigned bytes = (unsigned)(sizeof(C) << c);
+      for (int j = threadIdx.x; j < nseg * NS; j += kThreads) {
+        const int row = j % nseg, st = j / nseg;
+        const int off = nb | (row << h0);
+        prefetch_l2((st ? s1b : s0b) + off, bytes);
+      }
+    }
     __syncthreads();
     C* S0 = buf + (long long)slot * NS * T;
     C* S1 = S0 + T;
