@@ -745,7 +745,24 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
 
     if (P.store) {
       const int base = tile_base(f);
-      if ((NS == 1 && P.post && !(PRE == 1 && fpost_ok)) || P.scatter) {
+      if (IL && P.scatter) {
+        // backward scatter through the CNOT ring's inverse map f^-1, in
+        // 16-byte pairs: f^-1(k ^ 1 ^ 2^(n-1)) = f^-1(k) ^ 1, and this top
+        // pass holds both index bit 0 (local 0) and bit n-1 (local t-1), so
+        // the thread takes local i < T/2 with its partner i ^ 1 ^ T/2
+        for (int i = threadIdx.x, si = sw_tid; i < (T >> 1); i += kThreads, si += kThreads) {
+          const int d = ring_finv32(base | elem_off(i), n);
+          const int sp = tswz<EB>(i ^ 1 ^ (T >> 1));
+          const float4 qa = *reinterpret_cast<const float4*>(&S0[2 * si]);
+          const float4 qb = *reinterpret_cast<const float4*>(&S0[2 * sp]);
+          const bool odd = d & 1;
+          const int dd = d & ~1;
+          *reinterpret_cast<float4*>(&d0b[dd]) =
+              odd ? make_float4(qb.x, qb.y, qa.x, qa.y) : make_float4(qa.x, qa.y, qb.x, qb.y);
+          *reinterpret_cast<float4*>(&d1b[dd]) =
+              odd ? make_float4(qb.z, qb.w, qa.z, qa.w) : make_float4(qa.z, qa.w, qb.z, qb.w);
+        }
+      } else if ((NS == 1 && P.post && !(PRE == 1 && fpost_ok)) || P.scatter) {
         // forward post not applied in the round: the store-loop decomposition
         const bool loop_ok = NS == 1 && P.post && PRE == 0 &&
                              reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
