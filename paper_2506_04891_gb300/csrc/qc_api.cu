@@ -1100,7 +1100,8 @@ qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int 
         break;
       }
       case ST_RING: {
-        ProfScope ps(s.ns == 2 ? PC_RING_B : PC_RING_F, passb, st);
+        // with lambda formed from psi in the same launch only psi is read
+        ProfScope ps(s.ns == 2 ? PC_RING_B : PC_RING_F, s.laminit ? 3 * S : passb, st);
         e = launch_ring<R>(s.rp, s.ns, batch, buf(s.s0), buf(s.d0), s.laminit ? nullptr : buf(s.s1),
                            buf(s.d1), s.laminit ? gez : nullptr, st);
         break;

@@ -150,6 +150,17 @@ __global__ void k_prodvec(ProdVecJob P, int n, int batch, int n_in, const double
   o[0] = (R)v0.x; o[1] = (R)v0.y; o[2] = (R)v1.x; o[3] = (R)v1.y;
 }
 
+// two adjacent amplitudes at an even index: one 16-byte store for complex64
+template <class R>
+__device__ __forceinline__ void store_pair(cx<R>* p, cx<R> a, cx<R> b) {
+  if constexpr (sizeof(R) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
+}
+
 // psi[b][k] = prod_p v[b][p][bit_p(k)], one contiguous chunk of 2^cb per CTA.
 // With post_tabs != NULL the product state is multiplied by the diagonal
 // phase of the following diagonal layer (tables as in k_diag).
@@ -166,7 +177,11 @@ __global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* _
   const int b = (int)(blk >> nch_bits);
   const long long chunk = blk & ((1LL << nch_bits) - 1);
   const long long base = chunk << cb;
-  const R* v = pv + (long long)b * n * 4;
+  // the sample's per-qubit vectors, staged once: the product chains below then
+  // wait on shared-memory latency instead of one global load per link
+  __shared__ __align__(16) R v[kMaxQubits * 4];
+  for (int i = threadIdx.x; i < n * 4; i += blockDim.x) v[i] = pv[(long long)b * n * 4 + i];
+  __syncthreads();
   const int la = cb < 6 ? cb : 6, lb = cb - la;
   // constant factor of the chunk's fixed high bits
   C H = mk<R>(1, 0);
@@ -190,12 +205,33 @@ __global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* _
   C* out = psi + ((long long)b << n) + base;
   const int CH = 1 << cb, ma = (1 << la) - 1;
   if (post_tabs) {
+    // the first phase table (low z bits, which differ across a warp) staged in
+    // shared memory; the other two are nearly uniform across a warp
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* t0 = reinterpret_cast<R*>(smraw);
     const R* tabs = post_tabs + (long long)b * post_bstride;
-    for (int i = threadIdx.x; i < CH; i += blockDim.x)
-      out[i] = cmul<R>(diag_phase<R>(tabs, post_tb, ztrans(base + i, n, post_zmode)),
-                       cmul<R>(Tb[i >> la], Ta[i & ma]));
+    const int TT = 1 << post_tb;
+    for (int i = threadIdx.x; i < 2 * TT; i += blockDim.x) t0[i] = tabs[i];
+    __syncthreads();
+    const long long mask = TT - 1;
+    for (int i = 2 * threadIdx.x; i < CH; i += 2 * blockDim.x) {
+      C e[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long z = ztrans(base + i + h, n, post_zmode);
+        const C ph = cmul<R>(cmul<R>(ldc<R>(t0 + 2 * (z & mask)),
+                                     ldc<R>(tabs + 2 * (TT + ((z >> post_tb) & mask)))),
+                             ldc<R>(tabs + 2 * (2 * TT + ((z >> (2 * post_tb)) & mask))));
+        e[h] = cmul<R>(ph, cmul<R>(Tb[(i + h) >> la], Ta[(i + h) & ma]));
+      }
+      store_pair<R>(out + i, e[0], e[1]);
+    }
   } else {
-    for (int i = threadIdx.x; i < CH; i += blockDim.x) out[i] = cmul<R>(Tb[i >> la], Ta[i & ma]);
+    // pairs (i, i + 1) share Tb (n >= 1, so la >= 1)
+    for (int i = 2 * threadIdx.x; i < CH; i += 2 * blockDim.x) {
+      const C tb = Tb[i >> la];
+      store_pair<R>(out + i, cmul<R>(tb, Ta[i & ma]), cmul<R>(tb, Ta[(i + 1) & ma]));
+    }
   }
 }
 
@@ -369,7 +405,6 @@ __global__ void __launch_bounds__(kThreads) k_expect(int n, int cb, const cx<R>*
                                                      double* __restrict__ part) {
   using C = cx<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* sred = reinterpret_cast<double*>(smraw);
   const int nchb = n - cb;
   const int b = (int)(blockIdx.x >> nchb);
   const long long base = ((long long)blockIdx.x & ((1LL << nchb) - 1)) << cb;
@@ -390,9 +425,27 @@ __global__ void __launch_bounds__(kThreads) k_expect(int n, int cb, const cx<R>*
         if (((j << 8) >> (7 + q)) & 1) acc[q] += w;
     }
   }
-  marg_write<JB + 2, R>(sred, n, active ? (base + tid) : 0, W, acc, 7, false);
+  // per-CTA sums in the state's precision (the FP64 rate is a small fraction of
+  // the FP32 rate); one conversion per CTA value, the sums over CTAs in FP64
+  R* sr = reinterpret_cast<R*>(smraw);
+  const long long zt = active ? (base + tid) : 0;
+  sr[tid] = W;
+  for (int p = 0; p < n; ++p) {
+    R a = 0;
+#pragma unroll
+    for (int q = 0; q < JB + 2; ++q)
+      if (q == p - 7) a = acc[q];
+    sr[(1 + p) * kThreads + tid] = ((zt >> p) & 1) ? (W - a) : a;
+  }
   __syncthreads();
-  marg_flush(sred, n + 1, part, gridDim.x, blockIdx.x);
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int v = warp; v < n + 1; v += kWarps) {
+    R t = 0;
+#pragma unroll
+    for (int e = 0; e < kThreads / 32; ++e) t += sr[v * kThreads + lane + 32 * e];
+    t = warp_sum_r<R>(t);
+    if (lane == 0) part[(long long)v * gridDim.x + blockIdx.x] = (double)t;
+  }
 }
 
 // lambda[b][k] = (sum_q g[b][q] (1 - 2 bit_{n-1-q}(k))) psi[b][k]
@@ -401,40 +454,45 @@ __global__ void __launch_bounds__(kThreads) k_laminit(int n, int cb, const doubl
                                                       const cx<R>* __restrict__ psi,
                                                       cx<R>* __restrict__ lam) {
   using C = cx<R>;
-  __shared__ double Sa[64], Sb[64], g[kMaxQubits];
+  __shared__ double g[kMaxQubits];
+  __shared__ R Ta[64], Tb[64];
   const int nchb = n - cb;
   const int b = (int)(blockIdx.x >> nchb);
   const long long base = ((long long)blockIdx.x & ((1LL << nchb) - 1)) << cb;
   for (int q = threadIdx.x; q < n; q += blockDim.x) g[q] = gez[(long long)b * n + q];
   __syncthreads();
   const int la = cb < 6 ? cb : 6, lb = cb - la;
-  double tot = 0, hi = 0;
-  for (int q = 0; q < n; ++q) {
-    tot += g[q];
-    const int p = n - 1 - q;
-    if (p >= cb && ((base >> p) & 1)) hi += g[q];
-  }
+  // o(i) = Tb[i >> la] + Ta[i & (2^la - 1)]: Tb holds the total, the chunk's
+  // fixed bits and the upper in-chunk bits, Ta the low bits, both in the
+  // state's precision
   for (int e = threadIdx.x; e < 128; e += blockDim.x) {
-    double s = 0;
+    double acc = 0;
     if (e < 64) {
       for (int i = 0; i < la; ++i)
-        if ((e >> i) & 1) s += g[n - 1 - i];
-      Sa[e] = s;
+        if ((e >> i) & 1) acc += g[n - 1 - i];
+      Ta[e] = (R)(-2.0 * acc);
     } else {
       const int f = e - 64;
+      double tot = 0;
+      for (int q = 0; q < n; ++q) {
+        tot += g[q];
+        const int p = n - 1 - q;
+        if (p >= cb && ((base >> p) & 1)) acc += g[q];
+      }
       for (int i = 0; i < lb; ++i)
-        if ((f >> i) & 1) s += g[n - 1 - (la + i)];
-      Sb[f] = s + hi;
+        if ((f >> i) & 1) acc += g[n - 1 - (la + i)];
+      Tb[f] = (R)(tot - 2.0 * acc);
     }
   }
   __syncthreads();
   const long long off = ((long long)b << n) + base;
   const int CH = 1 << cb, ma = (1 << la) - 1;
-#pragma unroll 16
-  for (int i = threadIdx.x; i < CH; i += blockDim.x) {
-    const R o = (R)(tot - 2.0 * (Sa[i & ma] + Sb[i >> la]));
-    const C x = psi[off + i];
-    lam[off + i] = mk<R>(o * x.x, o * x.y);
+  // pairs (i, i + 1) share Tb (n >= 1, so la >= 1)
+  for (int i = 2 * threadIdx.x; i < CH; i += 2 * blockDim.x) {
+    const R tb = Tb[i >> la];
+    const R o0 = tb + Ta[i & ma], o1 = tb + Ta[(i + 1) & ma];
+    const C x0 = psi[off + i], x1 = psi[off + i + 1];
+    store_pair<R>(lam + off + i, mk<R>(o0 * x0.x, o0 * x0.y), mk<R>(o1 * x1.x, o1 * x1.y));
   }
 }
 
@@ -454,8 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
   C* S = reinterpret_cast<C*>(smraw);
   const int n = P.n;
   if (NS == 2 && gez) {
-    __shared__ double Sg[kMaxQubits], Sa[64], Sb[64];
-    __shared__ double tot_hi[2];
+    __shared__ double Sg[kMaxQubits];
     const int b = P.whole ? (int)blockIdx.x : (int)(blockIdx.x >> (n - P.t));
     const long long sb = (long long)b << n;
     for (int q = threadIdx.x; q < n; q += kThreads) Sg[q] = gez[(long long)b * n + q];
@@ -482,37 +539,42 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
     const long long Bk = A ^ (3LL << (n - 2));
     const int il = (int)(ib & (H - 1));
     const long long topbit = 1LL << (n - 1);
-    // o(k) = sum_q g_q - 2 sum_{bits p of k} g_{n-1-p}, split into the low 6 bits, the
-    // next bits of the half tile, the tile's fixed bits and the top bit
+    // o(k) = sum_q g_q - 2 sum_{bits p of k} g_{n-1-p}, split into the low 6 bits
+    // and the next 6 bits of the half-tile index (tables in the state's
+    // precision) and c0[top]: the total, the tile's fixed bits and the top bit
+    __shared__ R Ta[64], Tb[64], c0[2];
     for (int e = threadIdx.x; e < 128; e += kThreads) {
-      double acc = 0;
+      R acc = 0;
       const int lo = e < 64 ? 0 : 6, v = e & 63;
       for (int i = 0; i < 6; ++i)
-        if (((v >> i) & 1) && lo + i < t - 1) acc += Sg[n - 1 - (lo + i)];
-      if (e < 64) Sa[v] = acc; else Sb[v] = acc;
+        if (((v >> i) & 1) && lo + i < t - 1) acc += (R)Sg[n - 1 - (lo + i)];
+      if (e < 64) Ta[v] = -2 * acc; else Tb[v] = -2 * acc;
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 128) {
       double tot = 0, hi = 0;
       for (int q = 0; q < n; ++q) tot += Sg[q];
       for (int p = t - 1; p < n - 1; ++p)
         if ((tb >> p) & 1) hi += Sg[n - 1 - p];
-      tot_hi[0] = tot;
-      tot_hi[1] = hi;
+      c0[0] = (R)(tot - 2.0 * hi);
+      c0[1] = (R)(tot - 2.0 * (hi + Sg[0]));
     }
     for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
       const int top = e >> (t - 1), jl = e & (H - 1);
       S[e] = src0[sb + tb + jl + (top ? topbit : 0)];
     }
     __syncthreads();
-    const double tot = tot_hi[0], hi = tot_hi[1], g0 = Sg[0];
-    for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
+    // element pairs (yl, yl ^ 1): gray_inv(x ^ 1) = gray_inv(x) ^ 1, so the pair
+    // reads (top, jl) and (top ^ 1, jl ^ 1) and writes 16 (c64) bytes per state
+    for (int e = 2 * threadIdx.x; e < 2 * H; e += 2 * kThreads) {
       const int u = e >> (t - 1), yl = e & (H - 1);
       const int jl = gray_inv(yl ^ il);
       const int top = u ^ (jl & 1);
-      const C x = S[top * H + jl];
-      const double o = tot - 2.0 * (Sa[jl & 63] + Sb[(jl >> 6) & 63] + hi + (top ? g0 : 0.0));
-      dst0[sb + (u ? Bk : A) + yl] = x;
-      dst1[sb + (u ? Bk : A) + yl] = mk<R>((R)o * x.x, (R)o * x.y);
+      const C x0 = S[top * H + jl], x1 = S[(top ^ 1) * H + (jl ^ 1)];
+      const R o0 = c0[top] + Ta[jl & 63] + Tb[(jl >> 6) & 63];
+      const R o1 = c0[top ^ 1] + Ta[(jl ^ 1) & 63] + Tb[(jl >> 6) & 63];
+      const long long d = sb + (u ? Bk : A) + yl;
+      store_pair<R>(dst0 + d, x0, x1);
+      store_pair<R>(dst1 + d, mk<R>(o0 * x0.x, o0 * x0.y), mk<R>(o1 * x1.x, o1 * x1.y));
     }
     return;
   }
@@ -564,11 +626,11 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
         S[e] = src[sb + tb + jl + (top ? topbit : 0)];
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < 2 * H; e += kThreads) {
+      for (int e = 2 * threadIdx.x; e < 2 * H; e += 2 * kThreads) {
         const int u = e >> (t - 1), yl = e & (H - 1);
         const int jl = gray_inv(yl ^ il);
         const int top = u ^ (jl & 1);
-        dst[sb + (u ? Bk : A) + yl] = S[top * H + jl];
+        store_pair<R>(dst + sb + (u ? Bk : A) + yl, S[top * H + jl], S[(top ^ 1) * H + (jl ^ 1)]);
       }
     }
     __syncthreads();
@@ -1002,7 +1064,13 @@ cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi,
                            const void* post_tabs, long long post_bstride, int post_tb,
                            int post_zmode, cudaStream_t st) {
   long long grid = (long long)batch << (n - cb);
-  k_prodinit<R><<<(unsigned)grid, kThreads, 0, st>>>(n, cb, (const R*)pv, (cx<R>*)psi,
+  const size_t smem = post_tabs ? ((size_t)2 * sizeof(R)) << post_tb : 0;
+  if (smem > 40 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_prodinit<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_prodinit<R><<<(unsigned)grid, kThreads, smem, st>>>(n, cb, (const R*)pv, (cx<R>*)psi,
                                                      (const R*)post_tabs, post_bstride, post_tb,
                                                      post_zmode);
   return cudaGetLastError();
