@@ -227,13 +227,22 @@ int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 // Register bits per round: 4, except the complex128 backward (two states of
 // 16-byte amplitudes) takes 3.  With 2^12-amplitude tiles every thread of a
 // 256-thread CTA has work at 4 bits.
-int reg_bits(const qc_circuit* c, int ns) {
+// Default register bits: 4, and 3 for the backward passes whose gate math
+// needs the most registers per amplitude: every complex128 one, and complex64
+// complex-matrix single-qubit layers and parametrised brick layers (measured
+// faster with 3 on the IBM and IonQ native-gate circuits; real RY and fixed
+// brick layers with 4).
+int reg_bits(const qc_circuit* c, int ns, const LayerInfo* L = nullptr) {
   if (ns == 1 && c->opt.reg_bits_fwd > 0) return c->opt.reg_bits_fwd;
   if (ns == 2 && c->opt.reg_bits_bwd > 0) return c->opt.reg_bits_bwd;
   static const int kf = env_knob("QC_RB_FWD"), kb = env_knob("QC_RB_BWD");
   if (ns == 1 && kf > 0) return kf;
   if (ns == 2 && kb > 0) return kb;
-  return (ns == 2 && c->dtype == QC_C128) ? 3 : 4;
+  if (ns != 2) return 4;
+  if (c->dtype == QC_C128) return 3;
+  if (L && L->cls == LC_ROT1 && !L->real) return 3;
+  if (L && L->cls == LC_DENSE2 && L->diff && L->nparams > 0) return 3;
+  return 4;
 }
 
 // Shared-memory tile buffers of a pass.  Forward: two (one tile in flight
@@ -262,7 +271,7 @@ thread_local bool g_plan_unplaced = false;
 // of its bits in the same round, so brick layers take at least two, and a pass
 // has at most kMaxRounds rounds.
 int pass_rb(const qc_circuit* c, const LayerInfo& L, int ns, int t) {
-  int rb = std::max(reg_bits(c, ns), L.cls == LC_DENSE2 ? 2 : 1);
+  int rb = std::max(reg_bits(c, ns, &L), L.cls == LC_DENSE2 ? 2 : 1);
   rb = std::max(rb, (t + kMaxRounds - 1) / kMaxRounds);
   return std::min(rb, t);
 }
