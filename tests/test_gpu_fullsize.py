@@ -5,7 +5,8 @@ samples come from tests/golden/<workload>.npz (written by
 tests/golden/make_goldens.py, which calls only the oracle).  Per-sample
 d theta is checked by masking the upstream gradient to one sample while the
 launch keeps the full batch.  zz26 is also checked against a closed form that
-holds at any n (one block: RX, RY, IsingZZ ring, CNOT ring).
+holds at any n (one block: RX, RY, IsingZZ ring, CNOT ring), and so is the
+largest register, n = 30.
 """
 import os
 
@@ -85,16 +86,11 @@ def _closed_form(x, th):
     return out
 
 
-def test_zz26_one_block_closed_form_full_size():
-    """RX(x), RY(th), IsingZZ ring, CNOT ring at n = 26, B = 8: <Z_q> is a
-    product of cos x_j cos th_j (the ring maps bits to prefix parities), and
-    so are its derivatives; the ZZ angles do not enter."""
-    n, B = 26, 8
-    layers = W.zz_circuit(n, 1)
-    x, theta, _ = W.draw_inputs(n, layers, B, seed=0)
-    g = W.draw_upstream(B, n, seed=3)
-    got = run_gpu(n, layers, x, theta, g, psi=False)
-    dth_ref = np.zeros(2 * n)
+def _check_closed_form(got, x, theta, g, n_theta):
+    """<Z>, dx and d theta of a circuit whose <Z_q> is the prefix-parity
+    product of c_j = cos x_j cos th_j (th = the first n entries of theta)."""
+    B, n = g.shape
+    dth_ref = np.zeros(n_theta)
     for b in range(B):
         c = np.cos(x[b]) * np.cos(theta[:n])
         ez = _closed_form(x[b], theta[:n])
@@ -108,6 +104,40 @@ def test_zz26_one_block_closed_form_full_size():
         assert np.max(np.abs(got["dx"][b] - dx)) < ABS_C64
         dth_ref[:n] += dL_dc * (-np.cos(x[b]) * np.sin(theta[:n]))
     assert np.max(np.abs(got["dth"] - dth_ref)) < ABS_C64 * B
+
+
+def test_zz26_one_block_closed_form_full_size():
+    """RX(x), RY(th), IsingZZ ring, CNOT ring at n = 26, B = 8: <Z_q> is a
+    product of cos x_j cos th_j (the ring maps bits to prefix parities), and
+    so are its derivatives; the ZZ angles do not enter."""
+    n, B = 26, 8
+    layers = W.zz_circuit(n, 1)
+    x, theta, _ = W.draw_inputs(n, layers, B, seed=0)
+    g = W.draw_upstream(B, n, seed=3)
+    got = run_gpu(n, layers, x, theta, g, psi=False)
+    _check_closed_form(got, x, theta, g, 2 * n)
+
+
+def test_max_qubits_closed_form():
+    """n = 30, the largest register the library accepts (2^30 amplitudes, 8 GiB
+    per sample in complex64): [CNOT ring, RX(x), RY(th), CNOT ring] on |0..0>.
+    The first ring leaves |0..0> as it is, so <Z> has the same closed form as
+    one zz block; with no leading single-qubit layer every layer runs as its own
+    pass (forward tile passes with the ring gathered into the first, the ring
+    kernel, the backward ring with lambda formed in it, backward tile passes with
+    the RX gradients folded into RY's).  Small angles keep the 30-factor products
+    of order one."""
+    n, B = 30, 1
+    layers = [("CNOT_RING", "none", 0, 0), ("RX", "input", 0, 0), ("RY", "theta", 0, 0),
+              ("CNOT_RING", "none", 0, 0)]
+    rng = np.random.default_rng(30)
+    x = rng.uniform(0.0, 0.4, size=(B, n))
+    theta = rng.uniform(-0.4, 0.4, size=n)
+    g = W.draw_upstream(B, n, seed=30)
+    got = run_gpu(n, layers, x, theta, g, psi=False)
+    assert np.allclose(got["norms"], 1.0, atol=1e-4)
+    assert np.min(np.abs(got["ez"])) > 0.05
+    _check_closed_form(got, x, theta, g, n)
 
 
 def test_zz26_full_circuit_properties():
