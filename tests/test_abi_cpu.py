@@ -91,6 +91,35 @@ def test_create_rejects_invalid(q, bad, err):
     assert q.qc_last_error()
 
 
+def test_calls_refuse_empty_or_negative_batch_and_null_buffers_on_the_host(q):
+    """Argument checks run before any CUDA call, so they are exercised here
+    without a GPU: a batch of 0 or below, or a NULL state or workspace, is
+    QC_ERR_INVALID with a message."""
+    h = q.qc_create(4, "c64", [("RX", "input", 0, 0), ("RY", "theta", 0, 0)])
+    try:
+        for batch in (0, -3):
+            with pytest.raises(q.QCError) as e:
+                q.qc_workspace_bytes(h, batch)
+            assert e.value.status == 1
+            with pytest.raises(q.QCError) as e:
+                q.qc_forward(h, batch, None, None, None, None, None, 0, None)
+            assert e.value.status == 1 and "batch" in q.qc_last_error()
+            with pytest.raises(q.QCError) as e:
+                q.qc_backward(h, batch, None, None, None, None, None, None, None, 0, None)
+            assert e.value.status == 1
+            with pytest.raises(q.QCError) as e:
+                q.qc_expect_z(h, batch, None, None, None)
+            assert e.value.status == 1
+        with pytest.raises(q.QCError) as e:
+            q.qc_forward(h, 2, None, None, None, None, None, 0, None)
+        assert e.value.status == 1 and "psi_out" in q.qc_last_error()
+        with pytest.raises(q.QCError) as e:
+            q.qc_backward(h, 2, None, None, None, None, None, None, None, 0, None)
+        assert e.value.status == 1
+    finally:
+        q.qc_destroy(h)
+
+
 def test_rot_counts_three_parameters_per_qubit_and_constants_take_no_source(q):
     n = 6
     h = q.qc_create(n, "c64", [("ROT", "theta", 4, 0), ("H", "none", 0, 0), ("ROT", "input", 1, 0)])
