@@ -133,7 +133,10 @@ typedef struct {
    * where two CTAs per SM still fit; with 1 the CTAs of an SM overlap each
    * other's copies instead of their own).  A tuner may try
    * several (paper_2506_04891_gb300.tune); results never depend on them
-   * beyond rounding. */
+   * beyond rounding.  A field left at 0 takes, at qc_create, the process
+   * environment variable QC_TMAX_FWD, QC_TMAX_BWD, QC_RB_FWD, QC_RB_BWD or
+   * QC_TILE_STAGES (both sweeps) when set; out-of-range values, from either
+   * source, make qc_create return QC_ERR_INVALID. */
   int32_t tile_bits_fwd;
   int32_t tile_bits_bwd;
   int32_t reg_bits_fwd;

@@ -183,9 +183,6 @@ int env_knob(const char* name) {
 int tile_tmax(const qc_circuit* c, int ns) {
   if (ns == 1 && c->opt.tile_bits_fwd > 0) return c->opt.tile_bits_fwd;
   if (ns == 2 && c->opt.tile_bits_bwd > 0) return c->opt.tile_bits_bwd;
-  static const int kf = env_knob("QC_TMAX_FWD"), kb = env_knob("QC_TMAX_BWD");
-  if (ns == 1 && kf > 0) return kf;
-  if (ns == 2 && kb > 0) return kb;
   // complex64 backward: 2^12 amplitudes of psi and lambda in one buffer (64 KB),
   // two CTAs per SM overlapping each other's copies (see tile_stages)
   if (c->dtype == QC_C64) return 12;
@@ -235,9 +232,6 @@ int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 int reg_bits(const qc_circuit* c, int ns, const LayerInfo* L = nullptr) {
   if (ns == 1 && c->opt.reg_bits_fwd > 0) return c->opt.reg_bits_fwd;
   if (ns == 2 && c->opt.reg_bits_bwd > 0) return c->opt.reg_bits_bwd;
-  static const int kf = env_knob("QC_RB_FWD"), kb = env_knob("QC_RB_BWD");
-  if (ns == 1 && kf > 0) return kf;
-  if (ns == 2 && kb > 0) return kb;
   if (ns != 2) return 4;
   if (c->dtype == QC_C128) return 3;
   if (L && L->cls == LC_ROT1 && !L->real) return 3;
@@ -253,9 +247,7 @@ int reg_bits(const qc_circuit* c, int ns, const LayerInfo* L = nullptr) {
 // shared-memory rounds per 26-qubit layer (measured 6% faster on zz26 than
 // 2^11 tiles with two buffers).  Three buffers only where two CTAs still fit.
 int tile_stages(const qc_circuit* c, TilePass& P, int ns, int rsize) {
-  static const int ke = env_knob("QC_TILE_STAGES");
-  const int ko = ns == 1 ? c->opt.stages_fwd : c->opt.stages_bwd;
-  int k = ko > 0 ? ko : ke;
+  int k = ns == 1 ? c->opt.stages_fwd : c->opt.stages_bwd;
   if (k == 0 && ns == 2 && c->dtype == QC_C64) k = 1;
   if (k == 1) return 1;
   if (k != 3) return 2;
@@ -1274,18 +1266,29 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
   qc_options o;
   qc_default_options(&o);
   if (opt) o = *opt;
+  // geometry left at 0 takes the process environment (QC_TMAX_FWD / _BWD,
+  // QC_RB_FWD / _BWD, QC_TILE_STAGES), then the same range checks
+  auto from_env = [](int32_t& f, const char* name) {
+    if (f == 0) f = env_knob(name);
+  };
+  from_env(o.tile_bits_fwd, "QC_TMAX_FWD");
+  from_env(o.tile_bits_bwd, "QC_TMAX_BWD");
+  from_env(o.reg_bits_fwd, "QC_RB_FWD");
+  from_env(o.reg_bits_bwd, "QC_RB_BWD");
+  from_env(o.stages_fwd, "QC_TILE_STAGES");
+  from_env(o.stages_bwd, "QC_TILE_STAGES");
   if (o.path < 0 || o.path > 2) return fail(QC_ERR_INVALID, "options.path must be 0, 1 or 2");
   if (o.ckpt_every < -1) return fail(QC_ERR_INVALID, "options.ckpt_every must be >= -1");
   {
     const int fmax = dtype == QC_C64 ? 13 : 12, bmax = dtype == QC_C64 ? 12 : 11;
     if (o.tile_bits_fwd != 0 && (o.tile_bits_fwd < 6 || o.tile_bits_fwd > fmax))
-      return fail(QC_ERR_INVALID, "options.tile_bits_fwd out of range");
+      return fail(QC_ERR_INVALID, "options.tile_bits_fwd (or QC_TMAX_FWD) out of range");
     if (o.tile_bits_bwd != 0 && (o.tile_bits_bwd < 6 || o.tile_bits_bwd > bmax))
-      return fail(QC_ERR_INVALID, "options.tile_bits_bwd out of range");
+      return fail(QC_ERR_INVALID, "options.tile_bits_bwd (or QC_TMAX_BWD) out of range");
     if (o.reg_bits_fwd < 0 || o.reg_bits_fwd > 4 || o.reg_bits_bwd < 0 || o.reg_bits_bwd > 4)
-      return fail(QC_ERR_INVALID, "options.reg_bits_* must be in 0 .. 4");
+      return fail(QC_ERR_INVALID, "options.reg_bits_* (or QC_RB_*) must be in 0 .. 4");
     if (o.stages_fwd < 0 || o.stages_fwd > 3 || o.stages_bwd < 0 || o.stages_bwd > 3)
-      return fail(QC_ERR_INVALID, "options.stages_* must be in 0 .. 3");
+      return fail(QC_ERR_INVALID, "options.stages_* (or QC_TILE_STAGES) must be in 0 .. 3");
   }
   auto c = std::make_unique<qc_circuit>();
   c->n = n;

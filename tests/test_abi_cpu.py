@@ -156,6 +156,28 @@ def test_tuning_options_shape_the_plan_and_are_validated(q):
         q.Circuit(16, layers, tuning=dict(tiles=3))
 
 
+def test_geometry_environment_fills_unset_options_and_is_validated(q, monkeypatch):
+    layers = W.zz_circuit(16, 2)
+
+    def geo(desc, tag):
+        return {(int(d["t"]), int(d["rb"])) for d in
+                (dict(re.findall(r"(\w+)=(-?\d+)", l.split("[")[0])) for l in desc.splitlines()
+                 if l.startswith(tag) and " TILE " in l)}
+    monkeypatch.setenv("QC_TMAX_BWD", "10")
+    monkeypatch.setenv("QC_RB_FWD", "3")
+    env = q.Circuit(16, layers, path=2).describe(2)
+    assert geo(env, "F ") == {(12, 3)} and geo(env, "B ") == {(10, 4)}
+    # an explicit option wins over the environment
+    opt = q.Circuit(16, layers, path=2, tuning=dict(tile_bits_bwd=11)).describe(2)
+    assert geo(opt, "B ") == {(11, 4)}
+    for name, bad in (("QC_RB_BWD", "9"), ("QC_TMAX_FWD", "20"), ("QC_TILE_STAGES", "5")):
+        monkeypatch.setenv(name, bad)
+        with pytest.raises(q.QCError) as e:
+            q.Circuit(16, layers)
+        assert e.value.status == 1 and name.split("_")[1] in q.qc_last_error()
+        monkeypatch.delenv(name)
+
+
 def test_tuner_candidates_stay_in_range():
     from paper_2506_04891_gb300 import tune
     for dtype in ("c64", "c128"):
