@@ -492,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     if constexpr (IL) {
       if (ds_half >= 0) {
         int gi = base | elem_off(il_i);
+#pragma unroll 4
         for (int i = il_i, si = il_si; i < T; i += kThreads / 2, si += kThreads, gi += ds_half)
           cp_async_elem<sizeof(C)>(&d0[si], &il_src[P.gather ? ring_finv32(gi, n) : gi]);
       } else {
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
       const int nseg = 1 << m;                      // rows of the tile
       const unsigned bytes = (unsigned)(sizeof(C) << c);
       for (int j = threadIdx.x; j < nseg * NS; j += kThreads) {
-        const int row = j % nseg, st = j / nseg;
+        const int row = j & (nseg - 1), st = j >> m;
         const int off = nb | (row << h0);
         prefetch_l2((st ? s1b : s0b) + off, bytes);
       }
@@ -791,6 +792,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
         // paired 16-byte stores: i = 2 tid + k * 2 kThreads (c >= 1 here, so the
         // pair never straddles the contiguous segment)
         int gi_step = base | elem_off(2 * threadIdx.x);
+#pragma unroll 2
         for (int i = 2 * threadIdx.x, pi = sw_tid2; i < T;
              i += 2 * kThreads, pi += 2 * kThreads, gi_step += (ds_pair >= 0 ? ds_pair : 0)) {
           const int gi = ds_pair >= 0 ? gi_step : (base | elem_off(i));
