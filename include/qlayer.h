@@ -124,9 +124,10 @@ typedef struct {
    * amplitudes per shared-memory tile (forward default 12 for QC_C64, 11 for
    * QC_C128; backward 12 / 10; allowed 6 .. 13 / 12 forward, 6 .. 12 / 11
    * backward).  reg_bits_*: index bits held in registers per round (1 .. 4;
-   * defaults 4, except 3 for the QC_C128 backward and, for QC_C64, the backward
-   * passes of complex single-qubit layers and of parametrised brick layers;
-   * the planner raises it where a pass needs
+   * defaults 4, except in the backward: 3 for QC_C128, and one less again
+   * for the passes of complex single-qubit layers and of parametrised brick
+   * layers (3 for QC_C64, 2 for QC_C128; in QC_C128 every brick layer takes
+   * 2); the planner raises it where a pass needs
    * more: two for brick layers, and at most eight rounds per pass).
    * stages_*: shared-memory tile buffers per CTA (1, 2 or 3; default 2, 1 for
    * the QC_C64 backward; 3 only

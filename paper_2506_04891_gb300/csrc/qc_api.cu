@@ -224,19 +224,20 @@ int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 // Register bits per round: 4, except the complex128 backward (two states of
 // 16-byte amplitudes) takes 3.  With 2^12-amplitude tiles every thread of a
 // 256-thread CTA has work at 4 bits.
-// Default register bits: 4, and 3 for the backward passes whose gate math
-// needs the most registers per amplitude: every complex128 one, and complex64
-// complex-matrix single-qubit layers and parametrised brick layers (measured
-// faster with 3 on the IBM and IonQ native-gate circuits; real RY and fixed
-// brick layers with 4).
+// Default register bits: 4 forward.  Backward: 4 (complex64) or 3
+// (complex128), one less for the passes whose gate math needs the most
+// registers per amplitude: complex-matrix single-qubit layers, parametrised
+// brick layers and, in complex128, every brick layer (measured faster on the
+// IBM and IonQ native-gate circuits; real RY layers, and fixed brick layers
+// in complex64, keep the larger count).
 int reg_bits(const qc_circuit* c, int ns, const LayerInfo* L = nullptr) {
   if (ns == 1 && c->opt.reg_bits_fwd > 0) return c->opt.reg_bits_fwd;
   if (ns == 2 && c->opt.reg_bits_bwd > 0) return c->opt.reg_bits_bwd;
   if (ns != 2) return 4;
-  if (c->dtype == QC_C128) return 3;
-  if (L && L->cls == LC_ROT1 && !L->real) return 3;
-  if (L && L->cls == LC_DENSE2 && L->diff && L->nparams > 0) return 3;
-  return 4;
+  const int base = c->dtype == QC_C128 ? 3 : 4;
+  if (L && L->cls == LC_ROT1 && !L->real) return base - 1;
+  if (L && L->cls == LC_DENSE2 && (c->dtype == QC_C128 || (L->diff && L->nparams > 0))) return base - 1;
+  return base;
 }
 
 // Shared-memory tile buffers of a pass.  Forward: two (one tile in flight
@@ -775,6 +776,21 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
           if (pend_ring >= 0) {  // top pass first: it gathers through the ring
             std::rotate(h.steps.begin(), h.steps.end() - 1, h.steps.end());
             h.steps.front().tp.gather = 1;
+          }
+          if (fuse && is_phase(i + 1) && c->dtype == QC_C64 && Li.cls == LC_ROT1) {
+            // a following diagonal rides in the last round of the contiguous
+            // pass when that pass takes the compile-time element patterns: run
+            // it last (the layer's gates commute; a gathering pass stays first)
+            for (size_t k = pend_ring >= 0 ? 1 : 0; k + 1 < h.steps.size(); ++k) {
+              TilePass probe = h.steps[k].tp;
+              probe.post_zmode = LI[i + 1].zmode;
+              if (h.steps[k].rb == 4 && fwd_post_contig(probe)) {
+                const Step mv = h.steps[k];
+                h.steps.erase(h.steps.begin() + (long)k);
+                h.steps.push_back(mv);
+                break;
+              }
+            }
           }
           if (pend_pre >= 0) {
             const LayerInfo& D = LI[pend_pre];
@@ -1582,9 +1598,13 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
   auto dump = [&](const char* tag, const std::vector<Step>& v) {
     for (auto& st : v) {
       if (st.type == ST_TILE) {
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d src=%d dst=%d",
+        // post: 0 none, 1 a following diagonal's phase, 2 the same with the
+        // contiguous pass's compile-time element patterns
+        const int post = !st.tp.post ? 0
+                         : (st.ns == 1 && st.rb == 4 && c->dtype == QC_C64 && fwd_post_contig(st.tp)) ? 2 : 1;
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d post=%d src=%d dst=%d",
                  tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nstage, st.tp.nrounds, st.tp.nops, st.tp.nslots,
-                 st.tp.store, st.tp.pre, st.s0, st.d0);
+                 st.tp.store, st.tp.pre, post, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {
           snprintf(line, sizeof line, " [l=%d%s np=%d%s]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "",

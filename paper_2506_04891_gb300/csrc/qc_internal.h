@@ -112,6 +112,15 @@ struct TilePass {
   TileOp ops[kMaxTileOps];
 };
 
+// Forward pass whose post phase (a following diagonal layer) takes the
+// compile-time element patterns: a contiguous 2^12 tile (c = t) whose last
+// register round holds index bits 8 .. 11 (4 register bits), ring or
+// identity z map.
+__host__ __device__ inline bool fwd_post_contig(const TilePass& P) {
+  return P.t == 12 && P.c == 12 && P.nrounds >= 1 && P.nrounds <= kMaxRounds &&
+         P.rlo[P.nrounds - 1] == 8 && (P.post_zmode == Z_IDENT || P.post_zmode == Z_RINGXOR);
+}
+
 // Resident CTAs per SM a tile pass is compiled for (see the launch bounds of
 // the tile kernel): the complex64 real-gate forward pass 3, others 2 (a
 // fused-diagonal backward pass at one CTA per SM without spills measured

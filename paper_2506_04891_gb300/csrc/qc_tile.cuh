@@ -451,12 +451,14 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   // the post phase is applied in the last round, on its RB register bits
   const int rlast = P.nrounds - 1;
   if (NS == 1 && P.post) {
-    if (PRE == 1) fph_setup<R>(fph_post, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0, P.rlo[rlast], RB);
+    if (PRE >= 1) fph_setup<R>(fph_post, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0, P.rlo[rlast], RB);
     else fph_setup<R>(fph_post, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0);
   }
   const bool fpre_ok = NS == 1 && P.pre && reinterpret_cast<const FwdPhaseMeta*>(fph_pre)->ok;
-  // forward: the PRE = 1 variant multiplies the post phase in the last round
-  const bool fpost_ok = NS == 1 && PRE == 1 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
+  // forward: the PRE >= 1 variants multiply the post phase in the last round
+  // (PRE = 2 / 3: ring / identity z map on a contiguous 2^12 pass whose last
+  // round holds bits 8 .. 11, with compile-time element patterns)
+  const bool fpost_ok = NS == 1 && PRE >= 1 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
 
   // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
   // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
@@ -687,6 +689,22 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
                       ztrans32(tile_base(f) | elem_off(lidx), n, P.post_zmode), p0, z0se);
 #pragma unroll
           for (int a = 0; a < (1 << RB); ++a) v0[a] = cmul<R>(fph_elem<R>(fph_post, p0, z0se, a), v0[a]);
+        } else if (NS == 1 && PRE >= 2 && fpost_ok && r == rlast) {
+          // group g = tid holds local indices g | a << 8 (c = t = 12, lo = 8):
+          // z = z0 ^ z(a << 8), and z(a << 8) covers z bits zlo .. 11 with the
+          // compile-time pattern a ^ (a << 1) (ring) or a (identity); the
+          // per-CTA ratio table is indexed in that bit order
+          constexpr int zlo = PRE == 2 ? 7 : 8, nse = 12 - zlo;
+          constexpr int semask = ((1 << nse) - 1) << zlo;
+          const int z0 = ztrans32(tile_base(f) | g, n, PRE == 2 ? Z_RINGXOR : Z_IDENT);
+          const int z0se = (z0 >> zlo) & ((1 << nse) - 1);
+          const C p0 = diag_phase32<R>(fpost_tabs, P.post_tb, z0 & ~semask);
+          const C* ratio = reinterpret_cast<const C*>(fph_post + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) {
+            const int pat = PRE == 2 ? (a ^ (a << 1)) : a;
+            v0[a] = cmul<R>(cmul<R>(p0, ratio[z0se ^ pat]), v0[a]);
+          }
         }
 #pragma unroll
         for (int a = 0; a < (1 << RB); ++a) {
@@ -763,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           *reinterpret_cast<float4*>(&d1b[dd]) =
               odd ? make_float4(qb.z, qb.w, qa.z, qa.w) : make_float4(qa.z, qa.w, qb.z, qb.w);
         }
-      } else if ((NS == 1 && P.post && !(PRE == 1 && fpost_ok)) || P.scatter) {
+      } else if ((NS == 1 && P.post && !(PRE >= 1 && fpost_ok)) || P.scatter) {
         // forward post not applied in the round: the store-loop decomposition
         const bool loop_ok = NS == 1 && P.post && PRE == 0 &&
                              reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
@@ -899,6 +917,17 @@ static cudaError_t launch_tile_rb(const TilePass& P, int batch, int cps, const v
   // run the variant that applies it in the last round
   if constexpr (NS == 1 && (RB == 3 || RB == 4)) {
     if (P.post && P.kind != 2) {
+      if constexpr (RB == 4 && sizeof(R) == 4) {
+        // contiguous 2^12 pass whose last round holds bits 8 .. 11
+        if (fwd_post_contig(P)) {
+          const bool ring = P.post_zmode == Z_RINGXOR;
+          if (P.kind == 1)
+            return ring ? launch_tile_k<R, NS, RB, 1, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st)
+                        : launch_tile_k<R, NS, RB, 1, 3>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+          return ring ? launch_tile_k<R, NS, RB, 0, 2>(P, batch, cps, coef, s0, d0, s1, d1, part, st)
+                      : launch_tile_k<R, NS, RB, 0, 3>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
+        }
+      }
       if (P.kind == 1) return launch_tile_k<R, NS, RB, 1, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
       return launch_tile_k<R, NS, RB, 0, 1>(P, batch, cps, coef, s0, d0, s1, d1, part, st);
     }

@@ -178,6 +178,26 @@ def test_geometry_environment_fills_unset_options_and_is_validated(q, monkeypatc
         monkeypatch.delenv(name)
 
 
+def test_forward_diagonal_rides_on_the_contiguous_pass_run_last(q):
+    """zz26: each block's IsingZZ phase (but the first, which the product-state
+    kernel takes) is multiplied in the last round of the contiguous 2^12 pass,
+    which the planner runs last in its group (post=2: compile-time element
+    patterns); the gathering pass stays first."""
+    desc = q.Circuit(26, W.zz_circuit(26, 12), path=2).describe(8)
+    fwd = [dict(re.findall(r"(\w+)=(-?\d+)", l.split("[")[0])) for l in desc.splitlines()
+           if l.startswith("F ") and " TILE " in l]
+    posts = [d for d in fwd if d["post"] != "0"]
+    assert len(posts) == 11 and all(d["post"] == "2" and d["c"] == "12" and d["t"] == "12" for d in posts)
+    groups = {}
+    for d in fwd:
+        groups.setdefault(d["layer"], []).append(d)
+    for g in groups.values():
+        assert [d["post"] for d in g] == ["0", "0", "2"] and g[0]["h0"] == "19"
+    # complex128 (2^11 tiles) keeps the generic last-round phase on the last pass
+    d128 = q.Circuit(20, W.zz_circuit(20, 3), dtype="c128", path=2).describe(2)
+    assert "post=2" not in d128 and "post=1" in d128
+
+
 def test_tuner_candidates_stay_in_range():
     from paper_2506_04891_gb300 import tune
     for dtype in ("c64", "c128"):
