@@ -245,6 +245,15 @@ __device__ __forceinline__ int tswz(int i) {
     return i ^ (int)((0x0752613443162570ull >> (4 * ((i >> 3) & 15))) & 15);
 }
 
+// the same with a shared-space address (advanced by the caller)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_sa(unsigned sa, const void* gmem) {
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
 template <int BYTES>
 __device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -492,11 +501,18 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     const int base = tile_base(f);
     C* d0 = buf + slot * NS * T;
     if constexpr (IL) {
-      if (ds_half >= 0) {
+      if (ds_half >= 0 && !P.gather) {
+        // one pointer and one shared-space address, each advanced by a constant
+        const C* gp = il_src + (base | elem_off(il_i));
+        unsigned sa = (unsigned)__cvta_generic_to_shared(&d0[il_si]);
+#pragma unroll 4
+        for (int i = il_i; i < T; i += kThreads / 2, sa += kThreads * sizeof(C), gp += ds_half)
+          cp_async_sa<sizeof(C)>(sa, gp);
+      } else if (ds_half >= 0) {
         int gi = base | elem_off(il_i);
 #pragma unroll 4
         for (int i = il_i, si = il_si; i < T; i += kThreads / 2, si += kThreads, gi += ds_half)
-          cp_async_elem<sizeof(C)>(&d0[si], &il_src[P.gather ? ring_finv32(gi, n) : gi]);
+          cp_async_elem<sizeof(C)>(&d0[si], &il_src[ring_finv32(gi, n)]);
       } else {
         for (int i = il_i, si = il_si; i < T; i += kThreads / 2, si += kThreads) {
           int gi = base | elem_off(i);
@@ -504,10 +520,22 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           cp_async_elem<sizeof(C)>(&d0[si], &il_src[gi]);
         }
       }
+    } else if (ds_full >= 0 && !P.gather) {
+      const int g0 = base | elem_off(threadIdx.x);
+      const C* gp0 = s0b + g0;
+      const C* gp1 = NS == 2 ? s1b + g0 : nullptr;
+      unsigned sa = (unsigned)__cvta_generic_to_shared(&d0[sw_tid]);
+      for (int i = threadIdx.x; i < T; i += kThreads, sa += kThreads * sizeof(C), gp0 += ds_full) {
+        cp_async_sa<sizeof(C)>(sa, gp0);
+        if (NS == 2) {
+          cp_async_sa<sizeof(C)>(sa + T * sizeof(C), gp1);
+          gp1 += ds_full;
+        }
+      }
     } else if (ds_full >= 0) {
       int gi = base | elem_off(threadIdx.x);
       for (int i = threadIdx.x, si = sw_tid; i < T; i += kThreads, si += kThreads, gi += ds_full) {
-        const int g2 = P.gather ? ring_finv32(gi, n) : gi;
+        const int g2 = ring_finv32(gi, n);
         cp_async_elem<sizeof(C)>(&d0[si], &s0b[g2]);
         if (NS == 2) cp_async_elem<sizeof(C)>(&d0[T + si], &s1b[g2]);
       }
