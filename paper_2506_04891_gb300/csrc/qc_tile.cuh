@@ -834,6 +834,20 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
             if (NS == 2) d1b[gd] = S1[pi];
           }
         }
+      } else if (NS == 1 && sizeof(C) == 8 && ds_pair >= 0) {
+        // forward paired 16-byte stores, i = 2 tid + k * 2 kThreads, with the
+        // global and shared-memory pointers advanced by constants: the swizzle
+        // leaves bits >= 8 alone, so the partner pi ^ 1 sits at a fixed
+        // distance dp = +-1 from pi (the backward keeps the indexed loop below,
+        // measured faster there)
+        C* q0p = d0b + (base | elem_off(2 * threadIdx.x));
+        const int dp = (sw_tid2 ^ 1) - sw_tid2;
+        const C* sp = S0 + sw_tid2;
+#pragma unroll 2
+        for (int i = 2 * threadIdx.x; i < T; i += 2 * kThreads, sp += 2 * kThreads, q0p += ds_pair) {
+          const C e0 = sp[0], e1 = sp[dp];
+          *reinterpret_cast<float4*>(q0p) = make_float4(e0.x, e0.y, e1.x, e1.y);
+        }
       } else if (sizeof(C) == 8) {
         // paired 16-byte stores: i = 2 tid + k * 2 kThreads (c >= 1 here, so the
         // pair never straddles the contiguous segment)
