@@ -16,6 +16,18 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libqlayer.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["qc_tile_bwd.cu", "qc_tile_fwd.cu", "qc_kernels.cu", "qc_api.cu", "qc_noalloc.cu"]
+# the kernel files compile once per precision (QC_INST_R = 4 float, 8 double),
+# so the two halves build in parallel
+SPLIT = {"qc_tile_bwd.cu", "qc_tile_fwd.cu", "qc_kernels.cu"}
+
+
+def _units():
+    for src in SOURCES:
+        if src in SPLIT:
+            yield src, "_r4", ["-DQC_INST_R=4"]
+            yield src, "_r8", ["-DQC_INST_R=8"]
+        else:
+            yield src, "", []
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -26,10 +38,11 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found (set NVCC or put CUDA's bin on PATH)")
 
 
-def _compile(nvcc: str, src: str, extra) -> str:
-    obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
+def _compile(nvcc: str, unit, extra) -> str:
+    src, tag, defs = unit
+    obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + tag + ".o")
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
-           "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, src), "-o", obj, *extra]
+           "--expt-relaxed-constexpr", *defs, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -41,8 +54,9 @@ def _compile(nvcc: str, src: str, extra) -> str:
 def build(verbose: bool = False, extra=()) -> str:
     nvcc = nvcc_path()
     os.makedirs(BUILD_DIR, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(nvcc, s, list(extra)), SOURCES))
+    units = list(_units())
+    with cf.ThreadPoolExecutor(max_workers=len(units)) as ex:
+        objs = list(ex.map(lambda u: _compile(nvcc, u, list(extra)), units))
     tmp = OUT + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

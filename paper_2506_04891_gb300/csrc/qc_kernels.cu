@@ -10,6 +10,13 @@
 #include "qc_gates.cuh"
 #include "qc_kernels.h"
 
+// QC_INST_R selects the precision this object instantiates (4: float, 8:
+// double, 0: both); the build compiles the file once per precision, and the
+// non-template definitions go into the float object only
+#ifndef QC_INST_R
+#define QC_INST_R 0
+#endif
+
 namespace qc {
 // ---------------------------------------------------------------------------
 // Coefficients: gate matrices, generators, diagonal phase tables
@@ -642,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
 // ---------------------------------------------------------------------------
 // rows: job j has batch * nvals rows starting at row0[j]; V[row] = sum of the
 // sample's CTAs' partials for that value.
-__global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restrict__ jobs,
+static __global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restrict__ jobs,
                                                    const long long* __restrict__ row0, int njobs,
                                                    long long rowbase, const double* __restrict__ part,
                                                    double* __restrict__ V) {
@@ -671,7 +678,7 @@ __global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restrict__ jo
 
 // one thread per output of a job group: combine values into gradients
 // (added to d_theta / d_x, which the caller zeroes first).
-__global__ void k_finalize(const RedJob* __restrict__ jobs, const long long* __restrict__ row0,
+static __global__ void k_finalize(const RedJob* __restrict__ jobs, const long long* __restrict__ row0,
                            const int* __restrict__ out0, int njobs, int outbase, int nout,
                            const RedOut* __restrict__ outs, int batch, int n_in,
                            const double* __restrict__ V, double* __restrict__ d_theta,
@@ -703,7 +710,7 @@ __global__ void k_finalize(const RedJob* __restrict__ jobs, const long long* __r
 
 // <Z_q> from marginals: ez[b][q] = W - 2 M_{n-1-q}, one block per (b, q)
 // summing the sample's CTA partials of W and of the qubit's bit marginal.
-__global__ void __launch_bounds__(kThreads) k_ez_from_marg(int n, int blk_per_sample, long long nblk,
+static __global__ void __launch_bounds__(kThreads) k_ez_from_marg(int n, int blk_per_sample, long long nblk,
                                                            const double* __restrict__ part,
                                                            double* __restrict__ ez) {
   const int b = blockIdx.x / n, q = blockIdx.x % n;
@@ -1076,7 +1083,9 @@ cudaError_t launch_prodinit(int n, int cb, int batch, const void* pv, void* psi,
   return cudaGetLastError();
 }
 
+#if QC_INST_R != 8
 size_t tile_smem_bytes(const TilePass& P, int ns, int rsize) { return tile_smem_layout(P, ns, rsize).end; }
+#endif
 
 template <class R>
 cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, const void* coef,
@@ -1086,11 +1095,13 @@ cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, c
   return launch_tile_bwd<R>(P, rb, batch, cps, coef, s0, d0, s1, d1, part, st);
 }
 
+#if QC_INST_R != 8
 long long diag_grid(const DiagPass& P, int batch) {
   long long nch = 1LL << (P.n - P.cb);
   long long cpb = P.xcomp ? (nch > 1 ? nch / 2 : 1) : nch;
   return cpb * batch;
 }
+#endif
 
 template <class R, int NS, int ZM, int XC, int JB>
 static cudaError_t launch_diag_jb(const DiagPass& P, int batch, const void* coef, const void* s0,
@@ -1139,10 +1150,12 @@ cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, 
   return launch_diag_z<R, 2, Z_IDENT, 0>(P, batch, coef, s0, d0, s1, d1, part, st);
 }
 
+#if QC_INST_R != 8
 size_t ring_smem_bytes(const RingPass& P, int rsize) {
   size_t amps = P.whole ? ((size_t)1 << P.n) : ((size_t)1 << P.t);
   return amps * 2 * rsize;
 }
+#endif
 
 template <class R>
 cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, void* d0,
@@ -1207,6 +1220,7 @@ cudaError_t launch_laminit(int n, int cb, int batch, const double* gez, const vo
   return cudaGetLastError();
 }
 
+#if QC_INST_R != 8
 cudaError_t launch_reduce(const RedJob* jobs, const long long* row0, const int* out0, int njobs,
                           long long rowbase, long long nrows, int outbase, int nout,
                           const RedOut* outs, int batch, int n_in, const double* part, double* V,
@@ -1219,11 +1233,14 @@ cudaError_t launch_reduce(const RedJob* jobs, const long long* row0, const int* 
                                                  n_in, V, d_theta, d_x);
   return cudaGetLastError();
 }
+#endif
 
+#if QC_INST_R != 8
 size_t smem_circuit_bytes(int n, int bwd, int rsize) {
   size_t amps = (size_t)1 << n;
   return amps * 2 * rsize * (bwd ? 2 : 1) + (kWarps + kMaxQubits + 1) * sizeof(double);
 }
+#endif
 
 template <class R>
 cudaError_t launch_smem(const SmemLayer* prog, int nl, int n, int batch, int bwd, const void* coef,
@@ -1268,7 +1285,11 @@ cudaError_t launch_smem(const SmemLayer* prog, int nl, int n, int batch, int bwd
                                       const void*, void*, double*, const double*, double*, int,    \
                                       cudaStream_t);
 
+#if QC_INST_R != 8
 QC_INST(float)
+#endif
+#if QC_INST_R != 4
 QC_INST(double)
+#endif
 
 }  // namespace qc

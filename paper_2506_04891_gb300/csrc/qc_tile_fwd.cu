@@ -2,6 +2,11 @@
 // their own so the build compiles them in parallel with the other kernels.
 #include "qc_tile.cuh"
 
+// QC_INST_R: 4 float, 8 double, 0 both (the build compiles one object per precision)
+#ifndef QC_INST_R
+#define QC_INST_R 0
+#endif
+
 namespace qc {
 
 template <class R>
@@ -17,9 +22,13 @@ cudaError_t launch_tile_fwd(const TilePass& P, int rb, int batch, int cps, const
   return cudaErrorInvalidValue;
 }
 
+#if QC_INST_R != 8
 template cudaError_t launch_tile_fwd<float>(const TilePass&, int, int, int, const void*, const void*, void*,
                                              const void*, void*, double*, cudaStream_t);
+#endif
+#if QC_INST_R != 4
 template cudaError_t launch_tile_fwd<double>(const TilePass&, int, int, int, const void*, const void*, void*,
                                               const void*, void*, double*, cudaStream_t);
+#endif
 
 }  // namespace qc
