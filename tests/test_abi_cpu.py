@@ -281,6 +281,45 @@ def test_tile_passes_cover_every_qubit_once(q, n, dtype, rb):
                 assert bits == {b for q0 in range(1, n - 1, 2) for b in (n - 2 - q0, n - 1 - q0)}
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [5, 12, 13, 17, 20, 26])
+@pytest.mark.parametrize("family", ["zz", "hea", "ibm", "ionq", "qdi"])
+def test_fused_tile_groups_cover_every_qubit_once(q, family, n, dtype):
+    """With fusion on (diagonals as phases, rings as gathers and scatters,
+    companion gradients, the contiguous pass moved last for a forward post
+    phase, register bits by gate type), each tile group of the plan still
+    applies its layer's gates on every bit exactly once; a post phase with
+    compile-time patterns sits on a contiguous 2^12 pass that runs last."""
+    build = {"zz": W.zz_circuit, "hea": W.hea_circuit, "ibm": W.ibm_circuit,
+             "ionq": W.ionq_circuit, "qdi": W.qdi_circuit}[family]
+    desc, _ = _plan(q, n, build(n, 3), dtype=dtype)
+    groups = []
+    for tag, layer, d, ops in _tile_passes(desc):
+        if groups and groups[-1][0] == (tag, layer):
+            groups[-1][1].append((d, ops))
+        else:
+            groups.append(((tag, layer), [(d, ops)]))
+    assert groups
+    for (tag, layer), passes in groups:
+        bits = []
+        two = False
+        for d, ops in passes:
+            c, h0 = d["c"], d["h0"]
+            for l, is2q, _np in ops:
+                l = int(l)
+                glob = l if l < c else h0 + (l - c)
+                bits += [glob, glob + 1] if is2q else [glob]
+                two = two or bool(is2q)
+        assert len(bits) == len(set(bits)), (tag, layer, sorted(bits))
+        if two:
+            assert len(bits) in (2 * ((n - 0) // 2), 2 * ((n - 1) // 2))
+        else:
+            assert set(bits) == set(range(n)), (tag, layer, sorted(bits))
+        for k, (d, _ops) in enumerate(passes):
+            if d.get("post") == 2:
+                assert k == len(passes) - 1 and d["c"] == d["t"] == 12 and dtype == "c64"
+
+
 def test_zz26_plan_checkpoints_and_workspace(q):
     cfg = W.WORKLOADS["zz26"]
     desc, ws = _plan(q, 26, cfg["layers"](), batch=8, path=0)
