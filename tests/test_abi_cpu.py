@@ -320,6 +320,29 @@ def test_fused_tile_groups_cover_every_qubit_once(q, family, n, dtype):
                 assert k == len(passes) - 1 and d["c"] == d["t"] == 12 and dtype == "c64"
 
 
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8])
+def test_ring_pair_identity_the_permuted_stores_rely_on(n):
+    """The backward ring kernel and the scatter pass store 16-byte pairs because
+    the inverse CNOT-ring map sends k and k ^ 1 ^ 2^(n-1) to adjacent indices:
+    f^-1(k ^ 1 ^ 2^(n-1)) = f^-1(k) ^ 1.  Checked against the oracle's ring
+    layer applied to every basis state."""
+    import numpy as np
+    from oracle import qsim_oracle as O
+    N = 1 << n
+    f = np.empty(N, dtype=np.int64)
+    for k in range(N):
+        e = np.zeros(N, dtype=np.complex128)
+        e[k] = 1.0
+        out = O.forward_sample(n, [("CNOT_RING", "none", 0, 0)], None, None, psi0=e)
+        f[k] = int(np.argmax(np.abs(out)))
+        assert abs(out[f[k]]) == 1.0
+    finv = np.empty(N, dtype=np.int64)
+    finv[f] = np.arange(N)
+    top = 1 << (n - 1)
+    for k in range(N):
+        assert finv[k ^ 1 ^ top] == finv[k] ^ 1, (n, k)
+
+
 def test_zz26_plan_checkpoints_and_workspace(q):
     cfg = W.WORKLOADS["zz26"]
     desc, ws = _plan(q, 26, cfg["layers"](), batch=8, path=0)
