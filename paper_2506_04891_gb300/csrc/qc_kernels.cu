@@ -649,6 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
 // ---------------------------------------------------------------------------
 // rows: job j has batch * nvals rows starting at row0[j]; V[row] = sum of the
 // sample's CTAs' partials for that value.
+#if QC_INST_R != 8
 static __global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restrict__ jobs,
                                                    const long long* __restrict__ row0, int njobs,
                                                    long long rowbase, const double* __restrict__ part,
@@ -675,9 +676,11 @@ static __global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restri
     V[row] = tsum;
   }
 }
+#endif
 
 // one thread per output of a job group: combine values into gradients
 // (added to d_theta / d_x, which the caller zeroes first).
+#if QC_INST_R != 8
 static __global__ void k_finalize(const RedJob* __restrict__ jobs, const long long* __restrict__ row0,
                            const int* __restrict__ out0, int njobs, int outbase, int nout,
                            const RedOut* __restrict__ outs, int batch, int n_in,
@@ -707,6 +710,7 @@ static __global__ void k_finalize(const RedJob* __restrict__ jobs, const long lo
   }
   if (J.source == QC_SRC_THETA && d_theta) d_theta[ro.pidx] += tot;
 }
+#endif
 
 // <Z_q> from marginals: ez[b][q] = W - 2 M_{n-1-q}, one block per (b, q)
 // summing the sample's CTA partials of W and of the qubit's bit marginal.

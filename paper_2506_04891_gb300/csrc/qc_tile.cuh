@@ -468,6 +468,12 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   // (PRE = 2 / 3: ring / identity z map on a contiguous 2^12 pass whose last
   // round holds bits 8 .. 11, with compile-time element patterns)
   const bool fpost_ok = NS == 1 && PRE >= 1 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
+  // The last round stores straight to global memory when the pass is
+  // contiguous (c = t = 12) and that round holds bits 8 .. 11: thread g then
+  // has the amplitudes g + 256 a, 32 consecutive ones per warp for each a.
+  // The shared-memory write of that round and the store loop are skipped.
+  const bool dstore = RB == 4 && P.store && !P.scatter && t == 12 && c == t && P.nrounds >= 1 &&
+                      P.rlo[P.nrounds - 1] == 8 && !(NS == 1 && P.post && !fpost_ok);
 
   // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
   // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
@@ -734,17 +740,29 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
             v0[a] = cmul<R>(cmul<R>(p0, ratio[z0se ^ pat]), v0[a]);
           }
         }
+        if (dstore && r == rlast) {
+          // lo = 8: local index g | a << 8, global tile_base | g | a << 8
+          C* o0 = d0b + (tile_base(f) | g);
 #pragma unroll
-        for (int a = 0; a < (1 << RB); ++a) {
-          int ad = pb;
+          for (int a = 0; a < (1 << RB); ++a) o0[a << 8] = v0[a];
+          if constexpr (NS == 2) {
+            C* o1 = d1b + (tile_base(f) | g);
 #pragma unroll
-          for (int j = 0; j < RB; ++j)
-            if (a & (1 << j)) ad ^= basis[j];
-          if constexpr (IL) {
-            *reinterpret_cast<float4*>(&S0[2 * ad]) = make_float4(v0[a].x, v0[a].y, v1[a].x, v1[a].y);
-          } else {
-            S0[ad] = v0[a];
-            if (NS == 2) S1[ad] = v1[a];
+            for (int a = 0; a < (1 << RB); ++a) o1[a << 8] = v1[a];
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) {
+            int ad = pb;
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+              if (a & (1 << j)) ad ^= basis[j];
+            if constexpr (IL) {
+              *reinterpret_cast<float4*>(&S0[2 * ad]) = make_float4(v0[a].x, v0[a].y, v1[a].x, v1[a].y);
+            } else {
+              S0[ad] = v0[a];
+              if (NS == 2) S1[ad] = v1[a];
+            }
           }
         }
       }
@@ -790,7 +808,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
       __syncthreads();
     }
 
-    if (P.store) {
+    if (P.store && !dstore) {
       const int base = tile_base(f);
       if (IL && P.scatter) {
         // backward scatter through the CNOT ring's inverse map f^-1, in
