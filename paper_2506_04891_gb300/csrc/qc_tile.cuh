@@ -468,12 +468,15 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   // (PRE = 2 / 3: ring / identity z map on a contiguous 2^12 pass whose last
   // round holds bits 8 .. 11, with compile-time element patterns)
   const bool fpost_ok = NS == 1 && PRE >= 1 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph_post)->ok;
-  // The last round stores straight to global memory when the pass is
-  // contiguous (c = t = 12) and that round holds bits 8 .. 11: thread g then
-  // has the amplitudes g + 256 a, 32 consecutive ones per warp for each a.
-  // The shared-memory write of that round and the store loop are skipped.
-  const bool dstore = RB == 4 && P.store && !P.scatter && t == 12 && c == t && P.nrounds >= 1 &&
-                      P.rlo[P.nrounds - 1] == 8 && !(NS == 1 && P.post && !fpost_ok);
+  // The last round stores straight to global memory when it holds local bits
+  // 8 .. 11 of a 2^12 tile: thread g has the local indices g | a << 8, at
+  // global base | off(g) | a << dshift (dshift = 8 for a contiguous pass, 8 -
+  // c + h0 when c <= 8), and the lanes of a warp cover the contiguous low bits
+  // (c >= 5), so each a is 32 consecutive amplitudes.  The shared-memory
+  // write of that round and the store loop are skipped.
+  const int dshift = c >= t ? 8 : (c <= 8 ? 8 - c + h0 : -1);
+  const bool dstore = RB == 4 && P.store && !P.scatter && t == 12 && c >= 5 && dshift >= 0 &&
+                      P.nrounds >= 1 && P.rlo[P.nrounds - 1] == 8 && !(NS == 1 && P.post && !fpost_ok);
 
   // Offsets inside one sample (< 2^30) stay 32-bit; the sample base is in the
   // pointers.  Tile bits [c, h0) and [h0 + m, n) are disjoint from element
@@ -741,14 +744,21 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           }
         }
         if (dstore && r == rlast) {
-          // lo = 8: local index g | a << 8, global tile_base | g | a << 8
-          C* o0 = d0b + (tile_base(f) | g);
+          const int gb = tile_base(f) | elem_off(g);
+          C* o0 = d0b + gb;
+          C* o1 = NS == 2 ? d1b + gb : nullptr;
+          if (c >= t) {  // contiguous: compile-time offsets a << 8
 #pragma unroll
-          for (int a = 0; a < (1 << RB); ++a) o0[a << 8] = v0[a];
-          if constexpr (NS == 2) {
-            C* o1 = d1b + (tile_base(f) | g);
+            for (int a = 0; a < (1 << RB); ++a) {
+              o0[a << 8] = v0[a];
+              if constexpr (NS == 2) o1[a << 8] = v1[a];
+            }
+          } else {
 #pragma unroll
-            for (int a = 0; a < (1 << RB); ++a) o1[a << 8] = v1[a];
+            for (int a = 0; a < (1 << RB); ++a) {
+              o0[a << dshift] = v0[a];
+              if constexpr (NS == 2) o1[a << dshift] = v1[a];
+            }
           }
         } else {
 #pragma unroll
