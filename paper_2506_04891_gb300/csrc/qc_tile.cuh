@@ -558,6 +558,10 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     }
   };
 
+  // Backward, one buffer and a direct-store last round: the next tile's copy
+  // starts as soon as every thread holds its last-round elements (the buffer
+  // is free then), so it overlaps that round's gates and stores.
+  const bool early = NS == 2 && nst == 1 && dstore;
   long long f = r0;
   int slot = 0;
   for (int j = 0; j + 1 < nst; ++j) {
@@ -569,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     // tile f is complete once at most nst - 1 newer groups are pending
     const long long fn = f + (long long)(nst - 1) * cps;
     const int sn = slot + nst - 1 < nst ? slot + nst - 1 : slot - 1;
-    if (fn < tps) issue(fn, sn);
+    if (fn < tps && !(early && f != r0)) issue(fn, sn);  // early: already in flight
     cp_async_commit();
     if (nst == 3) cp_async_wait_group<2>();
     else if (nst == 2) cp_async_wait_group<1>();
@@ -709,6 +713,15 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
           } else {
             v0[a] = S0[ad];
             if (NS == 2) v1[a] = S1[ad];
+          }
+        }
+        if constexpr (NS == 2) {
+          if (early && r == rlast) {
+            // every thread holds its elements of this round (one group each):
+            // the buffer is free for the next tile
+            __syncthreads();
+            if (f + cps < tps) issue(f + cps, 0);
+            cp_async_commit();
           }
         }
         tile_bit<R, NS, RB, KIND, 0>(P, r, v0, v1, sco, acc);
