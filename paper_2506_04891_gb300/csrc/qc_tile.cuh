@@ -356,8 +356,11 @@ __device__ __forceinline__ cx<R> fph_elem(const unsigned char* blk, cx<R> p0, in
   return cmul<R>(p0, ratio[z0se ^ M->patk[k]]);
 }
 
-// PRE = 1 / 2: backward pass with a diagonal layer (identity / ring z map)
-// undone in round 0 (P.pre).
+// PRE, backward: 1 / 2 undo a diagonal layer (identity / ring z map) in a
+// sweep before the rounds (P.pre).  PRE, forward: 1 multiplies a following
+// diagonal's phase in the last round with table-driven element patterns, 2 / 3
+// the same on a contiguous 2^12 pass with compile-time patterns (ring /
+// identity z map).
 constexpr int tile_minb(int rsize, int ns, int kind, int pre) {
   return (rsize == 4 && kind == 1 && ns == 1) ? QC_REAL_MINB
          : (ns == 2 && pre > 0) ? QC_PRE_MINB
