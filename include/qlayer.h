@@ -34,9 +34,12 @@
  *   (3,0) = -i exp(+2 pi i (phi0+phi1)) sin(pi theta).
  *
  * Ownership: every device buffer passed in belongs to the caller.  A circuit
- *   handle owns only small device tables (coefficients, reduction scratch)
- *   that qc_create / the first call at a larger batch allocate and
- *   qc_destroy frees.
+ *   handle owns one device buffer, the partial sums of qc_expect_z, which
+ *   qc_create allocates and qc_destroy frees.  The plan tables a call needs
+ *   (coefficient and reduction jobs) are written into the caller's workspace
+ *   by each qc_forward / qc_backward, in stream order, so after qc_create no
+ *   compute call allocates device memory, frees it or synchronises the
+ *   device (qc_alloc_count counts the calls that do).
  * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Every
  *   compute call only enqueues work on that stream and returns; it never
  *   synchronises unless its description says so.
@@ -155,7 +158,10 @@ QC_API void qc_default_options(qc_options* opt);
 /* Validates a layer list and builds a circuit for n qubits (1 <= n <= 30).
  * `layers` (host memory, n_layers >= 0 entries) is copied.  `opt` may be
  * NULL for defaults.  On success *out receives a handle; on failure *out is
- * left NULL.  Allocates a few KB of device memory on the current device. */
+ * left NULL.  On the current device it allocates the qc_expect_z scratch
+ * (max(2 MiB, 8 (n+1) 2^(n - min(n,14)) bytes)) and loads the <Z> kernels;
+ * without a usable device the handle still serves the host-only calls
+ * (planning, sizes, descriptions). */
 QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_layers,
                            const qc_options* opt, qc_circuit** out);
 
@@ -166,7 +172,8 @@ QC_API qc_status qc_destroy(qc_circuit* c);
 /* Number of theta entries and per-sample x columns the circuit reads. */
 QC_API qc_status qc_num_params(const qc_circuit* c, int* n_theta, int* n_input_per_sample);
 
-/* Device workspace qc_forward / qc_backward need for `batch` samples. */
+/* Device workspace qc_forward / qc_backward need for `batch` samples
+ * (host only: plans the batch, at most 16 plans are kept per handle). */
 QC_API qc_status qc_workspace_bytes(const qc_circuit* c, int batch, size_t* bytes);
 
 /* Forward pass (Sec. 2/3): psi_out[b] = U_L ... U_1 |0...0> for b < batch.
@@ -184,8 +191,31 @@ QC_API qc_status qc_forward(qc_circuit* c, int batch, const double* x, const dou
 
 /* <Z_q> per sample: ez[b][q] = sum_k |psi[b][k]|^2 (1 - 2 bit_{n-1-q}(k)).
  * psi: device [batch][2^n] complex; ez: device [batch][n] float64.
- * Reductions are deterministic (fixed order, float64 above the thread level). */
+ * Reductions are deterministic (fixed order, float64 above the thread level).
+ * Large batches run as several launches that reuse the handle's scratch in
+ * stream order, so two calls on one handle must not overlap on the GPU. */
 QC_API qc_status qc_expect_z(qc_circuit* c, int batch, const void* psi, double* ez, void* stream);
+
+/* <Z_q> exactly as qc_expect_z computes it, for callers that must not
+ * allocate device memory while they run.  (The paper has no counterpart:
+ * this entry point exists for the library's users, not for the method.)
+ * Who needs it: a caller whose device memory is wholly held by another
+ * allocator (a framework's caching pool, a budget reserved at start-up), or
+ * whose loop cannot afford the device-wide synchronisation that a cudaMalloc
+ * or cudaFree may cause.  The per-CTA partial sums live in a fixed array that
+ * is part of this library's device image (8 MiB, held by every device that
+ * loads the library until the process exits); qc_create resolves its address
+ * and loads the kernels on the current device, so no call here loads code or
+ * allocates.  If qc_create ran before the device was usable, the first call
+ * does that set-up instead; make that first call outside any stream capture.
+ * Limit: batch * 2^(n - min(n, 14)) * (n + 1) <= 2^20 partial sums (n = 26:
+ * batch <= 9); larger requests return QC_ERR_INVALID and enqueue nothing.
+ * Every call on a device shares the one array: calls that overlap on the GPU
+ * (other streams, or other threads) race and give wrong results, so order
+ * them (one stream, or events).  psi, ez and the return values are as for
+ * qc_expect_z. */
+QC_API qc_status qc_expect_z_noalloc(qc_circuit* c, int batch, const void* psi, double* ez,
+                                     void* stream);
 
 /* Adjoint backward of L = sum_b sum_q g_ez[b][q] <Z_q>_b.
  *   psi_out  the state qc_forward wrote for the same (x, theta); read only
@@ -222,13 +252,23 @@ QC_API const char* qc_last_error(void);
  * qc_launch_count: number of kernels this library has enqueued in the process.
  * qc_profile_enable(1): from now on, bracket every enqueued kernel (or kernel
  *   pair) with CUDA events on its stream; (0) stops; both reset the records.
+ * qc_alloc_count: number of device allocations, frees and device-wide
+ *   synchronisations the library has made in the process (qc_create,
+ *   qc_destroy and qc_profile_summary make them; the compute calls do not).
  * qc_profile_summary: synchronises the device and writes one line per kernel
  *   class, "name launches total_ms algorithmic_bytes", where the bytes are
  *   the state traffic the method needs per launch (each state read and written
  *   once per pass), summed over launches. */
 QC_API unsigned long long qc_launch_count(void);
+QC_API unsigned long long qc_alloc_count(void);
 QC_API qc_status qc_profile_enable(int on);
 QC_API qc_status qc_profile_summary(char* buf, size_t len);
+
+/* Measured arithmetic ceiling of the current device (diagnostics for the
+ * roofline): kind 0 = FP32 fmaf, 1 = packed FP32x2 FMA (__ffma2_rn), 2 = FP64
+ * fma; *tflops receives TFLOP/s at 2 flops per FMA lane.  Runs its own
+ * kernels on a private stream and waits for them; allocates nothing. */
+QC_API qc_status qc_fma_peak(int kind, double* tflops);
 
 /* Text description of the plan for `batch` (host only: no device access):
  * one line per kernel pass with its geometry and buffers. */

@@ -37,11 +37,11 @@ thread_local std::string g_last_error;
 // ---- launch counting and optional per-launch event timing (diagnostics) ----
 enum ProfClass {
   PC_COEF, PC_PRODINIT, PC_TILE_F, PC_TILE_B, PC_DIAG_F, PC_DIAG_B, PC_RING_F, PC_RING_B,
-  PC_EXPECT, PC_LAMINIT, PC_REDUCE, PC_SMEM_F, PC_SMEM_B, PC_N
+  PC_EXPECT, PC_LAMINIT, PC_REDUCE, PC_SMEM_F, PC_SMEM_B, PC_UPLOAD, PC_N
 };
 const char* kProfNames[PC_N] = {"coef", "prodinit", "tile_fwd", "tile_bwd", "diag_fwd", "diag_bwd",
                                 "ring_fwd", "ring_bwd", "expect", "laminit", "reduce", "smem_fwd",
-                                "smem_bwd"};
+                                "smem_bwd", "upload"};
 unsigned long long g_launches = 0;
 bool g_prof = false;
 struct ProfRec {
@@ -139,17 +139,40 @@ struct Plan {
   // whole-circuit program
   std::vector<SmemLayer> prog;
   int nslots = 0;
-  // device copies (lazily uploaded)
-  void* dev = nullptr;
-  size_t dev_bytes = 0;
-  CoefJob* d_coef_jobs = nullptr;
-  RedJob* d_jobs = nullptr;
-  long long* d_row0 = nullptr;
-  int* d_out0 = nullptr;
-  RedOut* d_outs = nullptr;
-  SmemLayer* d_prog = nullptr;
+  // Device tables (coefficient jobs, reduction jobs and maps, the
+  // whole-circuit program): one host blob that every call writes into the
+  // first bytes of the caller's workspace (off_tables = 0) with the upload
+  // kernel, so no call allocates device memory or waits on the host.
+  std::vector<unsigned char> tables;
+  size_t o_cj = 0, o_j = 0, o_r = 0, o_o0 = 0, o_ro = 0, o_pr = 0;
+  unsigned long long last_use = 0;  // plan cache recency
   std::vector<std::vector<int>> job_groups;  // finalize groups (serial when outputs overlap)
 };
+
+// Device addresses of a plan's tables inside a workspace.
+struct PlanDev {
+  const CoefJob* coef_jobs;
+  const RedJob* jobs;
+  const long long* row0;
+  const int* out0;
+  const RedOut* outs;
+  const SmemLayer* prog;
+};
+PlanDev plan_dev(const Plan& p, const char* ws) {
+  PlanDev d;
+  d.coef_jobs = reinterpret_cast<const CoefJob*>(ws + p.o_cj);
+  d.jobs = reinterpret_cast<const RedJob*>(ws + p.o_j);
+  d.row0 = reinterpret_cast<const long long*>(ws + p.o_r);
+  d.out0 = reinterpret_cast<const int*>(ws + p.o_o0);
+  d.outs = reinterpret_cast<const RedOut*>(ws + p.o_ro);
+  d.prog = reinterpret_cast<const SmemLayer*>(ws + p.o_pr);
+  return d;
+}
+
+// Device allocations, frees and device-wide synchronisations made by the
+// library (diagnostics).  None is reachable from the compute calls after
+// qc_create.
+unsigned long long g_alloc_calls = 0;
 
 }  // namespace
 
@@ -160,7 +183,10 @@ struct qc_circuit {
   qc_options opt{};
   std::vector<LayerInfo> layers;
   int n_theta = 0, n_in = 0;
-  std::map<int, std::unique_ptr<Plan>> plans;
+  std::map<int, std::unique_ptr<Plan>> plans;  // host-only plans, at most kMaxPlans
+  unsigned long long plan_clock = 0;
+  // <Z> partial sums of qc_expect_z, allocated by qc_create: room for every
+  // CTA of at least one sample; larger batches run in sample chunks
   void* exp_scratch = nullptr;
   size_t exp_scratch_bytes = 0;
   const void* last_ws = nullptr;
@@ -484,6 +510,42 @@ void add_job(Plan& P, int kind, int source, long long part_off, long long nblk, 
     o.job = jid;
     P.outs.push_back(o);
   }
+}
+
+// Packs the plan's device tables into one blob (layout: coef jobs | jobs |
+// row0 | out0 | outs | prog, each 256-byte aligned) placed at the start of the
+// workspace, and moves every other workspace region after it.
+void build_tables(Plan& p) {
+  std::vector<unsigned char>& host = p.tables;
+  host.clear();
+  auto put = [&](const void* src, size_t bytes) {
+    size_t o = align256(host.size());
+    host.resize(o + bytes);
+    if (bytes) memcpy(host.data() + o, src, bytes);
+    return o;
+  };
+  p.o_cj = put(p.coef_jobs.data(), p.coef_jobs.size() * sizeof(CoefJob));
+  p.o_j = put(p.jobs.data(), p.jobs.size() * sizeof(RedJob));
+  p.o_r = put(p.row0.data(), p.row0.size() * sizeof(long long));
+  std::vector<RedOut> ro;
+  for (auto& o : p.outs) {
+    RedOut r;
+    r.val = o.val;
+    r.pidx = o.pidx;
+    r.scale = o.scale;
+    ro.push_back(r);
+  }
+  // outputs are ordered by job; k_finalize maps a flat output id to its job
+  std::vector<int> out0;
+  for (auto& J : p.jobs) out0.push_back(J.first);
+  p.o_o0 = put(out0.data(), out0.size() * sizeof(int));
+  p.o_ro = put(ro.data(), ro.size() * sizeof(RedOut));
+  p.o_pr = put(p.prog.data(), p.prog.size() * sizeof(SmemLayer));
+  host.resize(align256(std::max<size_t>(host.size(), 16)));
+  const size_t shift = host.size();
+  for (size_t* o : {&p.off_coef, &p.off_pv, &p.off_run0, &p.off_run1, &p.off_lam0, &p.off_lam1,
+                    &p.off_ckpt, &p.off_part, &p.off_V, &p.ws_fwd, &p.ws_bwd})
+    *o += shift;
 }
 
 std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
@@ -997,59 +1059,37 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
     }
   }
   P->unplaced = g_plan_unplaced;
+  build_tables(p);
   return P;
 }
 
-qc_status upload_plan(Plan& p) {
-  if (p.dev) return QC_OK;
-  // layout: coef jobs | jobs | row0 | out0 (per group) | outs | prog
-  std::vector<char> host;
-  auto put = [&](const void* src, size_t bytes) {
-    size_t o = align256(host.size());
-    host.resize(o + bytes);
-    if (bytes) memcpy(host.data() + o, src, bytes);
-    return o;
-  };
-  size_t o_cj = put(p.coef_jobs.data(), p.coef_jobs.size() * sizeof(CoefJob));
-  size_t o_j = put(p.jobs.data(), p.jobs.size() * sizeof(RedJob));
-  size_t o_r = put(p.row0.data(), p.row0.size() * sizeof(long long));
-  std::vector<RedOut> ro;
-  for (auto& o : p.outs) {
-    RedOut r;
-    r.val = o.val;
-    r.pidx = o.pidx;
-    r.scale = o.scale;
-    ro.push_back(r);
-  }
-  // outputs are ordered by job; k_finalize maps a flat output id to its job
-  std::vector<int> out0;
-  for (auto& J : p.jobs) out0.push_back(J.first);
-  size_t o_o0 = put(out0.data(), out0.size() * sizeof(int));
-  size_t o_ro = put(ro.data(), ro.size() * sizeof(RedOut));
-  size_t o_pr = put(p.prog.data(), p.prog.size() * sizeof(SmemLayer));
-  size_t bytes = std::max<size_t>(host.size(), 256);
-  cudaError_t e = cudaMalloc(&p.dev, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(plan tables)");
-  e = cudaMemcpy(p.dev, host.data(), host.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(plan tables)");
-  char* d = (char*)p.dev;
-  p.d_coef_jobs = (CoefJob*)(d + o_cj);
-  p.d_jobs = (RedJob*)(d + o_j);
-  p.d_row0 = (long long*)(d + o_r);
-  p.d_out0 = (int*)(d + o_o0);
-  p.d_outs = (RedOut*)(d + o_ro);
-  p.d_prog = (SmemLayer*)(d + o_pr);
-  p.dev_bytes = bytes;
+// Writes the plan's device tables into the caller's workspace (stream order).
+qc_status upload_tables(const Plan& p, char* ws, cudaStream_t st) {
+  if (p.tables.empty()) return QC_OK;
+  ProfScope ps(PC_UPLOAD, 0, st, (int)((p.tables.size() + kUploadBytes - 1) / kUploadBytes));
+  cudaError_t e = launch_upload(p.tables.data(), p.tables.size(), ws, st);
+  if (e != cudaSuccess) return cuda_fail(e, "plan table upload");
   return QC_OK;
 }
 
+constexpr size_t kMaxPlans = 16;
+
+// Plans are host-only (their device tables travel with every call), so the
+// cache is bounded: the least recently used plan is dropped beyond kMaxPlans.
 qc_status get_plan(qc_circuit* c, int batch, Plan** out) {
   auto it = c->plans.find(batch);
   if (it == c->plans.end()) {
     auto P = build_plan(c, batch);
     if (P->unplaced) return fail(QC_ERR_UNSUPPORTED, "planner: a gate found no round in its tile pass");
+    if (c->plans.size() >= kMaxPlans) {
+      auto lru = c->plans.begin();
+      for (auto j = c->plans.begin(); j != c->plans.end(); ++j)
+        if (j->second->last_use < lru->second->last_use) lru = j;
+      c->plans.erase(lru);
+    }
     it = c->plans.emplace(batch, std::move(P)).first;
   }
+  it->second->last_use = ++c->plan_clock;
   *out = it->second.get();
   return QC_OK;
 }
@@ -1059,8 +1099,8 @@ qc_status run_coef(qc_circuit* c, Plan& p, int batch, const double* x, const dou
                    char* ws, cudaStream_t st) {
   if (p.coef_jobs.empty()) return QC_OK;
   ProfScope ps(PC_COEF, 0, st);
-  cudaError_t e = launch_coef<R>(p.d_coef_jobs, (int)p.coef_jobs.size(), c->n, batch, c->n_in, x,
-                                 theta, ws + p.off_coef, st);
+  cudaError_t e = launch_coef<R>(plan_dev(p, ws).coef_jobs, (int)p.coef_jobs.size(), c->n, batch,
+                                 c->n_in, x, theta, ws + p.off_coef, st);
   if (e != cudaSuccess) return cuda_fail(e, "coef kernel");
   return QC_OK;
 }
@@ -1139,6 +1179,7 @@ qc_status run_reduce(qc_circuit* c, Plan& p, int batch, char* ws, double* d_thet
   if (p.jobs.empty()) return QC_OK;
   const double* part = (const double*)(ws + p.off_part);
   double* V = (double*)(ws + p.off_V);
+  const PlanDev d = plan_dev(p, ws);
   for (auto& g : p.job_groups) {
     // a group is a contiguous run of jobs
     const int j0 = g.front(), nj = (int)g.size();
@@ -1146,8 +1187,8 @@ qc_status run_reduce(qc_circuit* c, Plan& p, int batch, char* ws, double* d_thet
     int nout = 0;
     for (int j : g) { rows += (long long)batch * p.jobs[j].nvals; nout += p.jobs[j].nout; }
     ProfScope ps(PC_REDUCE, 0, st, 2);
-    cudaError_t e = launch_reduce(p.d_jobs + j0, p.d_row0 + j0, p.d_out0 + j0, nj, p.row0[j0], rows,
-                                  p.jobs[j0].first, nout, p.d_outs, batch, c->n_in, part, V,
+    cudaError_t e = launch_reduce(d.jobs + j0, d.row0 + j0, d.out0 + j0, nj, p.row0[j0], rows,
+                                  p.jobs[j0].first, nout, d.outs, batch, c->n_in, part, V,
                                   d_theta, d_x, st);
     if (e != cudaSuccess) return cuda_fail(e, "reduce kernels");
   }
@@ -1170,14 +1211,14 @@ qc_status forward_impl(qc_circuit* c, int batch, const double* x, const double* 
   if (wbytes < p->ws_fwd) return fail(QC_ERR_OOM, "workspace smaller than qc_workspace_bytes");
   if ((uintptr_t)workspace % 256) return fail(QC_ERR_INVALID, "workspace must be 256-byte aligned");
   if ((uintptr_t)psi_out % 16) return fail(QC_ERR_INVALID, "psi_out must be 16-byte aligned");
-  s = upload_plan(*p);
-  if (s != QC_OK) return s;
   char* ws = (char*)workspace;
+  s = upload_tables(*p, ws, st);
+  if (s != QC_OK) return s;
   s = run_coef<R>(c, *p, batch, x, theta, ws, st);
   if (s != QC_OK) return s;
   if (p->smem) {
     ProfScope ps(PC_SMEM_F, (double)p->S, st);
-    cudaError_t e = launch_smem<R>(p->d_prog, (int)p->prog.size(), c->n, batch, 0, ws + p->off_coef,
+    cudaError_t e = launch_smem<R>(plan_dev(*p, ws).prog, (int)p->prog.size(), c->n, batch, 0, ws + p->off_coef,
                                    nullptr, psi_out, ez, nullptr, nullptr, p->nslots, st);
     if (e != cudaSuccess) return cuda_fail(e, "whole-circuit forward kernel");
   } else {
@@ -1206,9 +1247,9 @@ qc_status backward_impl(qc_circuit* c, int batch, const double* x, const double*
   if ((uintptr_t)workspace % 256) return fail(QC_ERR_INVALID, "workspace must be 256-byte aligned");
   if (p->nckpt > 0 && (c->last_ws != workspace || c->last_batch != batch))
     return fail(QC_ERR_INVALID, "checkpointed backward needs the workspace of the preceding forward");
-  s = upload_plan(*p);
-  if (s != QC_OK) return s;
   char* ws = (char*)workspace;
+  s = upload_tables(*p, ws, st);
+  if (s != QC_OK) return s;
   cudaError_t e;
   if (d_theta && c->n_theta > 0) {
     e = cudaMemsetAsync(d_theta, 0, sizeof(double) * c->n_theta, st);
@@ -1222,7 +1263,7 @@ qc_status backward_impl(qc_circuit* c, int batch, const double* x, const double*
   if (s != QC_OK) return s;
   if (p->smem) {
     ProfScope ps(PC_SMEM_B, (double)p->S, st);
-    e = launch_smem<R>(p->d_prog, (int)p->prog.size(), c->n, batch, 1, ws + p->off_coef, psi_out,
+    e = launch_smem<R>(plan_dev(*p, ws).prog, (int)p->prog.size(), c->n, batch, 1, ws + p->off_coef, psi_out,
                        nullptr, nullptr, gez, (double*)(ws + p->off_part), p->nslots, st);
     if (e != cudaSuccess) return cuda_fail(e, "whole-circuit backward kernel");
   } else {
@@ -1246,6 +1287,7 @@ int layer_class(int kind) {
 }  // namespace
 
 namespace qc {
+void count_alloc() { ++g_alloc_calls; }
 void circuit_shape(const qc_circuit* c, int* n, int* dtype) {
   *n = c->n;
   *dtype = (int)c->dtype;
@@ -1386,18 +1428,35 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
     }
     c->layers.push_back(L);
   }
+  // the <Z> scratch of qc_expect_z: 2 MiB or one sample's partial sums,
+  // whichever is larger; on a host without a usable device it stays NULL
+  // (planning calls still work; qc_expect_z then reports the missing device)
+  {
+    const int cb = std::min(n, 14);
+    const size_t per_sample = ((size_t)1 << (n - cb)) * (n + 1) * sizeof(double);
+    const size_t bytes = std::max<size_t>(per_sample, (size_t)2 << 20);
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      count_alloc();
+      if (cudaMalloc(&c->exp_scratch, bytes) == cudaSuccess) c->exp_scratch_bytes = bytes;
+      else c->exp_scratch = nullptr;
+    }
+    cudaGetLastError();
+    noalloc_prepare(n, (int)dtype);
+  }
   *out = c.release();
   return QC_OK;
 }
 
 QC_API qc_status qc_destroy(qc_circuit* c) {
   if (!c) return QC_OK;
-  bool any_dev = c->exp_scratch != nullptr;
-  for (auto& kv : c->plans) any_dev = any_dev || kv.second->dev;
-  if (any_dev) cudaDeviceSynchronize();
-  for (auto& kv : c->plans)
-    if (kv.second->dev) cudaFree(kv.second->dev);
-  if (c->exp_scratch) cudaFree(c->exp_scratch);
+  if (c->exp_scratch) {
+    // work in flight may still read the scratch
+    count_alloc();
+    cudaDeviceSynchronize();
+    count_alloc();
+    cudaFree(c->exp_scratch);
+  }
   delete c;
   return QC_OK;
 }
@@ -1439,25 +1498,24 @@ QC_API qc_status qc_expect_z(qc_circuit* c, int batch, const void* psi, double* 
   qc_status s = check_common(c, batch);
   if (s != QC_OK) return s;
   if (!psi || !ez) return fail(QC_ERR_INVALID, "psi and ez must be non-NULL");
+  if (!c->exp_scratch)
+    return fail(QC_ERR_CUDA, "qc_expect_z: the circuit was created without a usable CUDA device");
   const int n = c->n, cb = std::min(n, 14);
-  const size_t need = (size_t)(((long long)batch << (n - cb)) * (n + 1)) * sizeof(double);
-  if (need > c->exp_scratch_bytes) {
-    if (c->exp_scratch) {
-      cudaDeviceSynchronize();
-      cudaFree(c->exp_scratch);
-      c->exp_scratch = nullptr;
-      c->exp_scratch_bytes = 0;
-    }
-    cudaError_t e = cudaMalloc(&c->exp_scratch, need);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(expect scratch)");
-    c->exp_scratch_bytes = need;
-  }
+  // samples per launch: the partial sums of a chunk fit the scratch qc_create
+  // allocated (launches on one stream reuse it in order)
+  const size_t per_sample = ((size_t)1 << (n - cb)) * (n + 1) * sizeof(double);
+  const int chunk = (int)std::max<size_t>(1, c->exp_scratch_bytes / per_sample);
   cudaStream_t st = (cudaStream_t)stream;
-  ProfScope ps(PC_EXPECT, (double)batch * ((size_t)1 << n) * 2 * c->rsize, st, 2);
-  cudaError_t e = c->dtype == QC_C64
-                      ? launch_expect<float>(n, cb, batch, psi, (double*)c->exp_scratch, ez, st)
-                      : launch_expect<double>(n, cb, batch, psi, (double*)c->exp_scratch, ez, st);
-  if (e != cudaSuccess) return cuda_fail(e, "expect kernel");
+  const size_t sbytes = ((size_t)1 << n) * 2 * c->rsize;
+  for (int b0 = 0; b0 < batch; b0 += chunk) {
+    const int nb = std::min(chunk, batch - b0);
+    const char* ps_in = (const char*)psi + (size_t)b0 * sbytes;
+    ProfScope ps(PC_EXPECT, (double)nb * sbytes, st, 2);
+    cudaError_t e = c->dtype == QC_C64
+                        ? launch_expect<float>(n, cb, nb, ps_in, (double*)c->exp_scratch, ez + (size_t)b0 * n, st)
+                        : launch_expect<double>(n, cb, nb, ps_in, (double*)c->exp_scratch, ez + (size_t)b0 * n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "expect kernel");
+  }
   return QC_OK;
 }
 
@@ -1548,6 +1606,8 @@ QC_API qc_status qc_wait(void* stream, int timeout_ms) {
 
 QC_API unsigned long long qc_launch_count(void) { return g_launches; }
 
+QC_API unsigned long long qc_alloc_count(void) { return g_alloc_calls; }
+
 QC_API qc_status qc_profile_enable(int on) {
   g_prof = on != 0;
   g_nrec = 0;
@@ -1555,6 +1615,7 @@ QC_API qc_status qc_profile_enable(int on) {
 }
 
 QC_API qc_status qc_profile_summary(char* buf, size_t len) {
+  count_alloc();
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
   double ms[PC_N] = {0}, bytes[PC_N] = {0};

@@ -224,9 +224,25 @@ struct SmemLayer {
   double gscale;
 };
 
+// One launch of the table-upload kernel: up to kUploadBytes bytes carried in
+// the kernel's parameter block, written to dst + off (16-byte multiples).
+constexpr size_t kUploadBytes = 16384;
+struct UploadChunk {
+  unsigned long long off;
+  unsigned n;
+  unsigned pad;
+  alignas(16) unsigned char data[kUploadBytes];
+};
+
 // Shape of a circuit handle and the thread-local error message, for entry
 // points defined outside qc_api.cu.
 void circuit_shape(const qc_circuit* c, int* n, int* dtype);
 qc_status set_error(qc_status s, const char* msg);
+// qc_noalloc.cu: resolves the no-allocation scratch array's address and loads
+// the <Z> kernels on the current device (best effort; errors are cleared)
+void noalloc_prepare(int n, int dtype);
+// counts a device allocation, free or device-wide synchronisation the
+// library makes (diagnostics: qc_alloc_count)
+void count_alloc();
 
 }  // namespace qc

@@ -6,6 +6,8 @@
 // State: psi[b][k] interleaved complex (float2 / double2), qubit q = bit n-1-q.
 // Every kernel here is bandwidth-shaped: a CTA streams a tile or a contiguous
 // chunk of one sample's state through shared memory or registers once.
+#include <string.h>
+
 #include "qc_device.cuh"
 #include "qc_gates.cuh"
 #include "qc_kernels.h"
@@ -1240,6 +1242,57 @@ cudaError_t launch_reduce(const RedJob* jobs, const long long* row0, const int* 
 #endif
 
 #if QC_INST_R != 8
+// Plan tables are written into the caller's workspace by this kernel: the
+// bytes travel in the kernel's parameter block, so the copy is ordered on the
+// stream like any launch and needs neither a device allocation nor a host
+// synchronisation.
+static __global__ void __launch_bounds__(kThreads) k_upload(const __grid_constant__ UploadChunk U,
+                                                          unsigned char* __restrict__ dst) {
+  const uint4* src = reinterpret_cast<const uint4*>(U.data);
+  uint4* d = reinterpret_cast<uint4*>(dst + U.off);
+  for (unsigned i = threadIdx.x; i < U.n / 16; i += blockDim.x) d[i] = src[i];
+}
+
+cudaError_t launch_upload(const void* host, size_t bytes, void* dst, cudaStream_t st) {
+  const unsigned char* h = static_cast<const unsigned char*>(host);
+  for (size_t o = 0; o < bytes; o += kUploadBytes) {
+    UploadChunk U;
+    const size_t k = bytes - o < kUploadBytes ? bytes - o : kUploadBytes;
+    U.off = o;
+    U.n = (unsigned)((k + 15) & ~(size_t)15);
+    memcpy(U.data, h + o, k);
+    if (U.n > k) memset(U.data + k, 0, U.n - k);
+    k_upload<<<1, kThreads, 0, st>>>(U, static_cast<unsigned char*>(dst));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+#endif
+
+// Loads the <Z> kernels of an n-qubit circuit into the current context (with
+// lazy module loading a kernel's code is otherwise loaded, which may allocate,
+// at its first launch).
+template <class R>
+cudaError_t preload_expect(int n) {
+  const int cb = n < 14 ? n : 14;
+  const int jb = cb > 8 ? cb - 8 : 0;
+  cudaFuncAttributes a;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (jb) {
+    case 0: e = cudaFuncGetAttributes(&a, k_expect<R, 0>); break;
+    case 1: e = cudaFuncGetAttributes(&a, k_expect<R, 1>); break;
+    case 2: e = cudaFuncGetAttributes(&a, k_expect<R, 2>); break;
+    case 3: e = cudaFuncGetAttributes(&a, k_expect<R, 3>); break;
+    case 4: e = cudaFuncGetAttributes(&a, k_expect<R, 4>); break;
+    case 5: e = cudaFuncGetAttributes(&a, k_expect<R, 5>); break;
+    case 6: e = cudaFuncGetAttributes(&a, k_expect<R, 6>); break;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&a, k_ez_from_marg);
+}
+
+#if QC_INST_R != 8
 size_t smem_circuit_bytes(int n, int bwd, int rsize) {
   size_t amps = (size_t)1 << n;
   return amps * 2 * rsize * (bwd ? 2 : 1) + (kWarps + kMaxQubits + 1) * sizeof(double);
@@ -1283,6 +1336,7 @@ cudaError_t launch_smem(const SmemLayer* prog, int nl, int n, int batch, int bwd
                                       void*, const double*, cudaStream_t);                         \
   template cudaError_t launch_expect<R>(int, int, int, const void*, double*, double*,              \
                                         cudaStream_t);                                             \
+  template cudaError_t preload_expect<R>(int);                                                     \
   template cudaError_t launch_laminit<R>(int, int, int, const double*, const void*, void*,         \
                                          cudaStream_t);                                            \
   template cudaError_t launch_smem<R>(const SmemLayer*, int, int, int, int, const void*,           \

@@ -72,6 +72,12 @@ cudaError_t launch_reduce(const RedJob* jobs, const long long* row0, const int* 
                           const RedOut* outs, int batch, int n_in, const double* part, double* V,
                           double* d_theta, double* d_x, cudaStream_t st);
 
+// copies `bytes` host bytes to device memory `dst` in stream order through
+// kernel parameters (no allocation, no synchronisation)
+cudaError_t launch_upload(const void* host, size_t bytes, void* dst, cudaStream_t st);
+template <class R>
+cudaError_t preload_expect(int n);
+
 size_t tile_smem_bytes(const TilePass& P, int ns, int rsize);
 size_t ring_smem_bytes(const RingPass& P, int rsize);
 size_t smem_circuit_bytes(int n, int bwd, int rsize);

@@ -27,10 +27,12 @@ def allreduce_dtheta(dtheta, group=None):
     return dtheta
 
 
-def data_parallel_step(circuit, x_shard, theta, g_shard, group=None):
+def data_parallel_step(circuit, x_shard, theta, g_shard, group=None, psi_out=None, workspace=None):
     """Forward + <Z> + adjoint backward of this rank's shard, then the d theta
-    all-reduce.  Returns (ez_shard, dtheta_total, dx_shard)."""
-    psi, ez = circuit.forward(x_shard, theta)
-    dth, dx = circuit.backward(x_shard, theta, psi, g_shard)
+    all-reduce.  `circuit` is a ``qlayer.Circuit`` (or anything with its
+    forward / backward signature); psi_out and workspace, if given, are reused
+    across steps.  Returns (ez_shard, dtheta_total, dx_shard)."""
+    psi, ez = circuit.forward(x_shard, theta, batch=g_shard.shape[0], psi_out=psi_out, workspace=workspace)
+    dth, dx = circuit.backward(x_shard, theta, psi, g_shard, workspace=workspace)
     allreduce_dtheta(dth, group)
     return ez, dth, dx

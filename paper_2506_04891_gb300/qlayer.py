@@ -33,9 +33,11 @@ STATUS = {0: "QC_OK", 1: "QC_ERR_INVALID", 2: "QC_ERR_OOM", 3: "QC_ERR_CUDA", 4:
 # Symbols include/qlayer.h declares (checked by the tests).
 EXPORTED = [
     "qc_version", "qc_default_options", "qc_create", "qc_destroy", "qc_num_params",
-    "qc_workspace_bytes", "qc_forward", "qc_expect_z", "qc_backward", "qc_staging_bytes",
-    "qc_step_host", "qc_wait", "qc_last_error", "qc_launch_count", "qc_profile_enable",
-    "qc_profile_summary", "qc_describe_plan",
+    "qc_workspace_bytes", "qc_forward", "qc_expect_z", "qc_expect_z_noalloc", "qc_backward",
+    "qc_staging_bytes",
+    "qc_step_host", "qc_wait", "qc_last_error", "qc_launch_count", "qc_alloc_count",
+    "qc_profile_enable",
+    "qc_profile_summary", "qc_describe_plan", "qc_fma_peak",
 ]
 
 
@@ -80,6 +82,7 @@ def _load():
         "qc_workspace_bytes": (I, [P, I, ctypes.POINTER(S)]),
         "qc_forward": (I, [P, I, P, P, P, P, P, S, P]),
         "qc_expect_z": (I, [P, I, P, P, P]),
+        "qc_expect_z_noalloc": (I, [P, I, P, P, P]),
         "qc_backward": (I, [P, I, P, P, P, P, P, P, P, S, P]),
         "qc_staging_bytes": (I, [P, I, ctypes.POINTER(S)]),
         "qc_step_host": (I, [P, I, P, P, P, P, P, P, P, P, S, P, P]),
@@ -87,8 +90,10 @@ def _load():
         "qc_last_error": (ctypes.c_char_p, []),
         "qc_describe_plan": (I, [P, I, ctypes.c_char_p, S]),
         "qc_launch_count": (ctypes.c_ulonglong, []),
+        "qc_alloc_count": (ctypes.c_ulonglong, []),
         "qc_profile_enable": (I, [I]),
         "qc_profile_summary": (I, [ctypes.c_char_p, S]),
+        "qc_fma_peak": (I, [I, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -164,6 +169,12 @@ def qc_expect_z(h, batch, psi, ez, stream):
     _check(_lib.qc_expect_z(h, int(batch), psi, ez, stream))
 
 
+def qc_expect_z_noalloc(h, batch, psi, ez, stream):
+    """<Z> without any device allocation (partial sums in the library's fixed
+    device array; see include/qlayer.h for the limit and the ordering rule)."""
+    _check(_lib.qc_expect_z_noalloc(h, int(batch), psi, ez, stream))
+
+
 def qc_backward(h, batch, x, theta, psi_out, g_ez, d_theta, d_x, workspace, workspace_bytes, stream):
     _check(_lib.qc_backward(h, int(batch), x, theta, psi_out, g_ez, d_theta, d_x, workspace,
                             workspace_bytes, stream))
@@ -187,6 +198,10 @@ def qc_launch_count() -> int:
     return _lib.qc_launch_count()
 
 
+def qc_alloc_count() -> int:
+    return _lib.qc_alloc_count()
+
+
 def qc_profile_enable(on: bool):
     _check(_lib.qc_profile_enable(1 if on else 0))
 
@@ -200,6 +215,13 @@ def qc_profile_summary():
         name, cnt, ms, by = line.split()
         out[name] = (int(cnt), float(ms), float(by))
     return out
+
+
+def qc_fma_peak(kind: int) -> float:
+    """Measured TFLOP/s: 0 FP32 fmaf, 1 FP32x2 FFMA2, 2 FP64 fma (synchronises)."""
+    v = ctypes.c_double()
+    _check(_lib.qc_fma_peak(int(kind), ctypes.byref(v)))
+    return v.value
 
 
 def qc_describe_plan(h: int, batch: int) -> str:

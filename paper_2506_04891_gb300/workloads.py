@@ -13,6 +13,7 @@ Workloads (the paper's circuits are synthetic with random inputs, Sec. 3):
 * ``ionq20`` n=20, B=32,  GPI2(0), RZ(x) encoding, 8 x [GPI, GPI2, MS brick]
 * ``zz26``   n=26, B=8,   RX(x) embedding, 12 x [RY, IsingZZ ring, CNOT ring]
 * serving requests: RX(x), 6 x [RZ, RY, RZ, CNOT ring], n in 8..24, B in 1..512
+  (``serve20`` / ``serve24``: that circuit at n = 20 and 24 with B = 2)
 
 The native-gate bodies (IBM: ECR, X, SX, RZ; IonQ: GPI, GPI2, MS with a
 virtual-RZ encoding layer) follow the gate sets named in Appendix B; the
@@ -137,6 +138,9 @@ WORKLOADS = {
     "ibm20": dict(n=20, batch=32, dtype="c64", layers=lambda: ibm_circuit(20, 8)),
     "ionq20": dict(n=20, batch=32, dtype="c64", layers=lambda: ionq_circuit(20, 8)),
     "zz26": dict(n=26, batch=8, dtype="c64", layers=lambda: zz_circuit(26, 12)),
+    # the serving request circuit at the two largest qubit counts of the stream
+    "serve20": dict(n=20, batch=2, dtype="c64", layers=lambda: serving_circuit(20)),
+    "serve24": dict(n=24, batch=2, dtype="c64", layers=lambda: serving_circuit(24)),
 }
 
 

@@ -5,12 +5,13 @@ per-gate einsum, reverse-sweep adjoint) on inputs drawn by
 ``paper_2506_04891_gb300.workloads.draw_inputs`` with seed 0.  The CUDA path is
 never called.  Usage:
 
-    python tests/golden/make_goldens.py hea12 ibm20 ionq20 zz26
+    python tests/golden/make_goldens.py hea4 hea12 ibm20 ionq20 zz26 serve20 serve24
 
 Output: tests/golden/<workload>.npz with, for each listed sample b:
 ez[b] (<Z_q>), dth[b] (per-sample d loss / d theta), dx[b], and the amplitudes
-psi[b][idx] at a fixed seeded set of indices; for hea12 also ez / dx of every
-sample and the batch-summed d theta.  The loss is sum_q <Z_q> / n per sample.
+psi[b][idx] at a fixed seeded set of indices; for the workloads whose every
+sample is listed ("all": hea12, serve20, serve24) also the batch-summed d theta
+(and, where n <= 12, two whole states).  The loss is sum_q <Z_q> / n per sample.
 """
 from __future__ import annotations
 
@@ -28,7 +29,8 @@ from oracle import qsim_oracle as O  # noqa: E402
 from paper_2506_04891_gb300 import workloads as W  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SAMPLES = {"hea12": "all", "ibm20": [0, 31], "ionq20": [0, 31], "zz26": [0]}
+SAMPLES = {"hea4": "all", "hea12": "all", "ibm20": [0, 31], "ionq20": [0, 31], "zz26": [0], "serve20": "all",
+           "serve24": "all"}
 N_PSI_IDX = 512
 
 
@@ -72,8 +74,9 @@ def main(names):
         if SAMPLES[name] == "all":
             out["dth_sum"] = out["dth"].sum(axis=0)
             keep = [0, len(bs) - 1]
-            out["psi_full"] = np.stack([per[bs[k]][7] for k in keep])
-            out["psi_full_samples"] = np.array([bs[k] for k in keep])
+            if per[bs[0]][7] is not None:  # whole states only where n <= 12
+                out["psi_full"] = np.stack([per[bs[k]][7] for k in keep])
+                out["psi_full_samples"] = np.array([bs[k] for k in keep])
             out["dth"] = out["dth"][keep]
             out["dth_samples"] = np.array([bs[k] for k in keep])
         np.savez_compressed(os.path.join(HERE, f"{name}.npz"), **out)

@@ -459,3 +459,20 @@ def test_workspace_grows_with_batch(q):
     _, w1 = _plan(q, 14, layers, batch=1)
     _, w8 = _plan(q, 14, layers, batch=8)
     assert w8 > w1 > 0
+
+
+def test_planning_many_batches_allocates_nothing_and_keeps_tables_in_the_workspace(q):
+    """Plans are host-only: sizing and describing plans for many batch sizes
+    (more than the handle keeps) makes no device allocation, frees nothing and
+    never synchronises, and the workspace holds the plan tables."""
+    layers = W.hea_circuit(16, 2)
+    c = q.Circuit(16, layers, dtype="c64", path=2)
+    a0 = q.qc_alloc_count()
+    sizes = {}
+    for b in list(range(1, 41)) + [7, 3, 1]:
+        sizes[b] = c.workspace_bytes(b)
+        assert "TILE" in c.describe(b)
+    assert q.qc_alloc_count() == a0
+    # a plan rebuilt after it left the bounded cache has the same layout
+    assert c.workspace_bytes(1) == sizes[1] and c.workspace_bytes(40) == sizes[40]
+    assert sizes[40] > sizes[1]

@@ -1,9 +1,10 @@
 """World-size-2 gloo tests of the batch-sharded data-parallel step (CPU).
 
-Each rank computes its shard's gradients (the oracle stands in for the GPU
-kernels, which these CPU ranks cannot run) and the shared-angle gradient is
-all-reduced with paper_2506_04891_gb300.dist; rank 0 checks the result
-against the full-batch oracle.  A second test makes one rank fail on the host
+Each rank runs paper_2506_04891_gb300.dist.data_parallel_step on its shard
+with a CPU stand-in circuit (the oracle stands in for the GPU kernels, which
+these CPU ranks cannot run; it has the forward / backward signature of
+qlayer.Circuit), so the step function itself and its d theta all-reduce are
+exercised; the parent checks every rank against the full-batch oracle.  A second test makes one rank fail on the host
 and checks that the other sees an error instead of hanging.
 """
 import os
@@ -27,6 +28,27 @@ def _free_port():
     return p
 
 
+class _OracleCircuit:
+    """CPU stand-in with qlayer.Circuit's forward / backward signature."""
+
+    def __init__(self, n, layers):
+        self.n, self.layers = n, layers
+        self.calls = []
+
+    def forward(self, x, theta, batch=None, psi_out=None, workspace=None):
+        from oracle import qsim_oracle as O
+        self.calls.append(("forward", psi_out is not None, workspace is not None))
+        psi = O.forward(self.n, self.layers, x.numpy(), theta.numpy())
+        ez = O.expect_z(psi, self.n)
+        return torch.tensor(psi), torch.tensor(ez)
+
+    def backward(self, x, theta, psi_out, g, workspace=None):
+        from oracle import qsim_oracle as O
+        self.calls.append(("backward", workspace is not None))
+        _, dth, _, dx = O.adjoint(self.n, self.layers, x.numpy(), theta.numpy(), g.numpy())
+        return torch.tensor(dth), torch.tensor(dx)
+
+
 def _worker(rank, world, port, out_q, mode):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -41,10 +63,11 @@ def _worker(rank, world, port, out_q, mode):
         lo, hi = D.shard_bounds(B, world, rank)
         if mode == "fail" and rank == 1:
             raise RuntimeError("planted host-side failure on rank 1")
-        ez, dth, _, dx = O.adjoint(n, layers, x[lo:hi], theta, g[lo:hi])
-        t = torch.tensor(dth)
-        D.allreduce_dtheta(t)
-        out_q.put((rank, lo, hi, ez, t.numpy(), dx))
+        circ = _OracleCircuit(n, layers)
+        ez, t, dx = D.data_parallel_step(circ, torch.tensor(x[lo:hi]), torch.tensor(theta),
+                                         torch.tensor(g[lo:hi]), workspace="ws")
+        assert circ.calls == [("forward", False, True), ("backward", True)]
+        out_q.put((rank, lo, hi, ez.numpy(), t.numpy(), dx.numpy()))
     except Exception as e:  # reported to the parent
         out_q.put((rank, "error", repr(e)))
     finally:
