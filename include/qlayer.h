@@ -147,12 +147,20 @@ typedef struct {
   int32_t reg_bits_bwd;
   int32_t stages_fwd;
   int32_t stages_bwd;
+  /* Tile copies of the QC_C64 layer path: 1 (default) = TMA
+   * (cp.async.bulk.tensor, mbarrier completion) wherever the pass geometry
+   * allows (2^12-amplitude tiles with at least 16 contiguous amplitudes, no
+   * gathered loads; the planner also checks that every register round reads
+   * shared memory without bank conflicts), per-thread cp.async copies
+   * elsewhere; 0 = per-thread copies everywhere.  With the default 1, the
+   * process environment variable QC_TMA=0 (read at qc_create) turns it off. */
+  int32_t tma;
 } qc_options;
 
 /* Version of this ABI (major * 100 + minor). */
 QC_API int qc_version(void);
 
-/* Fills *opt with the defaults {-1, 0, 1, 0, 0, 0, 0, 0, 0}. */
+/* Fills *opt with the defaults {-1, 0, 1, 0, 0, 0, 0, 0, 0, 1}. */
 QC_API void qc_default_options(qc_options* opt);
 
 /* Validates a layer list and builds a circuit for n qubits (1 <= n <= 30).
@@ -261,6 +269,10 @@ QC_API const char* qc_last_error(void);
  *   once per pass), summed over launches. */
 QC_API unsigned long long qc_launch_count(void);
 QC_API unsigned long long qc_alloc_count(void);
+/* CTAs of TMA-staged tile passes that gave up waiting (2 s) for a tile copy
+ * since the last call, which clears the count; such a CTA leaves its tiles
+ * unprocessed.  Synchronises the device (diagnostics). */
+QC_API qc_status qc_kernel_timeouts(unsigned long long* count);
 QC_API qc_status qc_profile_enable(int on);
 QC_API qc_status qc_profile_summary(char* buf, size_t len);
 

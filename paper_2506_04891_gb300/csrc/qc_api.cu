@@ -106,6 +106,7 @@ struct Step {
   long long post_coef = 0, post_bstride = 0;
   int post_tb = 0, post_zmode = 0;
   int laminit = 0;      // backward RING: lambda formed from psi (first backward step)
+  int tma = 0;          // TILE: the TMA-staged kernel runs this pass
 };
 
 struct OutMap {
@@ -405,6 +406,8 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
       lo = std::min(lo, P.t - RB);
       const int hi = lo + RB;
       int got = 0;
+      // a round's ops in increasing bit order (the TMA pass numbers them so)
+      std::vector<size_t> in_round;
       for (size_t k = 0; k < ops.size(); ++k) {
         if (assigned[k]) continue;
         const int top = ops[k].op.l + (ops[k].op.is2q ? 1 : 0);
@@ -412,10 +415,15 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
           assigned[k] = 1;
           ++nass;
           ++got;
-          ordered.push_back(ops[k].op);
-          ordered_pidx.push_back(ops[k].pidx);
-          ordered_cpidx.push_back(ops[k].cpidx);
+          in_round.push_back(k);
         }
+      }
+      std::stable_sort(in_round.begin(), in_round.end(),
+                       [&](size_t x, size_t y) { return ops[x].op.l < ops[y].op.l; });
+      for (size_t k : in_round) {
+        ordered.push_back(ops[k].op);
+        ordered_pidx.push_back(ops[k].pidx);
+        ordered_cpidx.push_back(ops[k].cpidx);
       }
       if (!got || nr >= kMaxRounds) break;  // the check below turns this into an error
       P.rlo[nr] = (int8_t)lo;
@@ -510,6 +518,73 @@ void add_job(Plan& P, int kind, int source, long long part_off, long long nblk, 
     o.job = jid;
     P.outs.push_back(o);
   }
+}
+
+// ---- TMA-staged tile passes (complex64) ----
+// Whether the TMA kernel may run a pass: 2^12-amplitude tiles of >= 16
+// contiguous amplitudes (one 128-byte swizzle row), a box of at most 256 rows
+// per dimension, no gathered loads, the fused diagonals in the forms that
+// kernel has, and every round's shared-memory accesses free of bank conflicts
+// in the 128-byte swizzled layout (element i at i ^ (((i >> 4) & 7) << 1)):
+// a round on bits [0, RB) reads 16-byte pairs, and the 3 lane bits of a
+// quarter warp must move to 3 independent chunk bits; a higher round reads
+// 8-byte elements, and the 4 lane bits of a half warp must move to 4
+// independent bits of the element's position in its 128-byte row.
+int gf2_rank(int* rows, int nr) {
+  int rank = 0;
+  for (int bit = 0; bit < 30 && rank < nr; ++bit) {
+    int piv = -1;
+    for (int i = rank; i < nr; ++i)
+      if ((rows[i] >> bit) & 1) { piv = i; break; }
+    if (piv < 0) continue;
+    std::swap(rows[rank], rows[piv]);
+    for (int i = 0; i < nr; ++i)
+      if (i != rank && ((rows[i] >> bit) & 1)) rows[i] ^= rows[rank];
+    ++rank;
+  }
+  return rank;
+}
+bool tma_rounds_conflict_free(const TilePass& P, int rb) {
+  auto swz = [](int i) { return i ^ (((i >> 4) & 7) << 1); };
+  for (int r = 0; r < P.nrounds; ++r) {
+    const int lo = P.rlo[r];
+    int lanes[5], k = 0;
+    for (int p = 0; p < P.t && k < 5; ++p)
+      if (p < lo || p >= lo + rb) lanes[k++] = p;
+    int rows[4];
+    const int nr = lo == 0 ? 3 : 4;
+    if (k < nr) return false;
+    for (int j = 0; j < nr; ++j) rows[j] = lo == 0 ? (swz(1 << lanes[j]) >> 1) & 7 : swz(1 << lanes[j]) & 15;
+    if (gf2_rank(rows, nr) < nr) return false;
+  }
+  return true;
+}
+bool tma_enabled(const qc_circuit* c) { return c->dtype == QC_C64 && c->opt.tma == 1; }
+bool tma_pass_ok(const qc_circuit* c, const Step& st) {
+  if (!tma_enabled(c) || st.type != ST_TILE) return false;
+  const TilePass& P = st.tp;
+  if (P.t != 12 || P.c < 4 || P.t - P.c > 8 || P.gather || P.nstage < 1 || P.nstage > 2) return false;
+  if (P.kind == 2) {
+    if (P.pre || P.post || st.rb < 2 || st.rb > 4) return false;
+  } else if (st.rb != 3 && st.rb != 4) {
+    return false;
+  }
+  if (st.ns == 1) {
+    if (P.pre || P.scatter) return false;
+    if (P.post && !(st.rb == 4 && P.kind != 2 && fwd_post_contig(P))) return false;
+  } else {
+    if (P.post) return false;
+    if (P.pre && !(st.rb == 4 && P.c == 12 && P.nrounds >= 1 && P.rlo[0] == 0)) return false;
+  }
+  return tma_rounds_conflict_free(P, st.rb);
+}
+// CTAs per sample of a TMA pass: three per SM for the real-gate forward, two
+// otherwise, fewer if the shared memory does not fit
+int tma_cps(const qc_circuit* c, int batch, const Step& st) {
+  int res = (st.ns == 1 && st.tp.kind == 1) ? 3 : 2;
+  const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
+  while (res > 1 && (size_t)res * (tile_tma_smem_bytes(st.tp, st.ns) + per_cta_reserved) > per_sm) --res;
+  return tile_cps(batch, c->n, st.tp.t, res);
 }
 
 // Packs the plan's device tables into one blob (layout: coef jobs | jobs |
@@ -1059,6 +1134,12 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
     }
   }
   P->unplaced = g_plan_unplaced;
+  for (auto* v : {&p.fwd, &p.bwd})
+    for (Step& st : *v)
+      if (st.type == ST_TILE && tma_pass_ok(c, st)) {
+        st.tma = 1;
+        st.cps = tma_cps(c, batch, st);
+      }
   build_tables(p);
   return P;
 }
@@ -1146,8 +1227,14 @@ qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int 
       }
       case ST_TILE: {
         ProfScope ps(s.ns == 2 ? PC_TILE_B : PC_TILE_F, passb, st);
-        e = launch_tile<R>(s.tp, s.rb, s.ns, batch, s.cps, coef, buf(s.s0), buf(s.d0), buf(s.s1),
-                           buf(s.d1), part + s.part_off, st);
+        if (s.tma && sizeof(R) == 4)
+          e = s.ns == 1 ? launch_tile_tma_fwd(s.tp, s.rb, batch, s.cps, coef, buf(s.s0), buf(s.d0), buf(s.s1),
+                                              buf(s.d1), part + s.part_off, st)
+                        : launch_tile_tma_bwd(s.tp, s.rb, batch, s.cps, coef, buf(s.s0), buf(s.d0), buf(s.s1),
+                                              buf(s.d1), part + s.part_off, st);
+        else
+          e = launch_tile<R>(s.tp, s.rb, s.ns, batch, s.cps, coef, buf(s.s0), buf(s.d0), buf(s.s1),
+                             buf(s.d1), part + s.part_off, st);
         break;
       }
       case ST_DIAG: {
@@ -1310,6 +1397,7 @@ QC_API void qc_default_options(qc_options* opt) {
   opt->tile_bits_fwd = opt->tile_bits_bwd = 0;
   opt->reg_bits_fwd = opt->reg_bits_bwd = 0;
   opt->stages_fwd = opt->stages_bwd = 0;
+  opt->tma = 1;
 }
 
 QC_API const char* qc_last_error(void) { return g_last_error.c_str(); }
@@ -1335,6 +1423,8 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
   from_env(o.reg_bits_bwd, "QC_RB_BWD");
   from_env(o.stages_fwd, "QC_TILE_STAGES");
   from_env(o.stages_bwd, "QC_TILE_STAGES");
+  // QC_TMA=0 turns the TMA-staged passes off for circuits left at the default
+  if (o.tma == 1 && getenv("QC_TMA") && atoi(getenv("QC_TMA")) == 0) o.tma = 0;
   if (o.path < 0 || o.path > 2) return fail(QC_ERR_INVALID, "options.path must be 0, 1 or 2");
   if (o.ckpt_every < -1) return fail(QC_ERR_INVALID, "options.ckpt_every must be >= -1");
   {
@@ -1347,6 +1437,7 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
       return fail(QC_ERR_INVALID, "options.reg_bits_* (or QC_RB_*) must be in 0 .. 4");
     if (o.stages_fwd < 0 || o.stages_fwd > 3 || o.stages_bwd < 0 || o.stages_bwd > 3)
       return fail(QC_ERR_INVALID, "options.stages_* (or QC_TILE_STAGES) must be in 0 .. 3");
+    if (o.tma != 0 && o.tma != 1) return fail(QC_ERR_INVALID, "options.tma must be 0 or 1");
   }
   auto c = std::make_unique<qc_circuit>();
   c->n = n;
@@ -1608,6 +1699,15 @@ QC_API unsigned long long qc_launch_count(void) { return g_launches; }
 
 QC_API unsigned long long qc_alloc_count(void) { return g_alloc_calls; }
 
+QC_API qc_status qc_kernel_timeouts(unsigned long long* count) {
+  if (!count) return fail(QC_ERR_INVALID, "count is NULL");
+  count_alloc();
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  *count = tma_take_timeouts_fwd() + tma_take_timeouts_bwd();
+  return QC_OK;
+}
+
 QC_API qc_status qc_profile_enable(int on) {
   g_prof = on != 0;
   g_nrec = 0;
@@ -1663,9 +1763,9 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
         // contiguous pass's compile-time element patterns
         const int post = !st.tp.post ? 0
                          : (st.ns == 1 && st.rb == 4 && c->dtype == QC_C64 && fwd_post_contig(st.tp)) ? 2 : 1;
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d post=%d src=%d dst=%d",
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d post=%d tma=%d src=%d dst=%d",
                  tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nstage, st.tp.nrounds, st.tp.nops, st.tp.nslots,
-                 st.tp.store, st.tp.pre, post, st.s0, st.d0);
+                 st.tp.store, st.tp.pre, post, st.tma, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {
           snprintf(line, sizeof line, " [l=%d%s np=%d%s]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "",

@@ -51,6 +51,14 @@ template <class R>
 cudaError_t launch_tile_bwd(const TilePass& P, int rb, int batch, int cps, const void* coef,
                             const void* s0, void* d0, const void* s1, void* d1, double* part,
                             cudaStream_t st);
+// TMA-staged complex64 tile passes (qc_tile_tma_fwd.cu / qc_tile_tma_bwd.cu)
+cudaError_t launch_tile_tma_fwd(const TilePass& P, int rb, int batch, int cps, const void* coef, const void* s0,
+                                void* d0, const void* s1, void* d1, double* part, cudaStream_t st);
+cudaError_t launch_tile_tma_bwd(const TilePass& P, int rb, int batch, int cps, const void* coef, const void* s0,
+                                void* d0, const void* s1, void* d1, double* part, cudaStream_t st);
+size_t tile_tma_smem_bytes(const TilePass& P, int ns);
+unsigned long long tma_take_timeouts_fwd();
+unsigned long long tma_take_timeouts_bwd();
 template <class R>
 cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, const void* s0,
                         void* d0, const void* s1, void* d1, double* part, cudaStream_t st);

@@ -55,10 +55,13 @@ __device__ __forceinline__ R pauli_grad(int ck, cx<R> w0, cx<R> w1, cx<R> y0, cx
 // companion generator ck, also the gradient of the preceding layer's RX / RY
 // gate on the same qubit into acc[3 I + 1]: its generator commutes with that
 // gate, so the pair just undone (that layer's output side) gives it.
-template <class R, int RB, int I>
-__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, int ck,
+// MAYCK = false compiles the companion code out (ck is then ignored): the
+// compiler otherwise evaluates it for every pair and selects the result.
+template <class R, int RB, int I, bool MAYCK = true>
+__device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, int ck_in,
                                     R* acc) {
   using C = cx<R>;
+  const int ck = MAYCK ? ck_in : 0;
   if (real) {
     // RY (the only real gate; m is its packed real matrix): undo with M^T;
     // 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)

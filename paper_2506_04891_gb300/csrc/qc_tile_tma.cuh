@@ -1,0 +1,542 @@
+// Tile pass with TMA-staged tiles (complex64, 2^12-amplitude tiles).
+//
+// The same method as the tile pass in qc_tile.cuh (the gates of one layer
+// applied, or undone with their gradients, on the index bits a tile holds:
+// Sec. 2.2.2's Einsum restricted to a tile of the state), with the copy in
+// done by the Tensor Memory Accelerator instead of per-thread copies: one
+// thread issues one cp.async.bulk.tensor per state and tile, completion is
+// tracked by an mbarrier (transaction bytes), and the tile lands in shared
+// memory in the 128-byte swizzled layout, which the rounds read without bank
+// conflicts:
+//   * the tile's local index i (bits [0, c) of the sample index, then
+//     [h0, h0 + m)) is a 5-dimensional box of the state: 16 amplitudes (bits
+//     0..3, 128 bytes, the swizzle span), bits 4..c-1, the gap [c, h0) (one
+//     element of the box), bits [h0, h0 + m) and, merged with the batch, the
+//     bits above;
+//   * element i sits at i ^ (((i >> 4) & 7) << 1) (16-byte chunks XORed with
+//     the 128-byte row), a GF(2)-linear map, so a round's element addresses
+//     are one base XOR compile-time combinations of per-bit offsets;
+//   * a round on bits 0..RB-1 reads and writes amplitude pairs as 16-byte
+//     accesses (8 lanes of a quarter warp hit 8 distinct chunks); a round on
+//     higher bits uses 8-byte accesses whose half warps cover 16 distinct
+//     8-byte bank pairs (the planner checks this for every round).
+// psi and lambda (backward) sit in two separate arrays.  Waits on an mbarrier
+// are bounded in time; a CTA that gives up records it in a device counter
+// (qc_kernel_timeouts) and leaves after waiting, again bounded, for its copies
+// in flight.
+#pragma once
+#include <cuda.h>
+
+#include "qc_tile.cuh"
+
+namespace qc {
+
+constexpr int kTmaT = 12;  // log2 amplitudes of a TMA-staged tile
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// true once the phase with this parity has completed; false after limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_5d(unsigned dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                            int c4, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+// element i of a TMA tile (8-byte elements, 128-byte swizzle)
+__device__ __forceinline__ int tma_swz(int i) { return i ^ (((i >> 4) & 7) << 1); }
+
+// CTAs that gave up waiting for a tile copy (one counter per translation
+// unit, which is its own device module; read and cleared by qc_kernel_timeouts)
+static __device__ unsigned long long g_tma_timeouts;
+constexpr unsigned long long kTmaWaitNs = 2000000000ull;  // 2 s: far above any tile copy
+
+// Shared-memory carve-out, from the 1024-byte aligned base: tile buffers
+// [stages][NS][2^12] float2, one mbarrier per stage, staged coefficients,
+// per-warp gradient sums, deferred companion sums, backward pre-diagonal
+// marginals and running sums, phase block.
+struct TmaSmem {
+  size_t buf, bar, sco, sred, sdef, smarg, smacc, fph, end;
+};
+__host__ __device__ inline TmaSmem tma_smem_layout(const TilePass& P, int ns) {
+  TmaSmem L;
+  L.buf = 0;
+  L.bar = L.buf + (size_t)P.nstage * ns * ((size_t)1 << kTmaT) * 8;
+  L.sco = tsm_align16(L.bar + 8 * (size_t)P.nstage);
+  L.sred = tsm_align16(L.sco + (size_t)P.ncoef * 4);
+  L.sdef = tsm_align16(L.sred + (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double));
+  L.smarg = tsm_align16(L.sdef + (ns == 2 && P.defer ? (size_t)P.ncomp * kThreads * 4 : 0));
+  const bool pre = ns == 2 && P.pre;
+  L.smacc = tsm_align16(L.smarg + (pre ? (size_t)kWarps * (P.n + 1) * sizeof(double) : 0));
+  L.fph = tsm_align16(L.smacc + (pre ? (size_t)kPreAcc * kThreads * 4 : 0));
+  const size_t nfph = ns == 1 ? (P.post ? 1 : 0) : (pre ? 1 : 0);
+  L.end = tsm_align16(L.fph + nfph * kFphBytes(4));
+  return L;
+}
+// dynamic shared memory of a launch: the carve-out plus alignment slack
+__host__ __device__ inline size_t tma_smem_bytes(const TilePass& P, int ns) {
+  return tma_smem_layout(P, ns).end + 1024;
+}
+
+constexpr int tma_minb(int ns, int kind) { return (ns == 1 && kind == 1) ? 3 : 2; }
+
+// The op on register bit I of a round, if any: round r's ops are numbered
+// from rop[r] in increasing bit order (the planner sorts them), every op of a
+// pass stages the same number of coefficients (nco) and has the same
+// gradient count and generator kinds, so the op's index and coefficient
+// block follow from the round's presence mask without per-op lookups.
+template <int NS, int RB, int KIND, int I, bool COMP>
+__device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, float2* v0,
+                                        float2* v1, const float* sco, float* acc) {
+  using R = float;
+  if (KIND == 2 && I + 1 >= RB) return;
+  if (!((rmask >> I) & 1u)) return;
+  const int k = k0 + __popc(rmask & ((1u << I) - 1u));
+  const R* mc = sco + k * nco;
+  if (NS == 1) {
+    if (KIND == 2) ap2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, mc);
+    else ap1<R, RB, I>(v0, mc, KIND == 1);
+  } else {
+    if (KIND == 2) bw2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, v1, mc, np, acc);
+    else bw1<R, RB, I, COMP>(v0, v1, mc, KIND == 1, np, gk, ck, acc);
+  }
+}
+
+// NS = 1 forward, 2 backward.  PRE: backward 1 / 2 = undo a diagonal layer
+// (identity / ring z map) in round 0 (contiguous pass, round 0 on bits 0..3);
+// forward 2 / 3 = a following diagonal's phase in the last round (contiguous
+// pass, last round on bits 8..11).
+// COMP: the pass also takes companion gradients (a folded preceding RX / RY
+// layer); without them that code is compiled out.
+template <int NS, int RB, int KIND, int PRE, bool COMP>
+__global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
+    k_tile_tma(const __grid_constant__ TilePass P, const __grid_constant__ CUtensorMap tm0,
+               const __grid_constant__ CUtensorMap tm1, const float* __restrict__ coef, float2* dst0,
+               float2* dst1, double* __restrict__ part, int cps) {
+  using R = float;
+  using C = float2;
+  constexpr int t = kTmaT;
+  constexpr int T = 1 << t;
+  extern __shared__ unsigned char smraw_tma[];
+  const unsigned raw_sa = smem_u32(smraw_tma);
+  unsigned char* sm = smraw_tma + (((raw_sa + 1023u) & ~1023u) - raw_sa);
+  const TmaSmem lay = tma_smem_layout(P, NS);
+  C* buf = reinterpret_cast<C*>(sm + lay.buf);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm + lay.bar);
+  R* sco = reinterpret_cast<R*>(sm + lay.sco);
+  double* sred = reinterpret_cast<double*>(sm + lay.sred);
+  R* sdef = reinterpret_cast<R*>(sm + lay.sdef);
+  double* smarg = reinterpret_cast<double*>(sm + lay.smarg);
+  R* macc = reinterpret_cast<R*>(sm + lay.smacc) + threadIdx.x;
+  unsigned char* fph = sm + lay.fph;
+
+  const int n = P.n, c = P.c, h0 = P.h0;
+  const int m = t - c, gap = h0 - c;
+  const int nst = P.nstage;
+  const long long tps = 1LL << (n - t);
+  const int b = blockIdx.x / cps;
+  const int r0 = blockIdx.x % cps;
+  const int cmask = (1 << c) - 1;
+  const long long sb = (long long)b << n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  C* d0b = dst0 + sb;
+  C* d1b = NS == 2 ? dst1 + sb : nullptr;
+  auto tile_base = [&](long long f) -> int {
+    return (int)(((f & ((1LL << gap) - 1)) << c) | ((f >> gap) << (h0 + m)));
+  };
+  auto elem_off = [&](int i) -> int { return (i & cmask) | ((i >> c) << h0); };
+
+  for (int k = 0; k < P.nops; ++k) {
+    const TileOp& o = P.ops[k];
+    const R* s = coef + o.coef + (long long)b * o.bstride;
+    for (int i = threadIdx.x; i < o.nco; i += kThreads) sco[o.soff + i] = s[i];
+  }
+  // per-pass op data (uniform over the pass's ops) and the presence mask of
+  // every round's register bits (4 bits per round)
+  const int op_nco = P.ops[0].nco, op_np = P.ops[0].np, op_gk = P.ops[0].gk, op_ck = COMP ? P.ops[0].ck : 0;
+  unsigned rmask_all = 0;
+  for (int r = 0; r < P.nrounds; ++r)
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+      if (P.rbit[r][i] >= 0) rmask_all |= 1u << (4 * r + i);
+  if (NS == 2) {
+    for (int i = threadIdx.x; i < kWarps * P.nslots; i += kThreads) sred[i] = 0;
+    if (P.defer)
+      for (int s = 0; s < P.ncomp; ++s) sdef[s * kThreads + threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    mbar_init_fence();
+  }
+
+  constexpr int kAR = RB == 4 ? 3 : 4;
+  R acct[kAR][4];
+#pragma unroll
+  for (int r = 0; r < kAR; ++r)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acct[r][i] = 0;
+
+  // backward pre-diagonal (round 0 holds bits 0..3 of group g = tid: local
+  // indices g << 4 | a): the element z bits are 0..3 (and n - 1 for the ring
+  // map, through index bit 0); bits whose z depends on the tile are warp
+  // uniform (index bits >= 9 only); the others depend on the thread alone
+  constexpr bool pre_b = NS == 2 && PRE >= 1;
+  constexpr int zmc = PRE == 2 ? Z_RINGXOR : Z_IDENT;
+  const R* ptabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
+  int zT = 0, fmask = 0;
+  bool lane_f = false;
+  if (pre_b) {
+    fph_setup<R>(fph, ptabs, P.pre_tb, zmc, n, t, c, h0, 0, 4);
+    const int sem = reinterpret_cast<const FwdPhaseMeta*>(fph)->semask;
+    zT = ztrans32(threadIdx.x << 4, n, zmc);
+    for (int q = t; q < n; ++q) fmask |= ztrans32(1 << q, n, zmc);
+    fmask &= ~sem;
+    lane_f = ((fmask >> lane) & 1) != 0;
+    for (int j = 0; j < kPreAcc; ++j) macc[j * kThreads] = 0;
+  }
+  // forward post phase in the last round (bits 8..11 of a contiguous pass)
+  const R* fpost_tabs = coef + P.post_coef + (long long)b * P.post_bstride;
+  const int rlast = P.nrounds - 1;
+  if (NS == 1 && PRE >= 2 && P.post)
+    fph_setup<R>(fph, fpost_tabs, P.post_tb, P.post_zmode, n, t, c, h0, P.rlo[rlast], RB);
+  const bool fpost_ok = NS == 1 && PRE >= 2 && P.post && reinterpret_cast<const FwdPhaseMeta*>(fph)->ok;
+  // the last round stores straight from registers unless the pass scatters
+  // (or stores nothing); the single-buffer backward then starts the next
+  // tile's copy as soon as every thread holds its last-round elements
+  const bool dstore = P.store && !P.scatter;
+  const bool early = NS == 2 && nst == 1 && dstore && RB == 4;
+  __syncthreads();
+
+  unsigned pending = 0, phase = 0;
+  auto issue = [&](long long f, int s) {  // thread 0
+    const int c2 = (int)(f & ((1LL << gap) - 1));
+    const int c4 = (int)(((long long)b << (n - h0 - m)) | (f >> gap));
+    const unsigned bar = smem_u32(&bars[s]);
+    mbar_expect_tx(bar, (unsigned)(NS * T * sizeof(C)));
+    tma_load_5d(smem_u32(buf + (size_t)s * NS * T), &tm0, 0, 0, c2, 0, c4, bar);
+    if (NS == 2) tma_load_5d(smem_u32(buf + (size_t)s * NS * T + T), &tm1, 0, 0, c2, 0, c4, bar);
+    pending |= 1u << s;
+  };
+  long long f = r0;
+  int slot = 0;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < nst; ++j)
+      if (f + (long long)j * cps < tps) issue(f + (long long)j * cps, j);
+
+  for (; f < tps; f += cps) {
+    const bool ok = mbar_wait_bounded(smem_u32(&bars[slot]), (phase >> slot) & 1u, kTmaWaitNs);
+    phase ^= 1u << slot;
+    pending &= ~(1u << slot);
+    if (__syncthreads_or(!ok)) {
+      // a copy did not complete in time: record it, wait (bounded) for the
+      // copies this CTA still has in flight, and leave
+      if (threadIdx.x == 0) {
+        atomicAdd(&g_tma_timeouts, 1ull);
+        for (int s = 0; s < nst; ++s)
+          if (((pending >> s) & 1u) || s == slot)
+            mbar_wait_bounded(smem_u32(&bars[s]), ((phase ^ (s == slot ? 1u << s : 0u)) >> s) & 1u, kTmaWaitNs);
+      }
+      __syncthreads();
+      return;
+    }
+    C* S0 = buf + (size_t)slot * NS * T;
+    C* S1 = S0 + T;
+    const int kb = tile_base(f);
+
+#pragma unroll 1
+    for (int r = 0; r < P.nrounds; ++r) {
+      const int lo = P.rlo[r];
+      const bool last = r == rlast;
+      const unsigned rmask = (rmask_all >> (4 * r)) & 15u;
+      const int k0 = P.rop[r];
+      R acc[RB * 3];
+#pragma unroll
+      for (int i = 0; i < RB * 3; ++i) acc[i] = 0;
+      int basis[RB], eo[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        basis[j] = tma_swz(1 << (lo + j));
+        eo[j] = elem_off(1 << (lo + j));  // global offset of register bit j (disjoint bits)
+      }
+      for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
+        const int li = (g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB));
+        const int pb = tma_swz(li);
+        C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
+        if (lo == 0) {
+          // amplitude pairs (bit 0) as 16-byte accesses; the swizzle keeps bit 0
+#pragma unroll
+          for (int a = 0; a < (1 << RB); a += 2) {
+            int ad = pb;
+#pragma unroll
+            for (int j = 1; j < RB; ++j)
+              if (a & (1 << j)) ad ^= basis[j];
+            const float4 q = *reinterpret_cast<const float4*>(&S0[ad]);
+            v0[a] = make_float2(q.x, q.y);
+            v0[a + 1] = make_float2(q.z, q.w);
+            if constexpr (NS == 2) {
+              const float4 u = *reinterpret_cast<const float4*>(&S1[ad]);
+              v1[a] = make_float2(u.x, u.y);
+              v1[a + 1] = make_float2(u.z, u.w);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) {
+            int ad = pb;
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+              if (a & (1 << j)) ad ^= basis[j];
+            v0[a] = S0[ad];
+            if constexpr (NS == 2) v1[a] = S1[ad];
+          }
+        }
+        if constexpr (pre_b) {
+          if (r == 0) {
+            // undo the diagonal layer on psi and lambda: element a has z =
+            // z0 ^ z(a) with the compile-time pattern a ^ (a >> 1) (| a_0 at
+            // z bit n - 1, pattern bit 4) for the ring map, a for the identity;
+            // w = Im(conj(lambda) psi) is unchanged by the phase
+            constexpr int nse = PRE == 2 ? 5 : 4;
+            const int z0 = ztrans32(kb | li, n, zmc);
+            const int semask = PRE == 2 ? (15 | (1 << (n - 1))) : 15;
+            const int z0se = (z0 & 15) | (PRE == 2 ? ((z0 >> (n - 1)) & 1) << 4 : 0);
+            const C p0 = diag_phase32<R>(ptabs, P.pre_tb, z0 & ~semask);
+            const C* ratio = reinterpret_cast<const C*>(fph + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
+            R Wt = 0, Ase[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < (1 << RB); ++a) {
+              const int pat = PRE == 2 ? ((a ^ (a >> 1)) | ((a & 1) << 4)) : a;
+              const C ph = cmul<R>(p0, ratio[z0se ^ pat]);
+              const R w = im_cdot<R>(v1[a], v0[a]);
+              v0[a] = cmulc<R>(ph, v0[a]);
+              v1[a] = cmulc<R>(ph, v1[a]);
+              Wt += w;
+#pragma unroll
+              for (int j = 0; j < nse; ++j)
+                if ((pat >> j) & 1) Ase[j] += w;
+            }
+            if (P.pre_grad) {
+#pragma unroll
+              for (int j = 0; j < nse; ++j)
+                if ((z0se >> j) & 1) Ase[j] = Wt - Ase[j];
+              macc[0] += Wt;
+#pragma unroll
+              for (int j = 0; j < nse; ++j) macc[(1 + j) * kThreads] += Ase[j];
+              const R sw = warp_sum_r<R>(Wt);
+              if (lane_f && ((z0 >> lane) & 1)) macc[11 * kThreads] += sw;
+            }
+          }
+        }
+        if (early && last) {
+          // every thread holds its elements of the last round: the buffer is
+          // free for the next tile's copy
+          __syncthreads();
+          if (threadIdx.x == 0 && f + cps < tps) issue(f + cps, 0);
+        }
+        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+        if (RB > 1)
+          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+        if (RB > 2)
+          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+        if (RB > 3)
+          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+        if (NS == 1 && PRE >= 2 && fpost_ok && last) {
+          // group g = tid holds local indices g | a << 8 of a contiguous pass:
+          // z = z0 ^ z(a << 8) with the compile-time pattern a ^ (a << 1)
+          // (ring) or a (identity) over z bits zlo .. 11
+          constexpr int zlo = PRE == 2 ? 7 : 8, nse = 12 - zlo;
+          constexpr int semask = ((1 << nse) - 1) << zlo;
+          const int z0 = ztrans32(kb | li, n, PRE == 2 ? Z_RINGXOR : Z_IDENT);
+          const int z0se = (z0 >> zlo) & ((1 << nse) - 1);
+          const C p0 = diag_phase32<R>(fpost_tabs, P.post_tb, z0 & ~semask);
+          const C* ratio = reinterpret_cast<const C*>(fph + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) {
+            const int pat = PRE == 2 ? (a ^ (a << 1)) : a;
+            v0[a] = cmul<R>(cmul<R>(p0, ratio[z0se ^ pat]), v0[a]);
+          }
+        }
+        if (last && dstore) {
+          // element a sits at gb + (sum of eo[j] over the set bits j of a)
+          const int gb = kb | elem_off(li);
+          C* o0 = d0b + gb;
+          C* o1 = NS == 2 ? d1b + gb : nullptr;
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) {
+            int go = 0;
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+              if (a & (1 << j)) go += eo[j];
+            o0[go] = v0[a];
+            if constexpr (NS == 2) o1[go] = v1[a];
+          }
+        } else if (lo == 0) {
+#pragma unroll
+          for (int a = 0; a < (1 << RB); a += 2) {
+            int ad = pb;
+#pragma unroll
+            for (int j = 1; j < RB; ++j)
+              if (a & (1 << j)) ad ^= basis[j];
+            *reinterpret_cast<float4*>(&S0[ad]) = make_float4(v0[a].x, v0[a].y, v0[a + 1].x, v0[a + 1].y);
+            if constexpr (NS == 2)
+              *reinterpret_cast<float4*>(&S1[ad]) = make_float4(v1[a].x, v1[a].y, v1[a + 1].x, v1[a + 1].y);
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < (1 << RB); ++a) {
+            int ad = pb;
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+              if (a & (1 << j)) ad ^= basis[j];
+            S0[ad] = v0[a];
+            if constexpr (NS == 2) S1[ad] = v1[a];
+          }
+        }
+      }
+      if (NS == 2) {
+        if (P.defer) {
+#pragma unroll
+          for (int rr = 0; rr < kAR; ++rr)
+            if (rr == r) {
+#pragma unroll
+              for (int i = 0; i < (RB < 4 ? RB : 4); ++i) acct[rr][i] += acc[i * 3];
+            }
+          if (P.ncomp) {
+#pragma unroll
+            for (int i = 0; i < (RB < 4 ? RB : 4); ++i) {
+              const int cs = P.rcslot[r][i];
+              if (cs >= 0) sdef[(cs - P.nslots + P.ncomp) * kThreads + threadIdx.x] += acc[i * 3 + 1];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            const int k = P.rbit[r][i];
+            if (k < 0) continue;
+            const TileOp& o = P.ops[k];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < o.np) {
+                const double v = warp_sum((double)acc[i * 3 + q]);
+                if (lane == 0) sred[warp * P.nslots + o.slot + q] += v;
+              }
+            if (o.ck) {
+              const double v = warp_sum((double)acc[i * 3 + 1]);
+              if (lane == 0) sred[warp * P.nslots + o.cslot] += v;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    if (P.store && P.scatter) {
+      // backward scatter through the CNOT ring's inverse map f^-1, in 16-byte
+      // pairs: f^-1(k ^ 1 ^ 2^(n-1)) = f^-1(k) ^ 1, and this top pass holds
+      // index bit 0 (local 0) and bit n-1 (local t-1)
+      for (int i = threadIdx.x; i < (T >> 1); i += kThreads) {
+        const int d = ring_finv32(kb | elem_off(i), n);
+        const int pa = tma_swz(i), pp = tma_swz(i ^ 1 ^ (T >> 1));
+        const C qa = S0[pa], qb = S0[pp];
+        const bool odd = d & 1;
+        const int dd = d & ~1;
+        *reinterpret_cast<float4*>(&d0b[dd]) = odd ? make_float4(qb.x, qb.y, qa.x, qa.y)
+                                                   : make_float4(qa.x, qa.y, qb.x, qb.y);
+        if constexpr (NS == 2) {
+          const C ua = S1[pa], ub = S1[pp];
+          *reinterpret_cast<float4*>(&d1b[dd]) = odd ? make_float4(ub.x, ub.y, ua.x, ua.y)
+                                                     : make_float4(ua.x, ua.y, ub.x, ub.y);
+        }
+      }
+    }
+    __syncthreads();  // the stage is free
+    const long long fn = f + (long long)nst * cps;
+    if (!early && threadIdx.x == 0 && fn < tps) issue(fn, slot);
+    slot = slot + 1 == nst ? 0 : slot + 1;
+  }
+
+  if (NS == 2 && P.defer) {
+#pragma unroll
+    for (int r = 0; r < kAR; ++r)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int sl = P.rslot[r][i];
+        if (sl >= 0) {
+          const double v = warp_sum((double)acct[r][i]);
+          if (lane == 0) sred[warp * P.nslots + sl] += v;
+        }
+      }
+    for (int s = 0; s < P.ncomp; ++s) {
+      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
+      if (lane == 0) sred[warp * P.nslots + P.nslots - P.ncomp + s] += v;
+    }
+  }
+  if (NS == 2 && P.nslots > 0) {
+    __syncthreads();
+    for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
+      double v = 0;
+      for (int w = 0; w < kWarps; ++w) v += sred[w * P.nslots + s];
+      part[(long long)s * gridDim.x + blockIdx.x] = v;
+    }
+  }
+  if (pre_b && P.pre_grad) {
+    // u_p = sum over the thread's elements of w * z_p: element bits exactly,
+    // tile-dependent (warp-uniform) bits from lane p's column after the warp
+    // sums, the rest from the thread's total and its tile-independent z bits
+    const FwdPhaseMeta* pm = reinterpret_cast<const FwdPhaseMeta*>(fph);
+    const R mW = macc[0], mF = macc[11 * kThreads];
+    const double wsum = warp_sum((double)mW);
+    if (lane == 0) smarg[warp * (n + 1)] = wsum;
+    for (int p = 0; p < n; ++p) {
+      R u;
+      int js = -1;
+      for (int j = 0; j < pm->nse; ++j)
+        if (pm->sepos[j] == p) js = j;
+      if (js >= 0) u = macc[(1 + js) * kThreads];
+      else if ((fmask >> p) & 1) u = 0;
+      else u = ((zT >> p) & 1) ? mW : (R)0;
+      double v = warp_sum((double)u);
+      v += (double)__shfl_sync(0xffffffffu, mF, p);
+      if (lane == 0) smarg[warp * (n + 1) + 1 + p] = v;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v <= n; v += kThreads) {
+      double s = 0;
+      for (int w = 0; w < kWarps; ++w) s += smarg[w * (n + 1) + v];
+      part[P.pre_moff + (long long)v * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+}  // namespace qc

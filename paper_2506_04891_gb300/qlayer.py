@@ -36,6 +36,7 @@ EXPORTED = [
     "qc_workspace_bytes", "qc_forward", "qc_expect_z", "qc_expect_z_noalloc", "qc_backward",
     "qc_staging_bytes",
     "qc_step_host", "qc_wait", "qc_last_error", "qc_launch_count", "qc_alloc_count",
+    "qc_kernel_timeouts",
     "qc_profile_enable",
     "qc_profile_summary", "qc_describe_plan", "qc_fma_peak",
 ]
@@ -51,10 +52,10 @@ class qc_options(ctypes.Structure):
                 ("fuse", ctypes.c_int32), ("tile_bits_fwd", ctypes.c_int32),
                 ("tile_bits_bwd", ctypes.c_int32), ("reg_bits_fwd", ctypes.c_int32),
                 ("reg_bits_bwd", ctypes.c_int32), ("stages_fwd", ctypes.c_int32),
-                ("stages_bwd", ctypes.c_int32)]
+                ("stages_bwd", ctypes.c_int32), ("tma", ctypes.c_int32)]
 
 TUNING_FIELDS = ("tile_bits_fwd", "tile_bits_bwd", "reg_bits_fwd", "reg_bits_bwd", "stages_fwd",
-                 "stages_bwd")
+                 "stages_bwd", "tma")
 
 
 class QCError(RuntimeError):
@@ -91,6 +92,7 @@ def _load():
         "qc_describe_plan": (I, [P, I, ctypes.c_char_p, S]),
         "qc_launch_count": (ctypes.c_ulonglong, []),
         "qc_alloc_count": (ctypes.c_ulonglong, []),
+        "qc_kernel_timeouts": (I, [ctypes.POINTER(ctypes.c_ulonglong)]),
         "qc_profile_enable": (I, [I]),
         "qc_profile_summary": (I, [ctypes.c_char_p, S]),
         "qc_fma_peak": (I, [I, ctypes.POINTER(ctypes.c_double)]),
@@ -200,6 +202,13 @@ def qc_launch_count() -> int:
 
 def qc_alloc_count() -> int:
     return _lib.qc_alloc_count()
+
+
+def qc_kernel_timeouts() -> int:
+    """CTAs that gave up waiting for a TMA tile copy since the last call (synchronises)."""
+    v = ctypes.c_ulonglong()
+    _check(_lib.qc_kernel_timeouts(ctypes.byref(v)))
+    return v.value
 
 
 def qc_profile_enable(on: bool):
