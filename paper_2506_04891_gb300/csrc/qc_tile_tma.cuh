@@ -74,6 +74,14 @@ __device__ __forceinline__ void tma_load_5d(unsigned dst, const CUtensorMap* tm,
       : "memory");
 }
 
+// the same box fetched into L2 only (no completion to wait for)
+__device__ __forceinline__ void tma_prefetch_5d(const CUtensorMap* tm, int c0, int c1, int c2, int c3, int c4) {
+  asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];\n" ::"l"(
+                   reinterpret_cast<unsigned long long>(tm)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+               : "memory");
+}
+
 // element i of a TMA tile (8-byte elements, 128-byte swizzle)
 __device__ __forceinline__ int tma_swz(int i) { return i ^ (((i >> 4) & 7) << 1); }
 
@@ -111,19 +119,115 @@ __host__ __device__ inline size_t tma_smem_bytes(const TilePass& P, int ns) {
 
 constexpr int tma_minb(int ns, int kind) { return (ns == 1 && kind == 1) ? 3 : 2; }
 
+// Real single-qubit gates (RY) in scaled form (the square-root-free "fast
+// Givens" rotation, Gentleman 1973): with c = M00 = M11, the rotation of a
+// pair is c * (x0 + tau0 x1, x1 + tau1 x0), so a gate costs one packed FMA
+// per output when the factor c is carried along instead of applied.  Every
+// gate of a pass but the last runs in this form (its record holds tau0,
+// tau1 and the gradient factor gf); the product C of the omitted factors
+// multiplies the last gate's matrix, so the pass's outputs are exact.  Between
+// gates the held amplitudes of psi and lambda are the true ones divided by
+// the product of the factors so far, so a gate's gradient products carry that
+// product squared, which gf (the product squared, including the gate's own
+// factor) puts back.  The forward applies M, the backward M^T.
+template <int RB, int I>
+__device__ __forceinline__ void ap1t(float2* v, const float* m) {
+  float t0, t1, gf, unused;
+  ld4<float>(m, t0, t1, gf, unused);
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (1 << I))) {
+      const float2 x0 = v[a], x1 = v[a | (1 << I)];
+      v[a] = rfma<float>(t0, x1, x0);
+      v[a | (1 << I)] = rfma<float>(t1, x0, x1);
+    }
+}
+template <int RB, int I, bool MAYCK>
+__device__ __forceinline__ void bw1t(float2* p, float2* l, const float* m, int np, int ck_in, float* acc) {
+  using C = float2;
+  const int ck = MAYCK ? ck_in : 0;
+  float t0, t1, gf, unused;
+  ld4<float>(m, t0, t1, gf, unused);
+  C ga = make_float2(0, 0), gb = make_float2(0, 0), hc = make_float2(0, 0);
+  float hs = 0;
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (1 << I))) {
+      const int a1 = a | (1 << I);
+      const C x0 = p[a], x1 = p[a1];
+      const C y0 = rfma<float>(t0, x1, x0), y1 = rfma<float>(t1, x0, x1);
+      p[a] = y0;
+      p[a1] = y1;
+      const C u0 = l[a], u1 = l[a1];
+      const C w0 = rfma<float>(t0, u1, u0), w1 = rfma<float>(t1, u0, u1);
+      l[a] = w0;
+      l[a1] = w1;
+      // 2 Re <l|(-i/2 Y)|p> = Re(l1* p0) - Re(l0* p1)
+      ga = pfma<float>(w1, y0, ga);
+      gb = pfma<float>(w0, y1, gb);
+      if (ck == 1) {
+        // companion RX: Im(l0* p1 + l1* p0), packed as l * swap(p)
+        hc = pfma<float>(w0, make_float2(y1.y, y1.x), hc);
+        hc = pfma<float>(w1, make_float2(y0.y, y0.x), hc);
+      } else if (ck == 2) {
+        hs += pauli_grad<float>(2, w0, w1, y0, y1);
+      }
+    }
+  if (np) acc[I * 3] += gf * ((ga.x + ga.y) - (gb.x + gb.y));
+  if (ck == 1) acc[I * 3 + 1] += gf * (hc.x - hc.y);
+  else if (ck == 2) acc[I * 3 + 1] += gf * hs;
+}
+
+// Rewrites a real pass's staged records for the scaled form (one thread, per
+// CTA: the records are shared by the CTA's tiles).  Returns false, leaving the
+// records as they are, when a factor is small (|c| < 2^-10) or their product
+// would leave the normal range (< 2^-60); the pass then runs every gate in
+// full form.  FWD: records become (M01 / M00, M10 / M11, gf, 0), else
+// (M10 / M00, M01 / M11, gf, 0); the last op's record is multiplied by C.
+template <bool FWD>
+__device__ bool scale_real_records(float* sco, int nops, int nco) {
+  if (nops < 2 || nco != 4) return false;
+  float cacc = 1.f;
+  for (int k = 0; k + 1 < nops; ++k) {
+    const float* r = sco + 4 * k;
+    const float cc = r[0];
+    if (!(fabsf(cc) >= 0x1p-10f) || r[3] != cc) return false;
+    cacc *= cc;
+    if (!(fabsf(cacc) >= 0x1p-60f)) return false;
+  }
+  cacc = 1.f;
+  for (int k = 0; k + 1 < nops; ++k) {
+    float* r = sco + 4 * k;
+    const float m00 = r[0], m01 = r[1], m10 = r[2], m11 = r[3];
+    cacc *= m00;
+    r[0] = FWD ? m01 / m00 : m10 / m00;
+    r[1] = FWD ? m10 / m11 : m01 / m11;
+    r[2] = cacc * cacc;
+    r[3] = 0.f;
+  }
+  float* r = sco + 4 * (nops - 1);
+  for (int j = 0; j < 4; ++j) r[j] *= cacc;
+  return true;
+}
+
 // The op on register bit I of a round, if any: round r's ops are numbered
 // from rop[r] in increasing bit order (the planner sorts them), every op of a
 // pass stages the same number of coefficients (nco) and has the same
 // gradient count and generator kinds, so the op's index and coefficient
 // block follow from the round's presence mask without per-op lookups.
 template <int NS, int RB, int KIND, int I, bool COMP>
-__device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, float2* v0,
-                                        float2* v1, const float* sco, float* acc) {
+__device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, int kscaled,
+                                        float2* v0, float2* v1, const float* sco, float* acc) {
   using R = float;
   if (KIND == 2 && I + 1 >= RB) return;
   if (!((rmask >> I) & 1u)) return;
   const int k = k0 + __popc(rmask & ((1u << I) - 1u));
   const R* mc = sco + k * nco;
+  if (KIND == 1 && k < kscaled) {  // scaled form: every op before the last when the pass allows it
+    if (NS == 1) ap1t<RB, I>(v0, mc);
+    else bw1t<RB, I, COMP>(v0, v1, mc, np, ck, acc);
+    return;
+  }
   if (NS == 1) {
     if (KIND == 2) ap2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, mc);
     else ap1<R, RB, I>(v0, mc, KIND == 1);
@@ -236,7 +340,14 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   // tile's copy as soon as every thread holds its last-round elements
   const bool dstore = P.store && !P.scatter;
   const bool early = NS == 2 && nst == 1 && dstore && RB == 4;
+  // real passes: switch the records to the scaled form (ops below kscaled)
+  __shared__ int s_kscaled;
+  if (KIND == 1) {
+    __syncthreads();  // the records are staged
+    if (threadIdx.x == 0) s_kscaled = scale_real_records<NS == 1>(sco, P.nops, op_nco) ? P.nops - 1 : 0;
+  }
   __syncthreads();
+  const int kscaled = KIND == 1 ? s_kscaled : 0;
 
   unsigned pending = 0, phase = 0;
   auto issue = [&](long long f, int s) {  // thread 0
@@ -247,6 +358,14 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
     tma_load_5d(smem_u32(buf + (size_t)s * NS * T), &tm0, 0, 0, c2, 0, c4, bar);
     if (NS == 2) tma_load_5d(smem_u32(buf + (size_t)s * NS * T + T), &tm1, 0, 0, c2, 0, c4, bar);
     pending |= 1u << s;
+  };
+  // the tile after the ones in flight, pulled into L2 while this one is
+  // processed, so its copy into shared memory does not wait on DRAM
+  auto prefetch = [&](long long f) {  // thread 0
+    const int c2 = (int)(f & ((1LL << gap) - 1));
+    const int c4 = (int)(((long long)b << (n - h0 - m)) | (f >> gap));
+    tma_prefetch_5d(&tm0, 0, 0, c2, 0, c4);
+    if (NS == 2) tma_prefetch_5d(&tm1, 0, 0, c2, 0, c4);
   };
   long long f = r0;
   int slot = 0;
@@ -273,6 +392,7 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
     C* S0 = buf + (size_t)slot * NS * T;
     C* S1 = S0 + T;
     const int kb = tile_base(f);
+    if (threadIdx.x == 0 && f + (long long)nst * cps < tps) prefetch(f + (long long)nst * cps);
 
 #pragma unroll 1
     for (int r = 0; r < P.nrounds; ++r) {
@@ -364,13 +484,16 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
           __syncthreads();
           if (threadIdx.x == 0 && f + cps < tps) issue(f + cps, 0);
         }
-        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1, sco, acc);
         if (RB > 1)
-          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1,
+                                                       sco, acc);
         if (RB > 2)
-          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1,
+                                                       sco, acc);
         if (RB > 3)
-          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, v0, v1, sco, acc);
+          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1,
+                                                       sco, acc);
         if (NS == 1 && PRE >= 2 && fpost_ok && last) {
           // group g = tid holds local indices g | a << 8 of a contiguous pass:
           // z = z0 ^ z(a << 8) with the compile-time pattern a ^ (a << 1)

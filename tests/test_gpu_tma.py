@@ -79,3 +79,32 @@ def test_tma_plan_covers_the_zz26_backward_and_strided_forward():
     bwd = [l for l in plan if l.startswith("B ") and "TILE" in l]
     assert all(" tma=1" in l for l in bwd)
     assert sum(" tma=1" in l for l in fwd) == 22  # the ring-gathering passes keep per-thread copies
+
+
+@pytest.mark.parametrize("case", ["near_cutoff", "exact_pi"])
+def test_scaled_rotations_near_singular_angles(case):
+    """Real (RY) passes run in scaled form (one packed FMA per output, the
+    cosines carried as a factor); a pass falls back to the full form when a
+    cosine is below 2^-10.  Angles with cos(theta/2) just above the cutoff
+    (large tangents) and exactly at theta = pi (cosine ~ 6e-17: fallback)
+    must both match the oracle."""
+    n, B = 15, 2
+    layers = W.zz_circuit(n, 3)
+    x, theta, _ = W.draw_inputs(n, layers, B, seed=5)
+    g = W.draw_upstream(B, n, seed=5)
+    ry = [off for kind, src, off, _ in layers if kind == "RY"]
+    if case == "near_cutoff":
+        c = 1.5e-3  # tangent ~ 670
+        for k, off in enumerate(ry):
+            theta[off + 3 * k] = 2 * np.arccos(c)
+            theta[off + 11] = 2 * np.arccos(-c)
+    else:
+        theta[ry[0] + 2] = np.pi
+        theta[ry[1] + 14] = np.pi
+    a = _run(n, layers, x, theta, g, 1)
+    ez, dth, _, dx = O.adjoint(n, layers, x, theta, g)
+    psi = O.forward(n, layers, x, theta)
+    assert rel(a["psi"], psi) < 1e-5
+    check("c64", "ez", a["ez"], ez)
+    check("c64", "dx", a["dx"][:, : dx.shape[1]], dx)
+    check("c64", "dtheta", a["dth"], dth, batch_sum=B)
