@@ -155,12 +155,19 @@ typedef struct {
    * elsewhere; 0 = per-thread copies everywhere.  With the default 1, the
    * process environment variable QC_TMA=0 (read at qc_create) turns it off. */
   int32_t tma;
+  /* Experiment, default 0: 1 runs every eligible forward pass of a real
+   * single-qubit layer (one gate on each of the 7 high bits of a 2^12 tile
+   * with 32 contiguous amplitudes, nothing fused) as one 128 x 128 dense
+   * block on the tensor cores (tcgen05.mma kind::tf32, 3xTF32 split, FP32
+   * accuracy).  On GB300 it is slower than the register rounds of the tile
+   * pass, which stay the default. */
+  int32_t tc_dense;
 } qc_options;
 
 /* Version of this ABI (major * 100 + minor). */
 QC_API int qc_version(void);
 
-/* Fills *opt with the defaults {-1, 0, 1, 0, 0, 0, 0, 0, 0, 1}. */
+/* Fills *opt with the defaults {-1, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0}. */
 QC_API void qc_default_options(qc_options* opt);
 
 /* Validates a layer list and builds a circuit for n qubits (1 <= n <= 30).

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libqlayer.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["qc_tile_bwd.cu", "qc_tile_fwd.cu", "qc_tile_tma_bwd.cu", "qc_tile_tma_fwd.cu", "qc_kernels.cu",
+SOURCES = ["qc_tile_bwd.cu", "qc_tile_fwd.cu", "qc_tile_tma_bwd.cu", "qc_tile_tma_fwd.cu", "qc_tile_tc.cu", "qc_kernels.cu",
            "qc_api.cu", "qc_noalloc.cu", "qc_peaks.cu"]
 # the kernel files compile once per precision (QC_INST_R = 4 float, 8 double),
 # so the two halves build in parallel

@@ -107,6 +107,7 @@ struct Step {
   int post_tb = 0, post_zmode = 0;
   int laminit = 0;      // backward RING: lambda formed from psi (first backward step)
   int tma = 0;          // TILE: the TMA-staged kernel runs this pass
+  int tc = 0;           // TILE: the tensor-core dense block runs this pass (experiment)
 };
 
 struct OutMap {
@@ -1136,7 +1137,10 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
   P->unplaced = g_plan_unplaced;
   for (auto* v : {&p.fwd, &p.bwd})
     for (Step& st : *v)
-      if (st.type == ST_TILE && tma_pass_ok(c, st)) {
+      if (st.type == ST_TILE && c->dtype == QC_C64 && c->opt.tc_dense == 1 && tile_tc_ok(st.tp, st.ns)) {
+        st.tc = 1;  // one 192 KB CTA per SM
+        st.cps = tile_cps(batch, c->n, st.tp.t, 1);
+      } else if (st.type == ST_TILE && tma_pass_ok(c, st)) {
         st.tma = 1;
         st.cps = tma_cps(c, batch, st);
       }
@@ -1227,7 +1231,9 @@ qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int 
       }
       case ST_TILE: {
         ProfScope ps(s.ns == 2 ? PC_TILE_B : PC_TILE_F, passb, st);
-        if (s.tma && sizeof(R) == 4)
+        if (s.tc && sizeof(R) == 4)
+          e = launch_tile_tc(s.tp, batch, s.cps, coef, buf(s.s0), buf(s.d0), st);
+        else if (s.tma && sizeof(R) == 4)
           e = s.ns == 1 ? launch_tile_tma_fwd(s.tp, s.rb, batch, s.cps, coef, buf(s.s0), buf(s.d0), buf(s.s1),
                                               buf(s.d1), part + s.part_off, st)
                         : launch_tile_tma_bwd(s.tp, s.rb, batch, s.cps, coef, buf(s.s0), buf(s.d0), buf(s.s1),
@@ -1398,6 +1404,7 @@ QC_API void qc_default_options(qc_options* opt) {
   opt->reg_bits_fwd = opt->reg_bits_bwd = 0;
   opt->stages_fwd = opt->stages_bwd = 0;
   opt->tma = 1;
+  opt->tc_dense = 0;
 }
 
 QC_API const char* qc_last_error(void) { return g_last_error.c_str(); }
@@ -1438,6 +1445,7 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
     if (o.stages_fwd < 0 || o.stages_fwd > 3 || o.stages_bwd < 0 || o.stages_bwd > 3)
       return fail(QC_ERR_INVALID, "options.stages_* (or QC_TILE_STAGES) must be in 0 .. 3");
     if (o.tma != 0 && o.tma != 1) return fail(QC_ERR_INVALID, "options.tma must be 0 or 1");
+    if (o.tc_dense != 0 && o.tc_dense != 1) return fail(QC_ERR_INVALID, "options.tc_dense must be 0 or 1");
   }
   auto c = std::make_unique<qc_circuit>();
   c->n = n;
@@ -1704,7 +1712,7 @@ QC_API qc_status qc_kernel_timeouts(unsigned long long* count) {
   count_alloc();
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-  *count = tma_take_timeouts_fwd() + tma_take_timeouts_bwd();
+  *count = tma_take_timeouts_fwd() + tma_take_timeouts_bwd() + tc_take_timeouts();
   return QC_OK;
 }
 
@@ -1763,9 +1771,9 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
         // contiguous pass's compile-time element patterns
         const int post = !st.tp.post ? 0
                          : (st.ns == 1 && st.rb == 4 && c->dtype == QC_C64 && fwd_post_contig(st.tp)) ? 2 : 1;
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d post=%d tma=%d src=%d dst=%d",
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d post=%d tma=%d tc=%d src=%d dst=%d",
                  tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nstage, st.tp.nrounds, st.tp.nops, st.tp.nslots,
-                 st.tp.store, st.tp.pre, post, st.tma, st.s0, st.d0);
+                 st.tp.store, st.tp.pre, post, st.tma, st.tc, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {
           snprintf(line, sizeof line, " [l=%d%s np=%d%s]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "",

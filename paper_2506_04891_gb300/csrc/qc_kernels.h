@@ -57,6 +57,11 @@ cudaError_t launch_tile_tma_fwd(const TilePass& P, int rb, int batch, int cps, c
 cudaError_t launch_tile_tma_bwd(const TilePass& P, int rb, int batch, int cps, const void* coef, const void* s0,
                                 void* d0, const void* s1, void* d1, double* part, cudaStream_t st);
 size_t tile_tma_smem_bytes(const TilePass& P, int ns);
+// tensor-core dense block of a forward real pass (qc_tile_tc.cu, experiment)
+bool tile_tc_ok(const TilePass& P, int ns);
+cudaError_t launch_tile_tc(const TilePass& P, int batch, int cps, const void* coef, const void* s0, void* d0,
+                           cudaStream_t st);
+unsigned long long tc_take_timeouts();
 unsigned long long tma_take_timeouts_fwd();
 unsigned long long tma_take_timeouts_bwd();
 template <class R>

@@ -52,10 +52,10 @@ class qc_options(ctypes.Structure):
                 ("fuse", ctypes.c_int32), ("tile_bits_fwd", ctypes.c_int32),
                 ("tile_bits_bwd", ctypes.c_int32), ("reg_bits_fwd", ctypes.c_int32),
                 ("reg_bits_bwd", ctypes.c_int32), ("stages_fwd", ctypes.c_int32),
-                ("stages_bwd", ctypes.c_int32), ("tma", ctypes.c_int32)]
+                ("stages_bwd", ctypes.c_int32), ("tma", ctypes.c_int32), ("tc_dense", ctypes.c_int32)]
 
 TUNING_FIELDS = ("tile_bits_fwd", "tile_bits_bwd", "reg_bits_fwd", "reg_bits_bwd", "stages_fwd",
-                 "stages_bwd", "tma")
+                 "stages_bwd", "tma", "tc_dense")
 
 
 class QCError(RuntimeError):

@@ -61,26 +61,38 @@ def make_requests(count: int, seed: int = 0, n_range=(8, 24), b_range=(1, 512)):
     return out
 
 
+ALIGN = 256  # every chunk's region in the device arena starts on a 256-byte boundary
+
+
+def _align(v: int) -> int:
+    return (v + ALIGN - 1) // ALIGN * ALIGN
+
+
 class Scheduler:
     """Admission by device footprint; no GPU needed.
 
     footprint(n, b) -> bytes a chunk of b samples of an n-qubit request holds on
-    the device while it runs.  ``slots`` bounds the chunks in flight.
+    the device while it runs.  The device memory is one arena of budget_bytes:
+    admitting a chunk reserves a contiguous region of it (first fit), which
+    the executor carves the chunk's buffers from, and releasing it frees the
+    region, so no chunk allocates device memory.  ``slots`` bounds the chunks
+    in flight.
     """
 
     def __init__(self, budget_bytes: int, slots: int, footprint):
-        self.budget = int(budget_bytes)
+        self.budget = int(budget_bytes) // ALIGN * ALIGN
         self.slots = int(slots)
         self.footprint = footprint
-        self.in_flight = {}   # chunk key -> bytes
+        self.in_flight = {}   # chunk key -> (offset, bytes)
         self.used = 0
+        self.free = [(0, self.budget)]  # sorted, disjoint (offset, bytes) gaps
 
     def max_chunk(self, n: int, batch: int) -> int:
         """Largest b <= batch whose footprint fits in the whole budget (0 if none)."""
         lo, hi = 0, batch
         while lo < hi:
             mid = (lo + hi + 1) // 2
-            if self.footprint(n, mid) <= self.budget:
+            if _align(self.footprint(n, mid)) <= self.budget:
                 lo = mid
             else:
                 hi = mid - 1
@@ -93,22 +105,58 @@ class Scheduler:
             raise ValueError(f"request {req.rid}: one sample of n={req.n} exceeds the HBM budget")
         return [(lo, min(lo + m, req.batch)) for lo in range(0, req.batch, m)]
 
-    def can_admit(self, n: int, b: int) -> bool:
-        return len(self.in_flight) < self.slots and self.used + self.footprint(n, b) <= self.budget
+    def _gap(self, need: int):
+        for i, (off, size) in enumerate(self.free):
+            if size >= need:
+                return i
+        return -1
 
-    def admit(self, key, n: int, b: int):
-        fp = self.footprint(n, b)
-        self.in_flight[key] = fp
-        self.used += fp
+    def can_admit(self, n: int, b: int) -> bool:
+        return len(self.in_flight) < self.slots and self._gap(_align(self.footprint(n, b))) >= 0
+
+    def admit(self, key, n: int, b: int) -> int:
+        """Reserves the chunk's region; returns its byte offset in the arena."""
+        need = _align(self.footprint(n, b))
+        i = self._gap(need)
+        if i < 0:
+            raise RuntimeError("admit without room (check can_admit first)")
+        off, size = self.free[i]
+        if size == need:
+            self.free.pop(i)
+        else:
+            self.free[i] = (off + need, size - need)
+        self.in_flight[key] = (off, need)
+        self.used += need
+        return off
 
     def release(self, key):
-        self.used -= self.in_flight.pop(key)
+        off, need = self.in_flight.pop(key)
+        self.used -= need
+        self.free.append((off, need))
+        self.free.sort()
+        merged = []
+        for o, sz in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + sz)
+            else:
+                merged.append((o, sz))
+        self.free = merged
 
 
 class GpuExecutor:
-    """Runs chunks on CUDA streams through the C ABI (asynchronous)."""
+    """Runs chunks on CUDA streams through the C ABI (asynchronous).
 
-    def __init__(self, slots: int, dtype: str = "c64", ckpt_every: int = 0):
+    All device memory of the chunks in flight is one arena, bound once to the
+    scheduler's budget (``bind``); a chunk's buffers (state, workspace, inputs
+    and outputs) are carved from the region the scheduler reserved for it.
+    Every stream slot has pinned host staging buffers, allocated once for
+    requests up to ``max_n`` qubits and ``max_b`` samples per chunk.  So
+    serving a request allocates neither device nor pinned memory, and the
+    compute calls themselves allocate nothing.
+    """
+
+    def __init__(self, slots: int, dtype: str = "c64", ckpt_every: int = 0, max_n: int = 24,
+                 max_b: int = 512):
         import torch
         from . import qlayer as Q
         self.torch = torch
@@ -118,6 +166,22 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.free_streams = list(range(slots))
         self.circuits = {}
+        self._layouts = {}
+        self.arena = None
+        nt = W.circuit_params(max_n, W.serving_circuit(max_n))[0]
+        big = max_b * max_n
+
+        def pin(k):
+            return torch.empty(k, dtype=torch.float64).pin_memory()
+        self.pinned = [dict(x=pin(big), theta=pin(nt), g=pin(big), ez=pin(big), dth=pin(nt), dx=pin(big))
+                       for _ in range(slots)]
+        self.max_n, self.max_b = max_n, max_b
+
+    def bind(self, budget_bytes: int):
+        """Allocates (or keeps, if large enough) the device arena."""
+        if self.arena is None or self.arena.numel() < budget_bytes:
+            self.arena = None
+            self.arena = self.torch.empty(int(budget_bytes), dtype=self.torch.uint8, device="cuda")
 
     def circuit(self, n: int):
         c = self.circuits.get(n)
@@ -126,51 +190,77 @@ class GpuExecutor:
             self.circuits[n] = c
         return c
 
-    def footprint(self, n: int, b: int) -> int:
+    def layout(self, n: int, b: int):
+        """Byte offsets of a chunk's buffers inside its region, and its size
+        (memoised: admission asks for it on every pass of the serving loop)."""
+        key = (n, b)
+        hit = self._layouts.get(key)
+        if hit is not None:
+            return hit
+        hit = self._layout(n, b)
+        self._layouts[key] = hit
+        return hit
+
+    def _layout(self, n: int, b: int):
         c = self.circuit(n)
         w = 8 if self.dtype == "c64" else 16
-        return (b << n) * w + c.workspace_bytes(b) + 16 * b * (3 * n + 2) + 8 * c.n_theta * 2
+        sizes = [("ws", max(c.workspace_bytes(b), 256)), ("psi", (b << n) * w),
+                 ("x", 8 * b * max(c.n_in, 1)), ("theta", 8 * max(c.n_theta, 1)), ("g", 8 * b * n),
+                 ("ez", 8 * b * n), ("dth", 8 * max(c.n_theta, 1)), ("dx", 8 * b * max(c.n_in, 1))]
+        off, out = 0, {}
+        for name, nb in sizes:
+            out[name] = (off, nb)
+            off = _align(off + nb)
+        return out, off
 
-    def launch(self, req: Request, lo: int, hi: int):
+    def footprint(self, n: int, b: int) -> int:
+        return self.layout(n, b)[1]
+
+    def launch(self, req: Request, lo: int, hi: int, offset: int = 0):
         torch, Q = self.torch, self.Q
+        if req.n > self.max_n or hi - lo > self.max_b:
+            raise ValueError(f"request {req.rid}: beyond the executor's staging sizes")
         si = self.free_streams.pop()
         st = self.streams[si]
+        pin = self.pinned[si]
         c = self.circuit(req.n)
-        b = hi - lo
+        b, n = hi - lo, req.n
+        lay, _ = self.layout(n, b)
+        base = self.arena.data_ptr() + offset
+
+        def dev(name, count):
+            o = offset + lay[name][0]
+            return self.arena[o: o + 8 * count].view(torch.float64)
+        nx, nt, ng = b * c.n_in, c.n_theta, b * n
+        pin["x"][:nx].numpy()[:] = req.x[lo:hi].reshape(-1)
+        pin["theta"][:nt].numpy()[:] = req.theta
+        pin["g"][:ng].numpy()[:] = req.g[lo:hi].reshape(-1)
         with torch.cuda.stream(st):
-            xh = torch.from_numpy(np.ascontiguousarray(req.x[lo:hi])).pin_memory()
-            th = torch.from_numpy(np.ascontiguousarray(req.theta)).pin_memory()
-            gh = torch.from_numpy(np.ascontiguousarray(req.g[lo:hi])).pin_memory()
-            x = xh.to("cuda", non_blocking=True)
-            t = th.to("cuda", non_blocking=True)
-            g = gh.to("cuda", non_blocking=True)
-            psi = torch.empty((b, 1 << req.n), dtype=c.state_dtype, device="cuda")
-            ez = torch.empty((b, req.n), dtype=torch.float64, device="cuda")
-            dth = torch.empty((c.n_theta,), dtype=torch.float64, device="cuda")
-            dx = torch.empty((b, c.n_in), dtype=torch.float64, device="cuda")
-            ws = torch.empty(max(c.workspace_bytes(b), 256), dtype=torch.uint8, device="cuda")
+            dev("x", nx).copy_(pin["x"][:nx], non_blocking=True)
+            dev("theta", nt).copy_(pin["theta"][:nt], non_blocking=True)
+            dev("g", ng).copy_(pin["g"][:ng], non_blocking=True)
+            p = {k: base + v[0] for k, v in lay.items()}
             h = st.cuda_stream
-            Q.qc_forward(c.handle, b, x.data_ptr(), t.data_ptr(), psi.data_ptr(), ez.data_ptr(),
-                         ws.data_ptr(), ws.numel(), h)
-            Q.qc_backward(c.handle, b, x.data_ptr(), t.data_ptr(), psi.data_ptr(), g.data_ptr(),
-                          dth.data_ptr(), dx.data_ptr(), ws.data_ptr(), ws.numel(), h)
-            out = (torch.empty(ez.shape, dtype=torch.float64).pin_memory(),
-                   torch.empty(dth.shape, dtype=torch.float64).pin_memory(),
-                   torch.empty(dx.shape, dtype=torch.float64).pin_memory())
-            out[0].copy_(ez, non_blocking=True)
-            out[1].copy_(dth, non_blocking=True)
-            out[2].copy_(dx, non_blocking=True)
+            Q.qc_forward(c.handle, b, p["x"], p["theta"], p["psi"], p["ez"], p["ws"], lay["ws"][1], h)
+            Q.qc_backward(c.handle, b, p["x"], p["theta"], p["psi"], p["g"], p["dth"], p["dx"], p["ws"],
+                          lay["ws"][1], h)
+            pin["ez"][:ng].copy_(dev("ez", ng), non_blocking=True)
+            pin["dth"][:nt].copy_(dev("dth", nt), non_blocking=True)
+            pin["dx"][:nx].copy_(dev("dx", nx), non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        # keep device buffers alive until the event completes
-        return dict(stream=si, event=ev, keep=(x, t, g, psi, ez, dth, dx, ws, xh, th, gh), out=out)
+        return dict(stream=si, event=ev, shape=(b, n, nt, c.n_in))
 
     def done(self, handle) -> bool:
         return handle["event"].query()
 
     def finish(self, handle):
+        b, n, nt, nin = handle["shape"]
+        pin = self.pinned[handle["stream"]]
+        ez = pin["ez"][: b * n].numpy().reshape(b, n).copy()
+        dth = pin["dth"][:nt].numpy().copy()
+        dx = pin["dx"][: b * nin].numpy().reshape(b, nin).copy()
         self.free_streams.append(handle["stream"])
-        ez, dth, dx = (a.numpy().copy() for a in handle["out"])
         handle.clear()
         return ez, dth, dx
 
@@ -188,6 +278,9 @@ class Server:
         reqs = list(requests)
         if arrivals is None:
             arrivals = [0.0] * len(reqs)
+        bind = getattr(self.ex, "bind", None)
+        if bind is not None:
+            bind(self.sch.budget)
         order = sorted(range(len(reqs)), key=lambda i: arrivals[i])
         t0 = clock()
         pending = []               # [req, [(lo, hi), ...]] in arrival order
@@ -234,11 +327,11 @@ class Server:
                 while chunks and self.sch.can_admit(req.n, chunks[0][1] - chunks[0][0]):
                     lo, hi = chunks.pop(0)
                     key = (req.rid, lo)
-                    self.sch.admit(key, req.n, hi - lo)
+                    off = self.sch.admit(key, req.n, hi - lo)
                     ent = partial[req.rid][0]
                     if math.isnan(ent.admitted):
                         ent.admitted = clock() - t0
-                    running.append((key, req, lo, hi, self.ex.launch(req, lo, hi)))
+                    running.append((key, req, lo, hi, self.ex.launch(req, lo, hi, off)))
             pending = [item for item in pending if item[1]]
             if not running and not pending and nxt < len(order):
                 time.sleep(max(0.0, min(0.001, arrivals[order[nxt]] - (clock() - t0))))
@@ -256,22 +349,42 @@ def poisson_arrivals(count: int, rate: float, seed: int = 0):
 
 
 def serve_benchmark(count: int = 10000, slots: int = 4, budget_frac: float = 0.8, seed: int = 0,
-                    n_range=(8, 24), b_range=(1, 512)):
-    """Closed-loop throughput, then a Poisson stream at 0.8 x that rate; returns stats."""
+                    n_range=(8, 24), b_range=(1, 512), closed_sample: int = 1000):
+    """The serving workload: a seeded stream of `count` requests (n and B
+    uniform in the ranges).  The closed-loop throughput is measured on the
+    stream's first `closed_sample` requests (all queued at once); the whole
+    stream then arrives as a Poisson process at 0.8 x that rate.  Returns the
+    statistics of both runs."""
     import torch
+    from . import qlayer as Q
     free, _ = torch.cuda.mem_get_info()
-    ex = GpuExecutor(slots)
-    sch = Scheduler(int(free * budget_frac), slots, ex.footprint)
-    reqs = make_requests(count, seed, n_range, b_range)
+    ex = GpuExecutor(slots, max_n=n_range[1], max_b=b_range[1])
+    budget = int(free * budget_frac)
+
+    def sched():
+        return Scheduler(budget, slots, ex.footprint)
     # warm up the kernels and plans of every qubit count
-    Server(ex, Scheduler(int(free * budget_frac), slots, ex.footprint)).run(
-        [r for r in make_requests(24, seed + 1, n_range, (1, 4))])
-    _, closed = Server(ex, sch).run(reqs)
+    Server(ex, sched()).run(make_requests(2 * (n_range[1] - n_range[0] + 1), seed + 1, n_range, (1, 4)))
+    torch.cuda.synchronize()
+    reqs = make_requests(count, seed, n_range, b_range)
+    sample = reqs[: min(closed_sample, count)]
+    a0 = Q.qc_alloc_count()
+    _, closed = Server(ex, sched()).run(sample)
     rate = 0.8 * closed["req_per_s"]
     reqs = make_requests(count, seed, n_range, b_range)
-    _, opened = Server(ex, Scheduler(int(free * budget_frac), slots, ex.footprint)).run(
-        reqs, poisson_arrivals(count, rate, seed))
-    return dict(closed_loop=closed, poisson=opened, arrival_rate=rate, slots=slots)
+    res, opened = Server(ex, sched()).run(reqs, poisson_arrivals(count, rate, seed))
+    allocs = Q.qc_alloc_count() - a0
+    lat = np.array([r.latency for r in res.values()])
+    wait = np.array([r.admitted - r.arrival for r in res.values()])
+    opened.update(p90_ms=float(np.percentile(lat, 90) * 1e3), mean_ms=float(lat.mean() * 1e3),
+                  admit_wait_p50_ms=float(np.percentile(wait, 50) * 1e3),
+                  admit_wait_p99_ms=float(np.percentile(wait, 99) * 1e3),
+                  split_requests=int(sum(r.chunks > 1 for r in res.values())),
+                  chunks=int(sum(r.chunks for r in res.values())))
+    return dict(closed_loop=closed, closed_loop_requests=len(sample), poisson=opened, arrival_rate=rate,
+                slots=slots, budget_bytes=budget, n_range=list(n_range), b_range=list(b_range),
+                library_device_allocs_during_runs=allocs,
+                request_evals=int(sum(r.batch for r in reqs)))
 
 
 if __name__ == "__main__":
@@ -282,5 +395,7 @@ if __name__ == "__main__":
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--nmax", type=int, default=24)
     ap.add_argument("--bmax", type=int, default=512)
+    ap.add_argument("--closed-sample", type=int, default=1000)
     a = ap.parse_args()
-    print(json.dumps(serve_benchmark(a.requests, a.slots, n_range=(8, a.nmax), b_range=(1, a.bmax))))
+    print(json.dumps(serve_benchmark(a.requests, a.slots, n_range=(8, a.nmax), b_range=(1, a.bmax),
+                                     closed_sample=a.closed_sample)))
