@@ -160,7 +160,8 @@ typedef struct {
    * with 32 contiguous amplitudes, nothing fused) as one 128 x 128 dense
    * block on the tensor cores (tcgen05.mma kind::tf32, 3xTF32 split, FP32
    * accuracy).  On GB300 it is slower than the register rounds of the tile
-   * pass, which stay the default. */
+   * pass, which stay the default.  The process environment variable
+   * QC_TC_DENSE=1 (read at qc_create) turns it on when the field is 0. */
   int32_t tc_dense;
 } qc_options;
 

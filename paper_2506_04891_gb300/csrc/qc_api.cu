@@ -1432,6 +1432,8 @@ QC_API qc_status qc_create(int n, qc_dtype dtype, const qc_layer* layers, int n_
   from_env(o.stages_bwd, "QC_TILE_STAGES");
   // QC_TMA=0 turns the TMA-staged passes off for circuits left at the default
   if (o.tma == 1 && getenv("QC_TMA") && atoi(getenv("QC_TMA")) == 0) o.tma = 0;
+  // QC_TC_DENSE=1 turns the tensor-core dense block on for circuits left at the default
+  if (o.tc_dense == 0 && getenv("QC_TC_DENSE") && atoi(getenv("QC_TC_DENSE")) == 1) o.tc_dense = 1;
   if (o.path < 0 || o.path > 2) return fail(QC_ERR_INVALID, "options.path must be 0, 1 or 2");
   if (o.ckpt_every < -1) return fail(QC_ERR_INVALID, "options.ckpt_every must be >= -1");
   {

@@ -9,15 +9,17 @@
 // Tile (2^12 amplitudes, contiguous bits 0..4 and gate bits h0..h0+6): the
 // TMA box is ordered [bit 4][gate row g][bits 0..3], so shared memory holds X
 // as two 16 KB blocks of 128 rows of 128 bytes (16 complex amplitudes, 32
-// floats), 128-byte swizzled: the B operand of D = K X in MN-major layout
-// (N = 64 floats: 32 amplitudes x (re, im); K = 128 gate rows).  K (M = 128
-// output rows) is built per CTA from the staged gate records in K-major
-// layout.  3xTF32: X = Xh + Xl with Xh the TF32 truncation the tensor core
+// floats), 128-byte swizzled.  The threads transpose it into the K-major
+// B operand of D = K X (N = 64 floats: 32 amplitudes x (re, im); K = 128 gate
+// rows; a probe showed the MN-major form of this operand multiplying to
+// zero), which frees the landing buffer for the next tile's copy before the
+// MMAs run.  K (M = 128 output rows) is built per CTA from the staged gate
+// records in K-major layout.  3xTF32: X = Xh + Xl with Xh the TF32 truncation the tensor core
 // applies and Xl = X - Xh (exact), the same for K; D = Kh Xh + Kh Xl + Kl Xh
 // accumulates in tensor memory (128 lanes x 64 FP32 columns), is read back by
 // tcgen05.ld and stored to global memory.
 //
-// One CTA of 256 threads per SM (192 KB of operands); one thread issues the
+// One CTA of 256 threads per SM (224 KB of operands); one thread issues the
 // TMA copies and the 48 MMAs of a tile and commits them to an mbarrier; every
 // wait is bounded in time (a CTA that gives up counts it in a timeout counter
 // that qc_kernel_timeouts reads, waits again with a bound for what it has in
@@ -31,8 +33,8 @@ namespace {
 constexpr int kTcThreads = 256;
 constexpr unsigned kTcCols = 64;                       // tensor-memory columns of D
 constexpr size_t kTcA = 4 * 128 * 128;                 // bytes of one A (K-matrix) copy: 4 K-atoms x 16 KB
-constexpr size_t kTcB = 2 * 128 * 128;                 // bytes of one B (tile) copy: 2 N-atoms x 16 KB
-constexpr size_t kTcSmem = 2 * kTcA + 2 * kTcB + 1024;  // Ah, Al, Xh, Xl + alignment slack
+constexpr size_t kTcB = 2 * 128 * 128;                 // bytes of one tile: 4096 complex64
+constexpr size_t kTcSmem = 2 * kTcA + 3 * kTcB + 1024;  // Ah, Al, landing tile, Bh, Bl + alignment slack
 static __device__ unsigned long long g_tc_timeouts;
 
 __device__ __forceinline__ uint64_t umma_sdesc(unsigned saddr, unsigned lbo, unsigned sbo) {
@@ -44,8 +46,8 @@ __device__ __forceinline__ uint64_t umma_sdesc(unsigned saddr, unsigned lbo, uns
   d |= (uint64_t)2 << 61;  // 128-byte swizzle
   return d;
 }
-// D f32, A and B tf32, A K-major, B MN-major, N = 64, M = 128
-constexpr unsigned kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (1u << 16) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// D f32, A and B tf32, both K-major, N = 64, M = 128
+constexpr unsigned kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ void umma_tf32(unsigned dt, uint64_t da, uint64_t db, unsigned acc) {
   asm volatile(
@@ -73,8 +75,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* sm = smraw_tc + (((raw_sa + 1023u) & ~1023u) - raw_sa);
   unsigned char* sAh = sm;
   unsigned char* sAl = sm + kTcA;
-  unsigned char* sXh = sm + 2 * kTcA;
-  unsigned char* sXl = sXh + kTcB;
+  unsigned char* sX = sm + 2 * kTcA;  // TMA landing buffer: [bit 4][gate row g][16 amplitudes], swizzled
+  unsigned char* sBh = sX + kTcB;      // B = X in K-major layout: 4 K-atoms (32 g each) x 64 n-rows x 128 B
+  unsigned char* sBl = sBh + kTcB;
   __shared__ unsigned long long bar_tma, bar_mma;
   __shared__ unsigned taddr_s;
   __shared__ float rec[7][4];
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int c4 = (int)(((long long)b << (n - h0 - 7)) | (f >> gap));
     const unsigned bar = smem_u32(&bar_tma);
     mbar_expect_tx(bar, (unsigned)kTcB);
-    tma_load_5d(smem_u32(sXh), &tm, 0, 0, 0, c3, c4, bar);
+    tma_load_5d(smem_u32(sX), &tm, 0, 0, 0, c3, c4, bar);
   };
   unsigned ph_tma = 0, ph_mma = 0;
   long long f = r0;
@@ -133,22 +136,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (!mbar_wait_bounded(smem_u32(&bar_tma), ph_tma, kTmaWaitNs)) bad = true;
     ph_tma ^= 1u;
     if (__syncthreads_or(bad)) { bad = true; break; }
-    // Xl = X - tf32(X), elementwise at the same (swizzled) positions
-    for (int i = tid; i < (int)(kTcB / 16); i += kTcThreads) {
-      const float4 x = reinterpret_cast<const float4*>(sXh)[i];
-      reinterpret_cast<float4*>(sXl)[i] = make_float4(tf32_lo(x.x), tf32_lo(x.y), tf32_lo(x.z), tf32_lo(x.w));
+    // B = X transposed into the K-major layout (the MN-major form of this
+    // operand did not multiply correctly), split into TF32 hi and lo: each
+    // thread reads one 16-byte chunk (4 floats n = 4c .. 4c+3 of row g) and
+    // writes 4 elements (n, g); a warp covers 32 consecutive rows of one
+    // chunk column, so reads hit 8 distinct chunks per quarter warp and the
+    // writes of each n fill one 128-byte row
+    for (int q = tid; q < (int)(kTcB / 16); q += kTcThreads) {
+      const int jh = q >> 10, cc = (q >> 7) & 7, g = q & 127;
+      const float4 x = *reinterpret_cast<const float4*>(sX + jh * 16384 + g * 128 + ((cc ^ (g & 7)) << 4));
+      const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const unsigned nn = (unsigned)(32 * jh + 4 * cc + e);
+        const unsigned off = (unsigned)(g >> 5) * 8192u + nn * 128u + (((((unsigned)g & 31u) >> 2) ^ (nn & 7u)) << 4) +
+                             ((unsigned)g & 3u) * 4u;
+        *reinterpret_cast<float*>(sBh + off) = xv[e];
+        *reinterpret_cast<float*>(sBl + off) = tf32_lo(xv[e]);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const unsigned ah = smem_u32(sAh), al = smem_u32(sAl), xh = smem_u32(sXh), xl = smem_u32(sXl);
-      // k-step s: A atom s / 4 at +32 bytes per step inside it; B rows 8 s .. 8 s + 7
+      // the landing buffer is free: the next tile's copy overlaps the MMAs
+      if (f + cps < tps) issue(f + cps);
+      const unsigned ah = smem_u32(sAh), al = smem_u32(sAl), xh = smem_u32(sBh), xl = smem_u32(sBl);
+      // k-step s: A and B atom s / 4, at +32 bytes per step inside it
       for (int pass = 0; pass < 3; ++pass) {
         const unsigned a0 = pass == 2 ? al : ah, b0 = pass == 1 ? xl : xh;
         for (int s = 0; s < 16; ++s) {
           const uint64_t da = umma_sdesc(a0 + (unsigned)(s >> 2) * (128u * 128u) + (unsigned)(s & 3) * 32u, 16, 1024);
-          const uint64_t dB = umma_sdesc(b0 + (unsigned)s * 1024u, 128u * 128u, 1024);
+          const uint64_t dB = umma_sdesc(b0 + (unsigned)(s >> 2) * 8192u + (unsigned)(s & 3) * 32u, 16, 1024);
           umma_tf32(taddr, da, dB, (pass | s) != 0);
         }
       }
@@ -158,8 +177,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     ph_mma ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (__syncthreads_or(bad)) { bad = true; break; }
-    // the operands are consumed: the next tile's copy overlaps the read-back
-    if (tid == 0 && f + cps < tps) issue(f + cps);
     // warp w reads lanes (rows g') 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31
     // = amplitudes j = 16 (w / 4) .. + 15 of row g'
     {
@@ -168,12 +185,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+          // the load is asynchronous: wait in the same statement, so that no
+          // copy of a destination register can be placed before the data lands
+          "tcgen05.wait::ld.sync.aligned;\n"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
             "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
             "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
             "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(ta));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          : "r"(ta)
+          : "memory");
       const int gr = 32 * (warp & 3) + lane, j0 = 16 * (warp >> 2);
       const int kb = (int)(((f & ((1LL << gap) - 1)) << 5) | ((f >> gap) << (h0 + 7)));
       float4* o = reinterpret_cast<float4*>(db + (kb | j0 | (gr << h0)));

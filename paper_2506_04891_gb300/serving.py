@@ -363,8 +363,15 @@ def serve_benchmark(count: int = 10000, slots: int = 4, budget_frac: float = 0.8
 
     def sched():
         return Scheduler(budget, slots, ex.footprint)
-    # warm up the kernels and plans of every qubit count
-    Server(ex, sched()).run(make_requests(2 * (n_range[1] - n_range[0] + 1), seed + 1, n_range, (1, 4)))
+    # warm up: every qubit count's circuit (qc_create allocates its <Z>
+    # scratch) and one small request of each, before anything is measured
+    warm = []
+    for k, n in enumerate(range(n_range[0], n_range[1] + 1)):
+        ex.circuit(n)
+        r = make_requests(1, seed + 1 + k, (n, n), (1, 2))[0]
+        r.rid = k
+        warm.append(r)
+    Server(ex, sched()).run(warm)
     torch.cuda.synchronize()
     reqs = make_requests(count, seed, n_range, b_range)
     sample = reqs[: min(closed_sample, count)]

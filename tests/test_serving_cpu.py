@@ -21,8 +21,8 @@ class FakeExecutor:
     def footprint(n, b):
         return (b << n) * 8 * 3
 
-    def launch(self, req, lo, hi):
-        self.log.append((req.rid, lo, hi))
+    def launch(self, req, lo, hi, offset=0):
+        self.log.append((req.rid, lo, hi, offset))
         return {"left": self.polls, "req": req, "lo": lo, "hi": hi}
 
     def done(self, h):
@@ -64,10 +64,17 @@ def test_request_too_large_for_budget_is_rejected():
 
 class BudgetCheckingScheduler(S.Scheduler):
     def admit(self, key, n, b):
-        super().admit(key, n, b)
+        off = super().admit(key, n, b)
         assert self.used <= self.budget
         assert len(self.in_flight) <= self.slots
+        # the regions of the chunks in flight are disjoint and inside the arena
+        spans = sorted(self.in_flight.values())
+        for (o1, s1), (o2, s2) in zip(spans, spans[1:]):
+            assert o1 + s1 <= o2
+        assert spans[-1][0] + spans[-1][1] <= self.budget
+        assert off % S.ALIGN == 0
         self.peak = max(getattr(self, "peak", 0), len(self.in_flight))
+        return off
 
 
 @pytest.mark.parametrize("slots", [1, 2, 5])
@@ -86,6 +93,7 @@ def test_mixed_results_equal_direct_computation(slots):
         assert res.chunks == len(sch.split(r))
         assert res.done >= res.admitted >= res.arrival
     assert sch.used == 0 and not sch.in_flight
+    assert sch.free == [(0, sch.budget)]  # every region returned and merged
     if slots > 1:
         assert sch.peak > 1  # work overlapped
     assert stats["p99_ms"] >= stats["p50_ms"] >= 0
@@ -96,3 +104,19 @@ def test_poisson_arrivals_are_seeded_and_increasing():
     b = S.poisson_arrivals(100, 50.0, seed=1)
     assert a == b and all(x < y for x, y in zip(a, a[1:]))
     assert abs(np.mean(np.diff(a)) - 1 / 50.0) < 0.01
+
+
+def test_arena_first_fit_reuses_and_merges_regions():
+    sch = S.Scheduler(10 * S.ALIGN, 4, lambda n, b: b * S.ALIGN)
+    a = sch.admit("a", 1, 3)
+    b = sch.admit("b", 1, 3)
+    c = sch.admit("c", 1, 4)
+    assert (a, b, c) == (0, 3 * S.ALIGN, 6 * S.ALIGN)
+    assert not sch.can_admit(1, 1)
+    sch.release("b")
+    assert sch.can_admit(1, 3) and not sch.can_admit(1, 4)
+    assert sch.admit("d", 1, 2) == 3 * S.ALIGN
+    sch.release("a")
+    sch.release("c")
+    sch.release("d")
+    assert sch.free == [(0, 10 * S.ALIGN)] and sch.used == 0
