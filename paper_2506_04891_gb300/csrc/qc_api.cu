@@ -233,10 +233,13 @@ int sm_count() {
 
 // CTAs per sample of a persistent tile pass: as many as the SMs hold at the
 // pass's residency (its compiled CTAs per SM, fewer if its shared memory does
-// not fit that many).
+// not fit that many), rounded down so the whole grid is resident at once: a
+// batch that does not divide the slots would otherwise leave a second wave of
+// up to batch - 1 CTAs that starts when the first one ends (32 samples at
+// two CTAs per SM: 320 CTAs for 304 slots before, 288 now).
 int tile_cps(int batch, int n, int t, int resident) {
   const long long tps = 1LL << (n - t);
-  long long c = ((long long)resident * sm_count() + batch - 1) / batch;
+  long long c = ((long long)resident * sm_count()) / batch;
   if (c > tps) c = tps;
   if (c < 1) c = 1;
   return (int)c;
@@ -336,7 +339,11 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     memset(&P, 0, sizeof(P));
     P.n = n;
     if (first) {
-      P.c = e; P.h0 = e; P.t = e;
+      // the tile keeps its full width when a brick pair ends the op range one
+      // bit early (the pair goes to the next pass, which starts at e): the
+      // extra bit carries no op, and the full-width tile can be staged by TMA
+      const int w = std::min(n, s + cap);
+      P.c = w; P.h0 = w; P.t = w;
     } else {
       // spare tile capacity widens the contiguous low segment
       P.c = std::min(s, std::max(cbits, tmax - (e - s)));
@@ -378,11 +385,12 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
         o.cpidx = -1;
         o.op.l = (int16_t)local(plo);
         o.op.is2q = 1;
+        o.op.pat = (int16_t)(L.kind == QC_L_ECR_BRICK ? 1 : 0);
         const int np = (ns == 2 && L.diff && L.kind == QC_L_MS_BRICK) ? 3 : 0;
         o.op.np = (int16_t)np;
         o.op.coef = L.coef_off + (long long)i * kRec2q;
         o.op.bstride = L.coef_bstride;
-        o.op.nco = 32 + (ns == 2 ? 32 * np : 0);
+        o.op.nco = 32 + (np ? 8 : 0);  // M, and for the MS backward its generator phases
         for (int k = 0; k < np; ++k) o.pidx.push_back(L.offset + 3 * i + k);
         ops.push_back(o);
       }
@@ -482,6 +490,15 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
       for (int r = 0; r < 4; ++r)
         for (int i = 0; i < 4; ++i) P.rslot[r][i] = P.rcslot[r][i] = -1;
     P.nstage = tile_stages(c, P, ns, (int)c->rsize);
+    if (!defer && slot > 0 && ns == 2) {
+      // otherwise every slot in shared memory, where two CTAs per SM still
+      // fit (plus the TMA pass's alignment slack): the per-round FP64 warp
+      // sums cost more than the pass's gate arithmetic on parametrised
+      // brick layers
+      P.defer = 2;
+      const size_t per_sm = 228 * 1024, per_cta = tile_smem_bytes(P, ns, (int)c->rsize) + 2048;
+      if (2 * per_cta > per_sm) P.defer = 0;
+    }
     out.push_back(P);
     s = e;
     first = false;
@@ -1773,8 +1790,9 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
         // contiguous pass's compile-time element patterns
         const int post = !st.tp.post ? 0
                          : (st.ns == 1 && st.rb == 4 && c->dtype == QC_C64 && fwd_post_contig(st.tp)) ? 2 : 1;
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d store=%d pre=%d post=%d tma=%d tc=%d src=%d dst=%d",
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d defer=%d store=%d pre=%d post=%d tma=%d tc=%d src=%d dst=%d",
                  tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nstage, st.tp.nrounds, st.tp.nops, st.tp.nslots,
+                 st.tp.defer,
                  st.tp.store, st.tp.pre, post, st.tma, st.tc, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {

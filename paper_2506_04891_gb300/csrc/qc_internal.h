@@ -32,7 +32,12 @@ enum ZMode { Z_IDENT = 0, Z_RINGXOR = 1 };
 constexpr int kRec1q = 20;    // M (2x2 complex) + A = M^dagger dM (2x2 complex) + the real parts
                               // of M packed (m00, m01, m10, m11) at kRealOff
 constexpr int kRealOff = 16;
-constexpr int kRec2q = 128;   // M (4x4 complex) + up to three A (4x4 complex)
+// two-qubit record: M (4x4 complex, 32 R), then for MS the phases e_r of its
+// generator K (K[r][r ^ 3] = e_r, M = cos(pi theta) I - i sin(pi theta) K;
+// 4 complex, 8 R) and the three A = M^dagger dM (4x4 complex each)
+constexpr int kRec2q = 136;
+constexpr int kRec2qK = 32;   // offset of the generator phases
+constexpr int kRec2qA = 40;   // offset of the first A
 
 struct LayerInfo {
   int kind, source, offset, parity;
@@ -67,7 +72,7 @@ struct TileOp {
   int16_t np;       // gradient parameters produced (0, 1 or 3)
   int16_t slot;     // first gradient slot in the pass's partial vector
   int16_t cslot;    // companion gradient slot (ck != 0)
-  int16_t pad1;
+  int16_t pat;      // 2q: nonzero pattern of the gate matrix, 0 columns r ^ {0, 3}, 1 r ^ {1, 3}
   int32_t soff;     // offset of the op's coefficients in the staged smem block (R units)
   int32_t nco;      // number of R to stage
   long long coef;   // coefficient offset (R units) for sample 0
@@ -88,10 +93,13 @@ struct TilePass {
   int ncomp;                         // companion slots: the last ncomp of the nslots
   int store;                         // 0: gradient only, no store
   int ncoef;                         // R units of staged coefficients
-  // deferred gradient reduction (single-qubit ops only, <= 4 rounds): slot of
-  // the op on register bit i of round r and of its companion, -1 if none.
-  // Per-thread sums stay in registers (own slots) and in shared memory
-  // (companions, [ncomp][kThreads] R) until the CTA's last tile.
+  // deferred gradient reduction: the per-thread FP32 sums of every slot stay
+  // on the SM until the CTA's last tile and are then reduced in FP64 once.
+  // 1 (single-qubit ops only, <= 4 rounds): own slots in registers, rslot /
+  // rcslot give the slot of the op on register bit i of round r and of its
+  // companion (-1 if none), companions in shared memory ([ncomp][kThreads] R);
+  // 2 (any pass whose sums fit): every slot in shared memory
+  // ([nslots][kThreads] R); 0: each round reduces its sums in FP64.
   int defer;
   int16_t rslot[4][4];
   int16_t rcslot[4][4];
@@ -156,13 +164,17 @@ constexpr size_t kFphBytes(int rsize) {
   return ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15) + (size_t)(1 << kFphMaxSE) * 2 * rsize;
 }
 __host__ __device__ inline size_t tsm_align16(size_t x) { return (x + 15) & ~(size_t)15; }
+// per-thread deferred sums a backward pass keeps in shared memory
+__host__ __device__ inline int tile_defer_slots(const TilePass& P) {
+  return P.defer == 1 ? P.ncomp : P.defer == 2 ? P.nslots : 0;
+}
 __host__ __device__ inline TileSmem tile_smem_layout(const TilePass& P, int ns, int rsize) {
   TileSmem L;
   L.buf = 0;
   L.sco = tsm_align16(L.buf + (size_t)P.nstage * ns * ((size_t)1 << P.t) * 2 * rsize);
   L.sred = tsm_align16(L.sco + (size_t)P.ncoef * rsize);
   L.sdef = tsm_align16(L.sred + (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double));
-  L.smarg = tsm_align16(L.sdef + (ns == 2 && P.defer ? (size_t)P.ncomp * kThreads * rsize : 0));
+  L.smarg = tsm_align16(L.sdef + (ns == 2 ? (size_t)tile_defer_slots(P) * kThreads * rsize : 0));
   const bool pre = ns == 2 && P.pre;
   L.sratio = tsm_align16(L.smarg + (pre ? (size_t)kWarps * (P.n + 1) * sizeof(double) : 0));
   L.smacc = L.sratio;

@@ -65,12 +65,19 @@ __global__ void k_coef(const CoefJob* __restrict__ jobs, int njobs, int n, int b
         double p1 = param_of(J, b, 3 * g + 1, x, theta, n_in);
         double th = param_of(J, b, 3 * g + 2, x, theta, n_in);
         gate_ms(p0, p1, th, M);
+        const double wt = 2.0 * kPi;
+        const dc e[4] = {dexpi(-wt * (p0 + p1)), dexpi(-wt * (p1 - p0)), dexpi(-wt * (p0 - p1)),
+                         dexpi(wt * (p0 + p1))};
+        for (int r = 0; r < 4; ++r) {
+          o[kRec2qK + 2 * r] = (R)e[r].x;
+          o[kRec2qK + 2 * r + 1] = (R)e[r].y;
+        }
         for (int w = 0; w < 3; ++w) {
           dgate_ms(p0, p1, th, w, D);
           mdag_mul(M, D, A, 4);
           for (int i = 0; i < 16; ++i) {
-            o[32 + 32 * w + 2 * i] = (R)A[i].x;
-            o[32 + 32 * w + 2 * i + 1] = (R)A[i].y;
+            o[kRec2qA + 32 * w + 2 * i] = (R)A[i].x;
+            o[kRec2qA + 32 * w + 2 * i + 1] = (R)A[i].y;
           }
         }
       } else if (J.kind == QC_L_CZ_BRICK) {
@@ -352,13 +359,13 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
     R W = 0, acc[JB + 2], Wm = 0, accm[JB + 2];
 #pragma unroll
     for (int s = 0; s < JB + 2; ++s) acc[s] = accm[s] = 0;
+    if constexpr (NS == 1) {
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      const int i = tid + (j << 8);
-      if (i < lim) {
-        const long long k = base + i;
-        const long long km = N - 1 - k;  // = mbase + (CH - 1 - i)
-        if (NS == 1) {
+      for (int j = 0; j < NJ; ++j) {
+        const int i = tid + (j << 8);
+        if (i < lim) {
+          const long long k = base + i;
+          const long long km = N - 1 - k;  // = mbase + (CH - 1 - i)
           const C xk = src0[sb + k], xm = src0[sb + km];
           if (P.has_phase) {
             dst0[sb + k] = cmul<R>(diag_phase<R>(tabs, P.tb, km), xm);
@@ -367,27 +374,59 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
             dst0[sb + k] = xm;
             dst0[sb + km] = xk;
           }
-        } else {
-          const C pk = src0[sb + k], pm = src0[sb + km];
-          const C lk = src1[sb + k], lm = src1[sb + km];
-          C yk, ym, uk, um;
-          if (P.has_phase) {
-            const C phk = diag_phase<R>(tabs, P.tb, k), phm = diag_phase<R>(tabs, P.tb, km);
-            yk = cmulc<R>(phk, pm); uk = cmulc<R>(phk, lm);  // in[k] = conj(ph(k)) out[~k]
-            ym = cmulc<R>(phm, pk); um = cmulc<R>(phm, lk);
-          } else {
-            yk = pm; uk = lm; ym = pk; um = lk;
-          }
-          dst0[sb + k] = yk; dst1[sb + k] = uk;
-          dst0[sb + km] = ym; dst1[sb + km] = um;
-          const R wk = im_cdot<R>(uk, yk), wm = im_cdot<R>(um, ym);
-          W += wk;
-          Wm += wm;
+        }
+      }
+    } else {
+      // U steps' loads (both states at k and ~k, and the phase-table entries)
+      // are issued before any of their stores, so a thread has 4U amplitude
+      // loads in flight instead of 4: a thread's elements are its own, and k
+      // and ~k of different steps never coincide (k + k' = N - 1 would need
+      // two indices of one chunk, or of a chunk and its mirror at the same
+      // step, to add up to an odd number they cannot reach), so the reorder
+      // is safe in place.
+      constexpr int U = NJ < 4 ? NJ : 4;
 #pragma unroll
-          for (int s = 0; s < JB + 2; ++s) {
-            // z = k: j-bit contribution (j << 8); mirror: z = km, i' = CH-1-i
-            if (((j << 8) >> (7 + s)) & 1) acc[s] += wk;
-            if (((j << 8) >> (7 + s)) & 1) accm[s] += wm;
+      for (int j0 = 0; j0 < NJ; j0 += U) {
+        C pk[U], pm[U], lk[U], lm[U], phk[U], phm[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = tid + ((j0 + u) << 8);
+          if (i < lim) {
+            const long long k = base + i;
+            const long long km = N - 1 - k;  // = mbase + (CH - 1 - i)
+            pk[u] = src0[sb + k]; pm[u] = src0[sb + km];
+            lk[u] = src1[sb + k]; lm[u] = src1[sb + km];
+            if (P.has_phase) {
+              phk[u] = diag_phase<R>(tabs, P.tb, k);
+              phm[u] = diag_phase<R>(tabs, P.tb, km);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + u;
+          const int i = tid + (j << 8);
+          if (i < lim) {
+            const long long k = base + i;
+            const long long km = N - 1 - k;
+            C yk, ym, uk, um;
+            if (P.has_phase) {
+              yk = cmulc<R>(phk[u], pm[u]); uk = cmulc<R>(phk[u], lm[u]);  // in[k] = conj(ph(k)) out[~k]
+              ym = cmulc<R>(phm[u], pk[u]); um = cmulc<R>(phm[u], lk[u]);
+            } else {
+              yk = pm[u]; uk = lm[u]; ym = pk[u]; um = lk[u];
+            }
+            dst0[sb + k] = yk; dst1[sb + k] = uk;
+            dst0[sb + km] = ym; dst1[sb + km] = um;
+            const R wk = im_cdot<R>(uk, yk), wm = im_cdot<R>(um, ym);
+            W += wk;
+            Wm += wm;
+#pragma unroll
+            for (int s = 0; s < JB + 2; ++s) {
+              // z = k: j-bit contribution (j << 8); mirror: z = km, i' = CH-1-i
+              if (((j << 8) >> (7 + s)) & 1) acc[s] += wk;
+              if (((j << 8) >> (7 + s)) & 1) accm[s] += wm;
+            }
           }
         }
       }
@@ -827,7 +866,7 @@ __device__ __forceinline__ void sm_2q_bwd(cx<R>* P, cx<R>* L, int n, int plo, co
     }
     for (int s = 0; s < 4; ++s) { P[a | (s << plo)] = y[s]; L[a | (s << plo)] = w[s]; }
     for (int k = 0; k < np; ++k) {
-      const R* A = m + 32 + 32 * k;
+      const R* A = m + kRec2qA + 32 * k;
       for (int r = 0; r < 4; ++r) {
         C t = mk<R>(0, 0);
         for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(A + 2 * (r * 4 + s)), y[s], t);

@@ -148,31 +148,53 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
   }
 }
 
-// forward two-qubit op on register bits (I, I+1); 4x4 index = 2*bit(I+1) + bit(I)
-template <class R, int RB, int I>
+// Two-qubit ops on register bits (I, I+1); 4x4 index = 2*bit(I+1) + bit(I),
+// the gate's first qubit the high bit.  Every brick gate has at most two
+// nonzeros per row, in columns r ^ P and r ^ Q: (P, Q) = (0, 3) for MS, CZ
+// and SWAP, (1, 3) for ECR (SP = 1).  M^dagger has the same pattern, and
+// A = M^dagger dM the pattern {0, P ^ Q}.  The staged records are the dense
+// 4x4 matrices; only the pattern's entries are read (the others are exact
+// zeros), so a gate costs 8 complex multiply-adds per 4 amplitudes, not 16.
+template <int SP>
+struct Pat2 {
+  static constexpr int P = SP ? 1 : 0, Q = 3, D = P ^ Q;
+};
+
+// forward: y = M x
+template <class R, int RB, int I, int SP>
 __device__ __forceinline__ void ap2(cx<R>* v, const R* m) {
   using C = cx<R>;
+  constexpr int P = Pat2<SP>::P, Q = Pat2<SP>::Q;
 #pragma unroll
   for (int a = 0; a < (1 << RB); ++a)
     if (!(a & (3 << I))) {
-      C x[4], y[4];
+      C x[4];
 #pragma unroll
       for (int s = 0; s < 4; ++s) x[s] = v[a | (s << I)];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        C t = mk<R>(0, 0);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(m + 2 * (r * 4 + s)), x[s], t);
-        y[r] = t;
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s) v[a | (s << I)] = y[s];
+      for (int r = 0; r < 4; ++r)
+        v[a | (r << I)] = cfma<R>(ldc<R>(m + 2 * (r * 4 + (r ^ Q))), x[r ^ Q],
+                                  cmul<R>(ldc<R>(m + 2 * (r * 4 + (r ^ P))), x[r ^ P]));
     }
 }
 
-template <class R, int RB, int I>
+// backward: undo M on psi and lambda (y = M^dagger x, w = M^dagger u).  The
+// only parametrised brick gate is MS (np = 3): M = c I - i s K with c, s =
+// cos, sin(pi theta) and K[r][r ^ 3] = e_r (e_0 = conj(e_3) = exp(-i alpha),
+// e_1 = conj(e_2) = exp(-i beta), alpha = 2 pi (phi0 + phi1), beta =
+// 2 pi (phi1 - phi0)), staged after M.  Gradients 2 Re <u| dM |y> (u the
+// lambda before the undo): alpha and beta enter only the entries M[r][r ^ 3],
+// d/d alpha of M[0][3], M[3][0] is -i, +i times the entry (beta: M[1][2],
+// M[2][1]), so with R_r = conj(u_r) M[r][r ^ 3] y[r ^ 3]
+//   g_alpha = 2 Im(R_0 - R_3),  g_beta = 2 Im(R_1 - R_2),
+// and d/d phi0 = 2 pi (g_alpha - g_beta), d/d phi1 = 2 pi (g_alpha + g_beta);
+// K commutes with M, so M^dagger dM/d theta = -i pi K and
+//   d/d theta = 2 pi Im <w| K |y>.
+template <class R, int RB, int I, int SP>
 __device__ __forceinline__ void bw2(cx<R>* p, cx<R>* l, const R* m, int np, R* acc) {
   using C = cx<R>;
+  constexpr int P = Pat2<SP>::P, Q = Pat2<SP>::Q;
+  constexpr R kTwoPi = (R)6.283185307179586;
 #pragma unroll
   for (int a = 0; a < (1 << RB); ++a)
     if (!(a & (3 << I))) {
@@ -181,30 +203,24 @@ __device__ __forceinline__ void bw2(cx<R>* p, cx<R>* l, const R* m, int np, R* a
       for (int s = 0; s < 4; ++s) { x[s] = p[a | (s << I)]; u[s] = l[a | (s << I)]; }
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        C t = mk<R>(0, 0), z = mk<R>(0, 0);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          C ms = ldc<R>(m + 2 * (s * 4 + r));  // (M^dagger)[r][s] = conj(M[s][r])
-          t = cfmac<R>(ms, x[s], t);
-          z = cfmac<R>(ms, u[s], z);
-        }
-        y[r] = t; w[r] = z;
+        // (M^dagger)[r][s] = conj(M[s][r]), nonzero for s = r ^ P, r ^ Q
+        const C mp = ldc<R>(m + 2 * ((r ^ P) * 4 + r)), mq = ldc<R>(m + 2 * ((r ^ Q) * 4 + r));
+        y[r] = cfmac<R>(mq, x[r ^ Q], cfmac<R>(mp, x[r ^ P], mk<R>(0, 0)));
+        w[r] = cfmac<R>(mq, u[r ^ Q], cfmac<R>(mp, u[r ^ P], mk<R>(0, 0)));
       }
 #pragma unroll
       for (int s = 0; s < 4; ++s) { p[a | (s << I)] = y[s]; l[a | (s << I)] = w[s]; }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {  // compile-time acc index (np <= 3)
-        if (k >= np) break;
-        const R* A = m + 32 + 32 * k;
-        R g = 0;
+      if (SP == 0 && np) {
+        R imr[4], kw = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          C t = mk<R>(0, 0);
-#pragma unroll
-          for (int s = 0; s < 4; ++s) t = cfma<R>(ldc<R>(A + 2 * (r * 4 + s)), y[s], t);
-          g += re_cdot<R>(w[r], t);
+          imr[r] = im_cdot<R>(u[r], cmul<R>(ldc<R>(m + 2 * (r * 4 + (r ^ 3))), y[r ^ 3]));
+          kw += im_cdot<R>(w[r], cmul<R>(ldc<R>(m + kRec2qK + 2 * r), y[r ^ 3]));
         }
-        acc[I * 3 + k] += 2 * g;
+        const R ga = 2 * (imr[0] - imr[3]), gb = 2 * (imr[1] - imr[2]);
+        acc[I * 3 + 0] += kTwoPi * (ga - gb);
+        acc[I * 3 + 1] += kTwoPi * (ga + gb);
+        acc[I * 3 + 2] += kTwoPi * kw;
       }
     }
 }
@@ -219,12 +235,21 @@ __device__ __forceinline__ void tile_bit(const TilePass& P, int r, cx<R>* v0, cx
   if (k < 0) return;
   const TileOp& o = P.ops[k];
   const R* mc = sco + o.soff;
+  constexpr int I2 = (KIND == 2 && I + 1 < RB) ? I : 0;
   if (NS == 1) {
-    if (KIND == 2) ap2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, mc);
-    else ap1<R, RB, I>(v0, mc, KIND == 1);
+    if (KIND == 2) {
+      if (o.pat) ap2<R, RB, I2, 1>(v0, mc);
+      else ap2<R, RB, I2, 0>(v0, mc);
+    } else {
+      ap1<R, RB, I>(v0, mc, KIND == 1);
+    }
   } else {
-    if (KIND == 2) bw2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, v1, mc, o.np, acc);
-    else bw1<R, RB, I>(v0, v1, mc, KIND == 1, o.np, o.gk, o.ck, acc);
+    if (KIND == 2) {
+      if (o.pat) bw2<R, RB, I2, 1>(v0, v1, mc, o.np, acc);
+      else bw2<R, RB, I2, 0>(v0, v1, mc, o.np, acc);
+    } else {
+      bw1<R, RB, I>(v0, v1, mc, KIND == 1, o.np, o.gk, o.ck, acc);
+    }
   }
 }
 
@@ -412,8 +437,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
   }
   if (NS == 2) {
     for (int i = threadIdx.x; i < kWarps * P.nslots; i += kThreads) sred[i] = 0;
-    if (P.defer)
-      for (int s = 0; s < P.ncomp; ++s) sdef[s * kThreads + threadIdx.x] = 0;
+    for (int s = 0, nd = tile_defer_slots(P); s < nd; ++s) sdef[s * kThreads + threadIdx.x] = 0;
   }
 
   constexpr int kAR = RB == 4 ? 3 : 4;  // deferred rounds (the planner matches)
@@ -796,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
         }
       }
       if (NS == 2) {
-        if (P.defer) {
+        if (P.defer == 1) {
           // keep per-thread sums across tiles, reduced once after the last
           // tile: the pass's own slots in registers, companion slots in this
           // thread's column of shared memory
@@ -812,6 +836,20 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
               const int cs = P.rcslot[r][i];
               if (cs >= 0) sdef[(cs - P.nslots + P.ncomp) * kThreads + threadIdx.x] += acc[i * 3 + 1];
             }
+          }
+        } else if (P.defer == 2) {
+          // the thread's column of every slot in shared memory (each thread
+          // touches only its own words: no barrier needed)
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            const int k = P.rbit[r][i];
+            if (k < 0) continue;
+            const TileOp& o = P.ops[k];
+            R* col = sdef + (int)o.slot * kThreads + threadIdx.x;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < o.np) col[q * kThreads] += acc[i * 3 + q];
+            if (o.ck) sdef[(int)o.cslot * kThreads + threadIdx.x] += acc[i * 3 + 1];
           }
         } else {
           // per op of the round, by its (lower) register bit: every acc index
@@ -931,7 +969,13 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     slot = slot + 1 == nst ? 0 : slot + 1;
   }
   cp_async_wait_group<0>();
-  if (NS == 2 && P.defer) {
+  if (NS == 2 && P.defer == 2) {
+    for (int s = 0; s < P.nslots; ++s) {
+      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
+      if (lane == 0) sred[warp * P.nslots + s] += v;
+    }
+  }
+  if (NS == 2 && P.defer == 1) {
 #pragma unroll
     for (int r = 0; r < kAR; ++r)
 #pragma unroll

@@ -104,7 +104,7 @@ __host__ __device__ inline TmaSmem tma_smem_layout(const TilePass& P, int ns) {
   L.sco = tsm_align16(L.bar + 8 * (size_t)P.nstage);
   L.sred = tsm_align16(L.sco + (size_t)P.ncoef * 4);
   L.sdef = tsm_align16(L.sred + (size_t)kWarps * (P.nslots > 0 ? P.nslots : 1) * sizeof(double));
-  L.smarg = tsm_align16(L.sdef + (ns == 2 && P.defer ? (size_t)P.ncomp * kThreads * 4 : 0));
+  L.smarg = tsm_align16(L.sdef + (ns == 2 ? (size_t)tile_defer_slots(P) * kThreads * 4 : 0));
   const bool pre = ns == 2 && P.pre;
   L.smacc = tsm_align16(L.smarg + (pre ? (size_t)kWarps * (P.n + 1) * sizeof(double) : 0));
   L.fph = tsm_align16(L.smacc + (pre ? (size_t)kPreAcc * kThreads * 4 : 0));
@@ -216,7 +216,7 @@ __device__ bool scale_real_records(float* sco, int nops, int nco) {
 // gradient count and generator kinds, so the op's index and coefficient
 // block follow from the round's presence mask without per-op lookups.
 template <int NS, int RB, int KIND, int I, bool COMP>
-__device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, int kscaled,
+__device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, int pat, int kscaled,
                                         float2* v0, float2* v1, const float* sco, float* acc) {
   using R = float;
   if (KIND == 2 && I + 1 >= RB) return;
@@ -228,12 +228,21 @@ __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np,
     else bw1t<RB, I, COMP>(v0, v1, mc, np, ck, acc);
     return;
   }
+  constexpr int I2 = (KIND == 2 && I + 1 < RB) ? I : 0;
   if (NS == 1) {
-    if (KIND == 2) ap2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, mc);
-    else ap1<R, RB, I>(v0, mc, KIND == 1);
+    if (KIND == 2) {
+      if (pat) ap2<R, RB, I2, 1>(v0, mc);
+      else ap2<R, RB, I2, 0>(v0, mc);
+    } else {
+      ap1<R, RB, I>(v0, mc, KIND == 1);
+    }
   } else {
-    if (KIND == 2) bw2<R, RB, (KIND == 2 && I + 1 < RB) ? I : 0>(v0, v1, mc, np, acc);
-    else bw1<R, RB, I, COMP>(v0, v1, mc, KIND == 1, np, gk, ck, acc);
+    if (KIND == 2) {
+      if (pat) bw2<R, RB, I2, 1>(v0, v1, mc, np, acc);
+      else bw2<R, RB, I2, 0>(v0, v1, mc, np, acc);
+    } else {
+      bw1<R, RB, I, COMP>(v0, v1, mc, KIND == 1, np, gk, ck, acc);
+    }
   }
 }
 
@@ -289,6 +298,7 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   // per-pass op data (uniform over the pass's ops) and the presence mask of
   // every round's register bits (4 bits per round)
   const int op_nco = P.ops[0].nco, op_np = P.ops[0].np, op_gk = P.ops[0].gk, op_ck = COMP ? P.ops[0].ck : 0;
+  const int op_pat = P.ops[0].pat;
   unsigned rmask_all = 0;
   for (int r = 0; r < P.nrounds; ++r)
 #pragma unroll
@@ -296,8 +306,7 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
       if (P.rbit[r][i] >= 0) rmask_all |= 1u << (4 * r + i);
   if (NS == 2) {
     for (int i = threadIdx.x; i < kWarps * P.nslots; i += kThreads) sred[i] = 0;
-    if (P.defer)
-      for (int s = 0; s < P.ncomp; ++s) sdef[s * kThreads + threadIdx.x] = 0;
+    for (int s = 0, nd = tile_defer_slots(P); s < nd; ++s) sdef[s * kThreads + threadIdx.x] = 0;
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -484,15 +493,15 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
           __syncthreads();
           if (threadIdx.x == 0 && f + cps < tps) issue(f + cps, 0);
         }
-        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1, sco, acc);
+        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1, sco, acc);
         if (RB > 1)
-          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1,
                                                        sco, acc);
         if (RB > 2)
-          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1,
                                                        sco, acc);
         if (RB > 3)
-          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, kscaled, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1,
                                                        sco, acc);
         if (NS == 1 && PRE >= 2 && fpost_ok && last) {
           // group g = tid holds local indices g | a << 8 of a contiguous pass:
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
         }
       }
       if (NS == 2) {
-        if (P.defer) {
+        if (P.defer == 1) {
 #pragma unroll
           for (int rr = 0; rr < kAR; ++rr)
             if (rr == r) {
@@ -561,6 +570,20 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
               const int cs = P.rcslot[r][i];
               if (cs >= 0) sdef[(cs - P.nslots + P.ncomp) * kThreads + threadIdx.x] += acc[i * 3 + 1];
             }
+          }
+        } else if (P.defer == 2) {
+          // the thread's column of every slot in shared memory (each thread
+          // touches only its own words: no barrier needed)
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            const int k = P.rbit[r][i];
+            if (k < 0) continue;
+            const TileOp& o = P.ops[k];
+            R* col = sdef + (int)o.slot * kThreads + threadIdx.x;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < o.np) col[q * kThreads] += acc[i * 3 + q];
+            if (o.ck) sdef[(int)o.cslot * kThreads + threadIdx.x] += acc[i * 3 + 1];
           }
         } else {
 #pragma unroll
@@ -609,7 +632,13 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
     slot = slot + 1 == nst ? 0 : slot + 1;
   }
 
-  if (NS == 2 && P.defer) {
+  if (NS == 2 && P.defer == 2) {
+    for (int s = 0; s < P.nslots; ++s) {
+      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
+      if (lane == 0) sred[warp * P.nslots + s] += v;
+    }
+  }
+  if (NS == 2 && P.defer == 1) {
 #pragma unroll
     for (int r = 0; r < kAR; ++r)
 #pragma unroll

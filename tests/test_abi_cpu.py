@@ -178,6 +178,22 @@ def test_geometry_environment_fills_unset_options_and_is_validated(q, monkeypatc
         monkeypatch.delenv(name)
 
 
+def test_backward_gradient_sums_kept_on_chip_per_pass_kind(q):
+    """Per-thread FP32 gradient sums stay on the SM across a CTA's tiles:
+    in registers for single-qubit passes of at most four rounds (defer=1), in
+    shared memory for the MS brick passes (two-qubit ops, three parameters
+    each: defer=2); zz26 keeps every pass in registers."""
+    desc = q.Circuit(20, W.ionq_circuit(20, 8), path=2).describe(32)
+    tiles = [l for l in desc.splitlines() if l.startswith("B") and " TILE " in l]
+    brick = [l for l in tiles if ",2q np=3" in l]
+    single = [l for l in tiles if ",2q" not in l]
+    assert brick and single
+    assert all("defer=2" in l for l in brick)
+    assert all("defer=1" in l for l in single)
+    zz = q.Circuit(26, W.zz_circuit(26, 12), path=2).describe(8)
+    assert all("defer=1" in l for l in zz.splitlines() if l.startswith("B") and " TILE " in l)
+
+
 def test_forward_diagonal_rides_on_the_contiguous_pass_run_last(q):
     """zz26: each block's IsingZZ phase (but the first, which the product-state
     kernel takes) is multiplied in the last round of the contiguous 2^12 pass,

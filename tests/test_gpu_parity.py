@@ -138,22 +138,42 @@ def test_leading_layer_gradient_folded_into_next_layer(name, dtype, n):
     compare(dtype, n, _fold_circuit(n, name), 3, seed=11, path=2, fuse=1)
 
 
-def test_folded_gradients_without_deferred_sums():
-    """Two register bits per round: more than four rounds per pass, so the
-    per-round warp reduction carries the companion slots (own process: the
-    knob is read once)."""
+def _run_with_env(code, env_extra):
+    import os
     import subprocess
     import sys
-    code = ("import sys; sys.path.insert(0, '.');"
-            "from tests.test_gpu_parity import compare, _fold_circuit;"
-            "[compare('c64', 14, _fold_circuit(14, k), 2, seed=12, path=2) for k in ('rx_ry', 'ry_rx', 'rx_sx')];"
-            "compare('c128', 13, _fold_circuit(13, 'ry_gpi2'), 2, seed=12, path=2)")
-    import os
-    env = dict(os.environ, QC_RB_BWD="2")
+    env = dict(os.environ, **env_extra)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+def test_folded_gradients_in_shared_memory_sums():
+    """Two register bits per round: more than four rounds per pass, so every
+    slot, companions included, keeps its per-thread sums in shared memory
+    (defer=2) instead of registers (own process: the knob is read once)."""
+    code = ("import sys; sys.path.insert(0, '.');"
+            "from tests.test_gpu_parity import compare, _fold_circuit;"
+            "[compare('c64', 14, _fold_circuit(14, k), 2, seed=12, path=2) for k in ('rx_ry', 'ry_rx', 'rx_sx')];"
+            "compare('c128', 13, _fold_circuit(13, 'ry_gpi2'), 2, seed=12, path=2)")
+    _run_with_env(code, {"QC_RB_BWD": "2"})
+
+
+def test_gradients_reduced_every_round_where_shared_sums_do_not_fit():
+    """Complex128 on 2^11-amplitude backward tiles (two buffers): the RX input
+    layer's pass has six rounds, and its per-thread sums do not fit in shared
+    memory beside two CTAs' tiles, so each round reduces them in FP64
+    (defer=0); the plan is checked to take that mode."""
+    code = ("import sys; sys.path.insert(0, '.');"
+            "from tests.test_gpu_parity import compare;"
+            "from paper_2506_04891_gb300 import workloads as W, qlayer as Q;"
+            "b = W._Builder(13);"
+            "[b.add(k, s, 0) for k, s in (('RX', 'input'), ('ROT', 'theta'), ('CNOT_RING', 'none'), ('ROT', 'theta'))];"
+            "d = Q.Circuit(13, b.layers, dtype='c128', path=2).describe(2);"
+            "assert any(l.startswith('B') and 'defer=0' in l and 'slots=11' in l for l in d.splitlines()), d;"
+            "compare('c128', 13, b.layers, 2, seed=15, path=2)")
+    _run_with_env(code, {"QC_TMAX_BWD": "11"})
 
 
 @pytest.mark.parametrize("path", [1, 2])
