@@ -322,26 +322,43 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
 #pragma unroll
     for (int s = 0; s < JB + 2; ++s) acc[s] = 0;
     if (active) {
+      if constexpr (NS == 1) {
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const long long k = base + tid + (j << 8);
-        const long long z = ztrans(k, n, ZM);
-        const C ph = diag_phase<R>(tabs, P.tb, z);
-        const C x = src0[sb + k];
-        if (NS == 1) {
-          dst0[sb + k] = cmul<R>(ph, x);
-        } else {
-          const C y = cmulc<R>(ph, x);             // conj(phase) * psi
-          const C u = cmulc<R>(ph, src1[sb + k]);  // conj(phase) * lambda
-          dst0[sb + k] = y;
-          dst1[sb + k] = u;
-          const R w = im_cdot<R>(u, y);
-          W += w;
-          constexpr int dummy = 0;
-          (void)dummy;
+        for (int j = 0; j < NJ; ++j) {
+          const long long k = base + tid + (j << 8);
+          const C ph = diag_phase<R>(tabs, P.tb, ztrans(k, n, ZM));
+          dst0[sb + k] = cmul<R>(ph, src0[sb + k]);
+        }
+      } else {
+        // U steps' loads (both states and the phase-table entries) before
+        // their stores: 2U amplitude loads in flight per thread; the step
+        // loop itself stays rolled (a fully unrolled one missed the
+        // instruction cache), the marginal bits of step j are runtime tests
+        constexpr int U = NJ < 4 ? NJ : 4;
+#pragma unroll 1
+        for (int j0 = 0; j0 < NJ; j0 += U) {
+          C xs[U], ls[U], ph[U];
 #pragma unroll
-          for (int s = 0; s < JB + 2; ++s)
-            if ((zj_bits<ZM>(j) >> (7 + s)) & 1) acc[s] += w;
+          for (int u = 0; u < U; ++u) {
+            const long long k = base + tid + ((j0 + u) << 8);
+            xs[u] = src0[sb + k];
+            ls[u] = src1[sb + k];
+            ph[u] = diag_phase<R>(tabs, P.tb, ztrans(k, n, ZM));
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int j = j0 + u;
+            const long long k = base + tid + (j << 8);
+            const C y = cmulc<R>(ph[u], xs[u]);  // conj(phase) * psi
+            const C w_ = cmulc<R>(ph[u], ls[u]);  // conj(phase) * lambda
+            dst0[sb + k] = y;
+            dst1[sb + k] = w_;
+            const R w = im_cdot<R>(w_, y);
+            W += w;
+            const int zb = zj_bits<ZM>(j);
+#pragma unroll
+            for (int s = 0; s < JB + 2; ++s) acc[s] += ((zb >> (7 + s)) & 1) ? w : (R)0;
+          }
         }
       }
     }
@@ -379,13 +396,14 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
     } else {
       // U steps' loads (both states at k and ~k, and the phase-table entries)
       // are issued before any of their stores, so a thread has 4U amplitude
-      // loads in flight instead of 4: a thread's elements are its own, and k
+      // loads in flight instead of 4 (the step loop stays rolled: fully
+      // unrolled it missed the instruction cache): a thread's elements are its own, and k
       // and ~k of different steps never coincide (k + k' = N - 1 would need
       // two indices of one chunk, or of a chunk and its mirror at the same
       // step, to add up to an odd number they cannot reach), so the reorder
       // is safe in place.
       constexpr int U = NJ < 4 ? NJ : 4;
-#pragma unroll
+#pragma unroll 1
       for (int j0 = 0; j0 < NJ; j0 += U) {
         C pk[U], pm[U], lk[U], lm[U], phk[U], phm[U];
 #pragma unroll
@@ -424,8 +442,9 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
 #pragma unroll
             for (int s = 0; s < JB + 2; ++s) {
               // z = k: j-bit contribution (j << 8); mirror: z = km, i' = CH-1-i
-              if (((j << 8) >> (7 + s)) & 1) acc[s] += wk;
-              if (((j << 8) >> (7 + s)) & 1) accm[s] += wm;
+              const bool on = ((j << 8) >> (7 + s)) & 1;
+              acc[s] += on ? wk : (R)0;
+              accm[s] += on ? wm : (R)0;
             }
           }
         }

@@ -178,6 +178,116 @@ __device__ __forceinline__ void bw1t(float2* p, float2* l, const float* m, int n
   else if (ck == 2) acc[I * 3 + 1] += gf * hs;
 }
 
+// Complex single-qubit gates with equal diagonal entries d = M00 = M11 (RX,
+// SX, GPI2) in the same scaled form: M = d (I + T), T off-diagonal, so a
+// gate costs one complex multiply-add per output instead of two.  Forward
+// records (tau0, tau1) = (M01 / d, M10 / d): y0 = x0 + tau0 x1, y1 = x1 +
+// tau1 x0.  Backward (M^dagger = conj(d) (I + T^dagger)): (sig0, sig1) =
+// (M10 / d, M01 / d), y0 = x0 + conj(sig0) x1, y1 = x1 + conj(sig1) x0, then
+// gf = |product of the factors so far|^2 and the record's A (unchanged) for
+// the gradient.  The product C of the omitted factors multiplies the last
+// gate's M (not its A), so the pass's outputs are exact.
+template <int RB, int I>
+__device__ __forceinline__ void ap1tc(float2* v, const float* m) {
+  float2 t0, t1;
+  ldc2<float>(m, t0, t1);
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (1 << I))) {
+      const float2 x0 = v[a], x1 = v[a | (1 << I)];
+      v[a] = cfma<float>(t0, x1, x0);
+      v[a | (1 << I)] = cfma<float>(t1, x0, x1);
+    }
+}
+template <int RB, int I, bool MAYCK>
+__device__ __forceinline__ void bw1tc(float2* p, float2* l, const float* m, int np, int gk, int ck_in,
+                                      float* acc) {
+  using C = float2;
+  const int ck = MAYCK ? ck_in : 0;
+  C s0, s1, a00, a01, a10, a11;
+  ldc2<float>(m, s0, s1);
+  const float gf = m[4];
+  if (np && gk != 1) {
+    ldc2<float>(m + 8, a00, a01);
+    ldc2<float>(m + 12, a10, a11);
+  }
+  float g = 0, h = 0;
+#pragma unroll
+  for (int a = 0; a < (1 << RB); ++a)
+    if (!(a & (1 << I))) {
+      const int a1 = a | (1 << I);
+      const C x0 = p[a], x1 = p[a1];
+      const C y0 = cfmac<float>(s0, x1, x0), y1 = cfmac<float>(s1, x0, x1);
+      p[a] = y0;
+      p[a1] = y1;
+      const C u0 = l[a], u1 = l[a1];
+      const C w0 = cfmac<float>(s0, u1, u0), w1 = cfmac<float>(s1, u0, u1);
+      l[a] = w0;
+      l[a1] = w1;
+      if (np) {
+        if (gk == 1) {
+          g += im_cdot<float>(w0, y1) + im_cdot<float>(w1, y0);
+        } else {
+          const C t0 = cfma<float>(a01, y1, cmul<float>(a00, y0));
+          const C t1 = cfma<float>(a11, y1, cmul<float>(a10, y0));
+          g += 2 * (re_cdot<float>(w0, t0) + re_cdot<float>(w1, t1));
+        }
+      }
+      if (ck) h += pauli_grad<float>(ck, w0, w1, y0, y1);
+    }
+  if (np) acc[I * 3] += gf * g;
+  if (ck) acc[I * 3 + 1] += gf * h;
+}
+
+// Rewrites a complex pass's staged records for the scaled form (one thread,
+// per CTA), under the same conditions as the real one below (every factor
+// but the last op's with |d| >= 2^-10, their product >= 2^-60 in magnitude)
+// and with M11 == M00 exactly; else returns false and leaves them.  The
+// ratios and the running product are formed in FP64 from the staged FP32
+// entries and rounded once (in FP32 their three roundings per ratio left the
+// pass's output norm off by ~5e-7 on a 12-gate pass, 8x the full form's).
+template <bool FWD>
+__device__ bool scale_complex_records(float* sco, int nops, int nco) {
+  if (nops < 2 || nco != (FWD ? 8 : 16)) return false;
+  double cr = 1.0, ci = 0.0;
+  for (int k = 0; k + 1 < nops; ++k) {
+    const float* r = sco + nco * k;
+    if (r[6] != r[0] || r[7] != r[1]) return false;
+    const double dr = r[0], di = r[1];
+    if (!(dr * dr + di * di >= 0x1p-20)) return false;
+    const double nr = cr * dr - ci * di, ni = cr * di + ci * dr;
+    cr = nr;
+    ci = ni;
+    if (!(cr * cr + ci * ci >= 0x1p-120)) return false;
+  }
+  cr = 1.0;
+  ci = 0.0;
+  for (int k = 0; k + 1 < nops; ++k) {
+    float* r = sco + nco * k;
+    const double dr = r[0], di = r[1], inv = 1.0 / (dr * dr + di * di);
+    const double nr = cr * dr - ci * di, ni = cr * di + ci * dr;
+    cr = nr;
+    ci = ni;
+    // x / d = x conj(d) / |d|^2
+    const double m01r = r[2], m01i = r[3], m10r = r[4], m10i = r[5];
+    const double q01r = (m01r * dr + m01i * di) * inv, q01i = (m01i * dr - m01r * di) * inv;
+    const double q10r = (m10r * dr + m10i * di) * inv, q10i = (m10i * dr - m10r * di) * inv;
+    r[0] = (float)(FWD ? q01r : q10r);
+    r[1] = (float)(FWD ? q01i : q10i);
+    r[2] = (float)(FWD ? q10r : q01r);
+    r[3] = (float)(FWD ? q10i : q01i);
+    r[4] = (float)(cr * cr + ci * ci);
+    r[5] = r[6] = r[7] = 0.f;
+  }
+  float* r = sco + nco * (nops - 1);
+  for (int j = 0; j < 4; ++j) {
+    const double xr = r[2 * j], xi = r[2 * j + 1];
+    r[2 * j] = (float)(cr * xr - ci * xi);
+    r[2 * j + 1] = (float)(cr * xi + ci * xr);
+  }
+  return true;
+}
+
 // Rewrites a real pass's staged records for the scaled form (one thread, per
 // CTA: the records are shared by the CTA's tiles).  Returns false, leaving the
 // records as they are, when a factor is small (|c| < 2^-10) or their product
@@ -187,26 +297,26 @@ __device__ __forceinline__ void bw1t(float2* p, float2* l, const float* m, int n
 template <bool FWD>
 __device__ bool scale_real_records(float* sco, int nops, int nco) {
   if (nops < 2 || nco != 4) return false;
-  float cacc = 1.f;
+  double cacc = 1.0;  // ratios and product in FP64, rounded once (as above)
   for (int k = 0; k + 1 < nops; ++k) {
     const float* r = sco + 4 * k;
     const float cc = r[0];
     if (!(fabsf(cc) >= 0x1p-10f) || r[3] != cc) return false;
     cacc *= cc;
-    if (!(fabsf(cacc) >= 0x1p-60f)) return false;
+    if (!(fabs(cacc) >= 0x1p-60)) return false;
   }
-  cacc = 1.f;
+  cacc = 1.0;
   for (int k = 0; k + 1 < nops; ++k) {
     float* r = sco + 4 * k;
-    const float m00 = r[0], m01 = r[1], m10 = r[2], m11 = r[3];
+    const double m00 = r[0], m01 = r[1], m10 = r[2], m11 = r[3];
     cacc *= m00;
-    r[0] = FWD ? m01 / m00 : m10 / m00;
-    r[1] = FWD ? m10 / m11 : m01 / m11;
-    r[2] = cacc * cacc;
+    r[0] = (float)(FWD ? m01 / m00 : m10 / m00);
+    r[1] = (float)(FWD ? m10 / m11 : m01 / m11);
+    r[2] = (float)(cacc * cacc);
     r[3] = 0.f;
   }
   float* r = sco + 4 * (nops - 1);
-  for (int j = 0; j < 4; ++j) r[j] *= cacc;
+  for (int j = 0; j < 4; ++j) r[j] = (float)(r[j] * cacc);
   return true;
 }
 
@@ -226,6 +336,11 @@ __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np,
   if (KIND == 1 && k < kscaled) {  // scaled form: every op before the last when the pass allows it
     if (NS == 1) ap1t<RB, I>(v0, mc);
     else bw1t<RB, I, COMP>(v0, v1, mc, np, ck, acc);
+    return;
+  }
+  if (KIND == 0 && k < kscaled) {
+    if (NS == 1) ap1tc<RB, I>(v0, mc);
+    else bw1tc<RB, I, COMP>(v0, v1, mc, np, gk, ck, acc);
     return;
   }
   constexpr int I2 = (KIND == 2 && I + 1 < RB) ? I : 0;
@@ -349,14 +464,19 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   // tile's copy as soon as every thread holds its last-round elements
   const bool dstore = P.store && !P.scatter;
   const bool early = NS == 2 && nst == 1 && dstore && RB == 4;
-  // real passes: switch the records to the scaled form (ops below kscaled)
+  // single-qubit passes: switch the records to the scaled form (ops below
+  // kscaled)
   __shared__ int s_kscaled;
-  if (KIND == 1) {
+  if (KIND == 1 || KIND == 0) {
     __syncthreads();  // the records are staged
-    if (threadIdx.x == 0) s_kscaled = scale_real_records<NS == 1>(sco, P.nops, op_nco) ? P.nops - 1 : 0;
+    if (threadIdx.x == 0) {
+      const bool ok = KIND == 1 ? scale_real_records<NS == 1>(sco, P.nops, op_nco)
+                                : scale_complex_records<NS == 1>(sco, P.nops, op_nco);
+      s_kscaled = ok ? P.nops - 1 : 0;
+    }
   }
   __syncthreads();
-  const int kscaled = KIND == 1 ? s_kscaled : 0;
+  const int kscaled = (KIND == 1 || KIND == 0) ? s_kscaled : 0;
 
   unsigned pending = 0, phase = 0;
   auto issue = [&](long long f, int s) {  // thread 0
