@@ -128,10 +128,11 @@ typedef struct {
    * QC_C128; backward 12 / 10; allowed 6 .. 13 / 12 forward, 6 .. 12 / 11
    * backward).  reg_bits_*: index bits held in registers per round (1 .. 4;
    * defaults 4, except in the backward: 3 for QC_C128, and one less again
-   * for the passes of complex single-qubit layers and of parametrised brick
-   * layers (3 for QC_C64, 2 for QC_C128; in QC_C128 every brick layer takes
-   * 2); the planner raises it where a pass needs
-   * more: two for brick layers, and at most eight rounds per pass).
+   * for the passes of complex single-qubit layers (3 for QC_C64, 2 for
+   * QC_C128) and, in QC_C128, of every brick layer (2); the planner raises
+   * it where a pass needs more: two for brick layers, and at most eight
+   * rounds per pass; a QC_C64 brick pass whose pairs start at odd bits takes
+   * 3 where 4 would keep it from TMA staging).
    * stages_*: shared-memory tile buffers per CTA (1, 2 or 3; default 2, 1 for
    * the QC_C64 backward; 3 only
    * where two CTAs per SM still fit; with 1 the CTAs of an SM overlap each

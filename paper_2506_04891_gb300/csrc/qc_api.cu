@@ -257,17 +257,18 @@ int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 // 256-thread CTA has work at 4 bits.
 // Default register bits: 4 forward.  Backward: 4 (complex64) or 3
 // (complex128), one less for the passes whose gate math needs the most
-// registers per amplitude: complex-matrix single-qubit layers, parametrised
-// brick layers and, in complex128, every brick layer (measured faster on the
-// IBM and IonQ native-gate circuits; real RY layers, and fixed brick layers
-// in complex64, keep the larger count).
+// registers per amplitude: complex-matrix single-qubit layers and, in
+// complex128, every brick layer (measured faster on the IBM and IonQ
+// native-gate circuits; real RY layers and, in complex64, brick layers keep
+// the larger count: the MS backward's two-nonzero rows and generator-phase
+// gradients fit four bits, two gates per round).
 int reg_bits(const qc_circuit* c, int ns, const LayerInfo* L = nullptr) {
   if (ns == 1 && c->opt.reg_bits_fwd > 0) return c->opt.reg_bits_fwd;
   if (ns == 2 && c->opt.reg_bits_bwd > 0) return c->opt.reg_bits_bwd;
   if (ns != 2) return 4;
   const int base = c->dtype == QC_C128 ? 3 : 4;
   if (L && L->cls == LC_ROT1 && !L->real) return base - 1;
-  if (L && L->cls == LC_DENSE2 && (c->dtype == QC_C128 || (L->diff && L->nparams > 0))) return base - 1;
+  if (L && L->cls == LC_DENSE2 && c->dtype == QC_C128) return base - 1;
   return base;
 }
 
@@ -315,6 +316,8 @@ struct PassOpInfo {
 // entry {pass, slot, parameter index, companion} per gradient slot.  `comp`
 // (backward, ROT1 only): the preceding RX / RY layer, whose gradients the ops
 // also produce (companion slots follow the pass's own slots).
+bool tma_rounds_conflict_free(const TilePass& P, int rb);
+bool tma_enabled(const qc_circuit* c);
 std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, int ns,
                                       std::vector<std::vector<int>>& pidx_per_slot,
                                       const LayerInfo* comp = nullptr) {
@@ -401,44 +404,64 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
       continue;
     }
     // rounds of RB register bits
-    const int RB = pass_rb(c, L, ns, P.t);
-    std::vector<int> assigned(ops.size(), 0);
+    int RB = pass_rb(c, L, ns, P.t);
+    std::vector<int> assigned;
     int nass = 0, nr = 0;
     std::vector<TileOp> ordered;
     std::vector<std::vector<int>> ordered_pidx;
     std::vector<int> ordered_cpidx;
-    P.rop[0] = 0;
-    while (nass < (int)ops.size()) {
-      int lo = 1 << 30;
-      for (size_t k = 0; k < ops.size(); ++k)
-        if (!assigned[k]) lo = std::min(lo, (int)ops[k].op.l);
-      lo = std::min(lo, P.t - RB);
-      const int hi = lo + RB;
-      int got = 0;
-      // a round's ops in increasing bit order (the TMA pass numbers them so)
-      std::vector<size_t> in_round;
-      for (size_t k = 0; k < ops.size(); ++k) {
-        if (assigned[k]) continue;
-        const int top = ops[k].op.l + (ops[k].op.is2q ? 1 : 0);
-        if (ops[k].op.l >= lo && top < hi) {
-          assigned[k] = 1;
-          ++nass;
-          ++got;
-          in_round.push_back(k);
+    auto place = [&](int rb) {
+      assigned.assign(ops.size(), 0);
+      nass = nr = 0;
+      ordered.clear();
+      ordered_pidx.clear();
+      ordered_cpidx.clear();
+      P.rop[0] = 0;
+      while (nass < (int)ops.size()) {
+        int lo = 1 << 30;
+        for (size_t k = 0; k < ops.size(); ++k)
+          if (!assigned[k]) lo = std::min(lo, (int)ops[k].op.l);
+        lo = std::min(lo, P.t - rb);
+        const int hi = lo + rb;
+        int got = 0;
+        // a round's ops in increasing bit order (the TMA pass numbers them so)
+        std::vector<size_t> in_round;
+        for (size_t k = 0; k < ops.size(); ++k) {
+          if (assigned[k]) continue;
+          const int top = ops[k].op.l + (ops[k].op.is2q ? 1 : 0);
+          if (ops[k].op.l >= lo && top < hi) {
+            assigned[k] = 1;
+            ++nass;
+            ++got;
+            in_round.push_back(k);
+          }
         }
+        std::stable_sort(in_round.begin(), in_round.end(),
+                         [&](size_t x, size_t y) { return ops[x].op.l < ops[y].op.l; });
+        for (size_t k : in_round) {
+          ordered.push_back(ops[k].op);
+          ordered_pidx.push_back(ops[k].pidx);
+          ordered_cpidx.push_back(ops[k].cpidx);
+        }
+        if (!got || nr >= kMaxRounds) break;  // the check below turns this into an error
+        P.rlo[nr] = (int8_t)lo;
+        ++nr;
+        P.rop[nr] = (int16_t)ordered.size();
       }
-      std::stable_sort(in_round.begin(), in_round.end(),
-                       [&](size_t x, size_t y) { return ops[x].op.l < ops[y].op.l; });
-      for (size_t k : in_round) {
-        ordered.push_back(ops[k].op);
-        ordered_pidx.push_back(ops[k].pidx);
-        ordered_cpidx.push_back(ops[k].cpidx);
-      }
-      if (!got || nr >= kMaxRounds) break;  // the check below turns this into an error
-      P.rlo[nr] = (int8_t)lo;
-      ++nr;
-      P.rop[nr] = (int16_t)ordered.size();
+      P.nrounds = nr;
+      return nass == (int)ops.size();
+    };
+    place(RB);
+    if (L.cls == LC_DENSE2 && RB == 4 && tma_enabled(c) && P.t == 12 && nass == (int)ops.size() &&
+        !tma_rounds_conflict_free(P, 4)) {
+      // pairs at odd local bits put round 0 at bit 1, where four register
+      // bits leave bit 7 as a lane bit and the TMA tile's shared-memory reads
+      // conflict; three register bits keep the lanes on bits 0 and 4..6, so
+      // the pass can be staged by TMA
+      if (place(3) && tma_rounds_conflict_free(P, 3)) RB = 3;
+      else place(RB);
     }
+    P.rb = RB;
     if (nass < (int)ops.size()) g_plan_unplaced = true;
     P.nrounds = nr;
     P.nops = (int)ordered.size();
@@ -738,7 +761,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       std::vector<Step> v;
       for (auto& tp : plan_tile_layer(c, Li, ns, pslots, comp)) {
         Step st;
-        st.type = ST_TILE; st.ns = ns; st.tp = tp; st.rb = pass_rb(c, Li, ns, tp.t);
+        st.type = ST_TILE; st.ns = ns; st.tp = tp; st.rb = tp.rb;
         st.cps = pass_cps(c, batch, tp, ns);
         v.push_back(st);
       }
@@ -818,7 +841,10 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
             Step& f0 = h.steps.front();
             TilePass& tp = f0.tp;
             // a contiguous pass of 2^9 .. 2^12 amplitudes (2 .. 16 per thread);
-            // the kernel's pre variant is built for 3 and 4 register bits
+            // the kernel's pre variant is built for 3 and 4 register bits (its
+            // TMA form for 4 only; a complex64 pass at 3 bits fused with
+            // per-thread copies measured as fast as a diagonal pass plus a TMA
+            // tile pass)
             if (tp.c == tp.t && tp.nrounds > 0 && tp.t >= 9 && tp.t <= 12 && (f0.rb == 3 || f0.rb == 4) &&
                 (Li.zmode == Z_IDENT || Li.zmode == Z_RINGXOR)) {
               tp.pre = 1;

@@ -106,6 +106,7 @@ struct TilePass {
   // op on register bit i of round r (lower bit for two-qubit ops), -1 if none
   int8_t rbit[kMaxRounds][5];
   int kind;                          // 0: complex 1q, 1: real 1q, 2: two-qubit (uniform per pass)
+  int rb;                            // register bits per round the rounds were planned for
   // fused neighbours (forward unless noted)
   int gather;        // 1: load psi[f^-1(k)] (a CNOT ring applied before this pass's gates)
   int scatter;       // 1: store to f^-1(k) (backward: inverse CNOT ring after this pass)
