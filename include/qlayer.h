@@ -128,8 +128,9 @@ typedef struct {
    * QC_C128; backward 12 / 10; allowed 6 .. 13 / 12 forward, 6 .. 12 / 11
    * backward).  reg_bits_*: index bits held in registers per round (1 .. 4;
    * defaults 4, except in the backward: 3 for QC_C128, and one less again
-   * for the passes of complex single-qubit layers (3 for QC_C64, 2 for
-   * QC_C128) and, in QC_C128, of every brick layer (2); the planner raises
+   * for the passes of complex single-qubit layers (3 for QC_C64 where the
+   * layer has gradients, 2 for QC_C128) and, in QC_C128, of every brick
+   * layer (2); the planner raises
    * it where a pass needs more: two for brick layers, and at most eight
    * rounds per pass; a QC_C64 brick pass whose pairs start at odd bits takes
    * 3 where 4 would keep it from TMA staging).

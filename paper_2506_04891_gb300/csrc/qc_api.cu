@@ -257,9 +257,10 @@ int contig_bits(const qc_circuit* c) { return c->dtype == QC_C64 ? 3 : 2; }
 // 256-thread CTA has work at 4 bits.
 // Default register bits: 4 forward.  Backward: 4 (complex64) or 3
 // (complex128), one less for the passes whose gate math needs the most
-// registers per amplitude: complex-matrix single-qubit layers and, in
-// complex128, every brick layer (measured faster on the IBM and IonQ
-// native-gate circuits; real RY layers and, in complex64, brick layers keep
+// registers per amplitude: complex-matrix single-qubit layers with gradients
+// (in complex128 all of them) and, in complex128, every brick layer
+// (measured faster on the IBM and IonQ native-gate circuits; real RY layers,
+// constant complex layers such as SX and, in complex64, brick layers keep
 // the larger count: the MS backward's two-nonzero rows and generator-phase
 // gradients fit four bits, two gates per round).
 int reg_bits(const qc_circuit* c, int ns, const LayerInfo* L = nullptr) {
@@ -267,7 +268,7 @@ int reg_bits(const qc_circuit* c, int ns, const LayerInfo* L = nullptr) {
   if (ns == 2 && c->opt.reg_bits_bwd > 0) return c->opt.reg_bits_bwd;
   if (ns != 2) return 4;
   const int base = c->dtype == QC_C128 ? 3 : 4;
-  if (L && L->cls == LC_ROT1 && !L->real) return base - 1;
+  if (L && L->cls == LC_ROT1 && !L->real && (c->dtype == QC_C128 || (L->diff && L->nparams > 0))) return base - 1;
   if (L && L->cls == LC_DENSE2 && c->dtype == QC_C128) return base - 1;
   return base;
 }

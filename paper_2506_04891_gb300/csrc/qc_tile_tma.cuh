@@ -187,10 +187,12 @@ __device__ __forceinline__ void bw1t(float2* p, float2* l, const float* m, int n
 // gf = |product of the factors so far|^2 and the record's A (unchanged) for
 // the gradient.  The product C of the omitted factors multiplies the last
 // gate's M (not its A), so the pass's outputs are exact.
-template <int RB, int I>
+// FIXED: every scaled record of the pass is tau0 = tau1 = -i (SX, RX(pi/2),
+// GPI2(0): constant gates without gradients), so the gate is additions only.
+template <int RB, int I, bool FIXED = false>
 __device__ __forceinline__ void ap1tc(float2* v, const float* m) {
-  float2 t0, t1;
-  ldc2<float>(m, t0, t1);
+  float2 t0 = make_float2(0.f, -1.f), t1 = make_float2(0.f, -1.f);
+  if (!FIXED) ldc2<float>(m, t0, t1);
 #pragma unroll
   for (int a = 0; a < (1 << RB); ++a)
     if (!(a & (1 << I))) {
@@ -199,14 +201,15 @@ __device__ __forceinline__ void ap1tc(float2* v, const float* m) {
       v[a | (1 << I)] = cfma<float>(t1, x0, x1);
     }
 }
-template <int RB, int I, bool MAYCK>
-__device__ __forceinline__ void bw1tc(float2* p, float2* l, const float* m, int np, int gk, int ck_in,
+template <int RB, int I, bool MAYCK, bool FIXED = false>
+__device__ __forceinline__ void bw1tc(float2* p, float2* l, const float* m, int np_in, int gk, int ck_in,
                                       float* acc) {
   using C = float2;
-  const int ck = MAYCK ? ck_in : 0;
-  C s0, s1, a00, a01, a10, a11;
-  ldc2<float>(m, s0, s1);
-  const float gf = m[4];
+  const int ck = MAYCK && !FIXED ? ck_in : 0;
+  const int np = FIXED ? 0 : np_in;
+  C s0 = make_float2(0.f, -1.f), s1 = make_float2(0.f, -1.f), a00, a01, a10, a11;
+  if (!FIXED) ldc2<float>(m, s0, s1);
+  const float gf = FIXED ? 1.f : m[4];
   if (np && gk != 1) {
     ldc2<float>(m + 8, a00, a01);
     ldc2<float>(m + 12, a10, a11);
@@ -327,6 +330,7 @@ __device__ bool scale_real_records(float* sco, int nops, int nco) {
 // block follow from the round's presence mask without per-op lookups.
 template <int NS, int RB, int KIND, int I, bool COMP>
 __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, int pat, int kscaled,
+                                        bool fixed,
                                         float2* v0, float2* v1, const float* sco, float* acc) {
   using R = float;
   if (KIND == 2 && I + 1 >= RB) return;
@@ -339,8 +343,13 @@ __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np,
     return;
   }
   if (KIND == 0 && k < kscaled) {
-    if (NS == 1) ap1tc<RB, I>(v0, mc);
-    else bw1tc<RB, I, COMP>(v0, v1, mc, np, gk, ck, acc);
+    if (fixed) {
+      if (NS == 1) ap1tc<RB, I, true>(v0, mc);
+      else bw1tc<RB, I, false, true>(v0, v1, mc, 0, 0, 0, acc);
+    } else {
+      if (NS == 1) ap1tc<RB, I>(v0, mc);
+      else bw1tc<RB, I, COMP>(v0, v1, mc, np, gk, ck, acc);
+    }
     return;
   }
   constexpr int I2 = (KIND == 2 && I + 1 < RB) ? I : 0;
@@ -466,17 +475,25 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   const bool early = NS == 2 && nst == 1 && dstore && RB == 4;
   // single-qubit passes: switch the records to the scaled form (ops below
   // kscaled)
-  __shared__ int s_kscaled;
+  __shared__ int s_kscaled, s_fixed;
   if (KIND == 1 || KIND == 0) {
     __syncthreads();  // the records are staged
     if (threadIdx.x == 0) {
       const bool ok = KIND == 1 ? scale_real_records<NS == 1>(sco, P.nops, op_nco)
                                 : scale_complex_records<NS == 1>(sco, P.nops, op_nco);
       s_kscaled = ok ? P.nops - 1 : 0;
+      // constant complex gates whose scaled records are all -i: additions only
+      bool fx = KIND == 0 && ok && op_np == 0 && op_ck == 0;
+      for (int k = 0; fx && k + 1 < P.nops; ++k) {
+        const float* r = sco + op_nco * k;
+        fx = r[0] == 0.f && r[1] == -1.f && r[2] == 0.f && r[3] == -1.f;
+      }
+      s_fixed = fx ? 1 : 0;
     }
   }
   __syncthreads();
   const int kscaled = (KIND == 1 || KIND == 0) ? s_kscaled : 0;
+  const bool kfixed = KIND == 0 && s_fixed != 0;
 
   unsigned pending = 0, phase = 0;
   auto issue = [&](long long f, int s) {  // thread 0
@@ -613,15 +630,15 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
           __syncthreads();
           if (threadIdx.x == 0 && f + cps < tps) issue(f + cps, 0);
         }
-        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1, sco, acc);
+        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1, sco, acc);
         if (RB > 1)
-          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1,
                                                        sco, acc);
         if (RB > 2)
-          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1,
                                                        sco, acc);
         if (RB > 3)
-          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1,
                                                        sco, acc);
         if (NS == 1 && PRE >= 2 && fpost_ok && last) {
           // group g = tid holds local indices g | a << 8 of a contiguous pass:
