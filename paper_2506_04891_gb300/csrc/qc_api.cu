@@ -487,6 +487,7 @@ std::vector<TilePass> plan_tile_layer(const qc_circuit* c, const LayerInfo& L, i
     P.nslots = slot;
     P.store = 1;
     P.kind = L.cls == LC_DENSE2 ? 2 : (L.real ? 1 : 0);
+    P.sx = (L.kind == QC_L_SX && P.ncomp == 0) ? 1 : 0;
     for (int r = 0; r < kMaxRounds; ++r)
       for (int i = 0; i < 5; ++i) P.rbit[r][i] = -1;
     for (int k = 0, r = 0; k < P.nops; ++k) {

@@ -337,6 +337,19 @@ __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np,
   if (!((rmask >> I) & 1u)) return;
   const int k = k0 + __popc(rmask & ((1u << I) - 1u));
   const R* mc = sco + k * nco;
+  if (KIND == 3) {
+    // constant -i butterflies (SX) without gradients: additions only in
+    // scaled form, the last op (or every op, if the records did not scale)
+    // in full form
+    if (k < kscaled) {
+      if (NS == 1) ap1tc<RB, I, true>(v0, mc);
+      else bw1tc<RB, I, false, true>(v0, v1, mc, 0, 0, 0, acc);
+    } else {
+      if (NS == 1) ap1<float, RB, I>(v0, mc, 0);
+      else bw1<float, RB, I, false>(v0, v1, mc, 0, 0, 0, 0, acc);
+    }
+    return;
+  }
   if (KIND == 1 && k < kscaled) {  // scaled form: every op before the last when the pass allows it
     if (NS == 1) ap1t<RB, I>(v0, mc);
     else bw1t<RB, I, COMP>(v0, v1, mc, np, ck, acc);
@@ -475,24 +488,37 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   const bool early = NS == 2 && nst == 1 && dstore && RB == 4;
   // single-qubit passes: switch the records to the scaled form (ops below
   // kscaled)
+  // (KIND 3: constant -i butterflies, scaled only when every record is -i)
   __shared__ int s_kscaled, s_fixed;
-  if (KIND == 1 || KIND == 0) {
+  if (KIND == 1 || KIND == 0 || KIND == 3) {
     __syncthreads();  // the records are staged
     if (threadIdx.x == 0) {
-      const bool ok = KIND == 1 ? scale_real_records<NS == 1>(sco, P.nops, op_nco)
-                                : scale_complex_records<NS == 1>(sco, P.nops, op_nco);
-      s_kscaled = ok ? P.nops - 1 : 0;
-      // constant complex gates whose scaled records are all -i: additions only
-      bool fx = KIND == 0 && ok && op_np == 0 && op_ck == 0;
-      for (int k = 0; fx && k + 1 < P.nops; ++k) {
-        const float* r = sco + op_nco * k;
-        fx = r[0] == 0.f && r[1] == -1.f && r[2] == 0.f && r[3] == -1.f;
+      bool ok, fx;
+      if (KIND == 3) {
+        // the raw records must be d (I - i X) (M01 = M10 = -i M00, M11 =
+        // M00) before they are rewritten; otherwise every op runs in full form
+        fx = op_np == 0 && op_ck == 0;
+        for (int k = 0; fx && k < P.nops; ++k) {
+          const float* r = sco + op_nco * k;
+          fx = r[6] == r[0] && r[7] == r[1] && r[2] == r[1] && r[3] == -r[0] && r[4] == r[1] && r[5] == -r[0];
+        }
+        ok = fx && scale_complex_records<NS == 1>(sco, P.nops, op_nco);
+      } else {
+        ok = KIND == 1 ? scale_real_records<NS == 1>(sco, P.nops, op_nco)
+                       : scale_complex_records<NS == 1>(sco, P.nops, op_nco);
+        // constant complex gates whose scaled records are all -i: additions only
+        fx = KIND == 0 && ok && op_np == 0 && op_ck == 0;
+        for (int k = 0; fx && k + 1 < P.nops; ++k) {
+          const float* r = sco + op_nco * k;
+          fx = r[0] == 0.f && r[1] == -1.f && r[2] == 0.f && r[3] == -1.f;
+        }
       }
       s_fixed = fx ? 1 : 0;
+      s_kscaled = ok ? P.nops - 1 : 0;
     }
   }
   __syncthreads();
-  const int kscaled = (KIND == 1 || KIND == 0) ? s_kscaled : 0;
+  const int kscaled = (KIND == 1 || KIND == 0 || KIND == 3) ? s_kscaled : 0;
   const bool kfixed = KIND == 0 && s_fixed != 0;
 
   unsigned pending = 0, phase = 0;

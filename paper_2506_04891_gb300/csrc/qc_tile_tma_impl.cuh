@@ -48,7 +48,7 @@ template <int NS, int RB, int KIND, int PRE>
 static cudaError_t launch_tma_k(const TilePass& P, int batch, int cps, const void* coef, const void* s0,
                                 void* d0, const void* s1, void* d1, double* part, cudaStream_t st) {
   // companion gradients only occur in backward single-qubit passes
-  constexpr bool kMayComp = NS == 2 && KIND != 2;
+  constexpr bool kMayComp = NS == 2 && KIND != 2 && KIND != 3;
   const bool comp = kMayComp && P.ncomp > 0;
   CUtensorMap tm0, tm1;
   cudaError_t e = make_tile_map(&tm0, s0, P, batch);
@@ -69,8 +69,8 @@ static cudaError_t launch_tma_k(const TilePass& P, int batch, int cps, const voi
 }
 
 // Kinds and register bits the TMA pass is built for: single-qubit layers
-// (complex, real) at 3 or 4 register bits, brick layers at 2 .. 4; the fused
-// diagonal variants at 4.
+// (complex, real, constant SX) at 3 or 4 register bits, brick layers at
+// 2 .. 4; the fused diagonal variants at 4.
 template <int NS>
 static cudaError_t launch_tma_ns(const TilePass& P, int rb, int batch, int cps, const void* coef, const void* s0,
                                  void* d0, const void* s1, void* d1, double* part, cudaStream_t st) {
@@ -85,20 +85,24 @@ static cudaError_t launch_tma_ns(const TilePass& P, int rb, int batch, int cps, 
     return cudaErrorInvalidValue;
   }
   const bool diag = NS == 2 ? P.pre != 0 : P.post != 0;
+  // constant SX passes run the additions-only variant (kind 3)
+  const bool sx = P.kind == 0 && P.sx;
   if (diag) {
     if (rb != 4) return cudaErrorInvalidValue;
     const bool ring = (NS == 2 ? P.pre_zmode : P.post_zmode) == Z_RINGXOR;
     // backward 1 / 2 identity / ring; forward 3 / 2 identity / ring
     if constexpr (NS == 2) {
       if (P.kind == 1) return ring ? QC_TMA_L(4, 1, 2) : QC_TMA_L(4, 1, 1);
+      if (sx) return ring ? QC_TMA_L(4, 3, 2) : QC_TMA_L(4, 3, 1);
       return ring ? QC_TMA_L(4, 0, 2) : QC_TMA_L(4, 0, 1);
     } else {
       if (P.kind == 1) return ring ? QC_TMA_L(4, 1, 2) : QC_TMA_L(4, 1, 3);
+      if (sx) return ring ? QC_TMA_L(4, 3, 2) : QC_TMA_L(4, 3, 3);
       return ring ? QC_TMA_L(4, 0, 2) : QC_TMA_L(4, 0, 3);
     }
   }
-  if (rb == 3) return P.kind == 1 ? QC_TMA_L(3, 1, 0) : QC_TMA_L(3, 0, 0);
-  if (rb == 4) return P.kind == 1 ? QC_TMA_L(4, 1, 0) : QC_TMA_L(4, 0, 0);
+  if (rb == 3) return P.kind == 1 ? QC_TMA_L(3, 1, 0) : sx ? QC_TMA_L(3, 3, 0) : QC_TMA_L(3, 0, 0);
+  if (rb == 4) return P.kind == 1 ? QC_TMA_L(4, 1, 0) : sx ? QC_TMA_L(4, 3, 0) : QC_TMA_L(4, 0, 0);
 #undef QC_TMA_L
   return cudaErrorInvalidValue;
 }
