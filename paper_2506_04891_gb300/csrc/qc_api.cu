@@ -231,18 +231,32 @@ int sm_count() {
   return cached;
 }
 
-// CTAs per sample of a persistent tile pass: as many as the SMs hold at the
+// CTAs per sample of a persistent tile pass.  The slots are the SMs times the
 // pass's residency (its compiled CTAs per SM, fewer if its shared memory does
-// not fit that many), rounded down so the whole grid is resident at once: a
-// batch that does not divide the slots would otherwise leave a second wave of
-// up to batch - 1 CTAs that starts when the first one ends (32 samples at
-// two CTAs per SM: 320 CTAs for 304 slots before, 288 now).
+// not fit that many); each CTA walks its sample's tiles with a stride of the
+// CTAs per sample c, so a pass takes about ceil(B c / slots) waves of
+// ceil(tiles / c) tile times plus a per-CTA fixed cost (staging, the final
+// reductions: about two tile times).  c minimises that: a batch that does not
+// divide the slots would otherwise leave a nearly empty last wave (32
+// samples: 288 CTAs, not 320 for 304 slots) or idle slots (200 samples of
+// 2^24 amplitudes: three CTAs per sample in two full waves, 1.5x faster than
+// one CTA per sample).
 int tile_cps(int batch, int n, int t, int resident) {
   const long long tps = 1LL << (n - t);
-  long long c = ((long long)resident * sm_count()) / batch;
-  if (c > tps) c = tps;
-  if (c < 1) c = 1;
-  return (int)c;
+  const long long slots = std::max<long long>(1, (long long)resident * sm_count());
+  constexpr long long kCtaFixedTiles = 2;
+  long long best = 1;
+  long long best_cost = -1;
+  const long long cmax = std::min<long long>(tps, 4096);
+  for (long long c = 1; c <= cmax; ++c) {
+    const long long waves = ((long long)batch * c + slots - 1) / slots;
+    const long long cost = waves * ((tps + c - 1) / c + kCtaFixedTiles);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return (int)best;
 }
 int pass_cps(const qc_circuit* c, int batch, const TilePass& tp, int ns) {
   const int rs = (int)c->rsize;
