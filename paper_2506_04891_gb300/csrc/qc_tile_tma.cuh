@@ -123,13 +123,16 @@ constexpr int tma_minb(int ns, int kind) { return (ns == 1 && kind == 1) ? 3 : 2
 // Givens" rotation, Gentleman 1973): with c = M00 = M11, the rotation of a
 // pair is c * (x0 + tau0 x1, x1 + tau1 x0), so a gate costs one packed FMA
 // per output when the factor c is carried along instead of applied.  Every
-// gate of a pass but the last runs in this form (its record holds tau0,
-// tau1 and the gradient factor gf); the product C of the omitted factors
-// multiplies the last gate's matrix, so the pass's outputs are exact.  Between
-// gates the held amplitudes of psi and lambda are the true ones divided by
-// the product of the factors so far, so a gate's gradient products carry that
-// product squared, which gf (the product squared, including the gate's own
-// factor) puts back.  The forward applies M, the backward M^T.
+// gate of the pass runs in this form (its record holds tau0, tau1 and the
+// gradient factor gf), and after the pass's last gate the held amplitudes are
+// multiplied by the product C of the factors, so the outputs are exact.
+// Between gates the held amplitudes of psi and lambda are the true ones
+// divided by the product of the factors so far, so a gate's gradient products
+// carry that product squared, which gf (the product squared, including the
+// gate's own factor) puts back.  The forward applies M, the backward M^T.
+// The form is chosen per pass, so the round loop is compiled once per form
+// with no per-gate branch between them (a per-gate choice had the compiler
+// reconcile the two forms' registers with moves after every gate).
 template <int RB, int I>
 __device__ __forceinline__ void ap1t(float2* v, const float* m) {
   float t0, t1, gf, unused;
@@ -185,8 +188,8 @@ __device__ __forceinline__ void bw1t(float2* p, float2* l, const float* m, int n
 // tau1 x0.  Backward (M^dagger = conj(d) (I + T^dagger)): (sig0, sig1) =
 // (M10 / d, M01 / d), y0 = x0 + conj(sig0) x1, y1 = x1 + conj(sig1) x0, then
 // gf = |product of the factors so far|^2 and the record's A (unchanged) for
-// the gradient.  The product C of the omitted factors multiplies the last
-// gate's M (not its A), so the pass's outputs are exact.
+// the gradient.  After the last gate the held amplitudes are multiplied by
+// the product C of the factors (backward: its conjugate).
 // FIXED: every scaled record of the pass is tau0 = tau1 = -i (SX, RX(pi/2),
 // GPI2(0): constant gates without gradients), so the gate is additions only.
 template <int RB, int I, bool FIXED = false>
@@ -243,17 +246,18 @@ __device__ __forceinline__ void bw1tc(float2* p, float2* l, const float* m, int 
 }
 
 // Rewrites a complex pass's staged records for the scaled form (one thread,
-// per CTA), under the same conditions as the real one below (every factor
-// but the last op's with |d| >= 2^-10, their product >= 2^-60 in magnitude)
-// and with M11 == M00 exactly; else returns false and leaves them.  The
-// ratios and the running product are formed in FP64 from the staged FP32
-// entries and rounded once (in FP32 their three roundings per ratio left the
-// pass's output norm off by ~5e-7 on a 12-gate pass, 8x the full form's).
+// per CTA), when every factor has |d| >= 2^-10, their running product stays
+// >= 2^-60 in magnitude and M11 == M00 exactly; else returns false and leaves
+// them.  *corr gets the factor the held amplitudes take after the last gate:
+// C forward, conj(C) backward.  The ratios and the running product are formed
+// in FP64 from the staged FP32 entries and rounded once (in FP32 their three
+// roundings per ratio left the pass's output norm off by ~5e-7 on a 12-gate
+// pass, 8x the full form's).
 template <bool FWD>
-__device__ bool scale_complex_records(float* sco, int nops, int nco) {
-  if (nops < 2 || nco != (FWD ? 8 : 16)) return false;
+__device__ bool scale_complex_records(float* sco, int nops, int nco, float2* corr) {
+  if (nops < 1 || nco != (FWD ? 8 : 16)) return false;
   double cr = 1.0, ci = 0.0;
-  for (int k = 0; k + 1 < nops; ++k) {
+  for (int k = 0; k < nops; ++k) {
     const float* r = sco + nco * k;
     if (r[6] != r[0] || r[7] != r[1]) return false;
     const double dr = r[0], di = r[1];
@@ -265,7 +269,7 @@ __device__ bool scale_complex_records(float* sco, int nops, int nco) {
   }
   cr = 1.0;
   ci = 0.0;
-  for (int k = 0; k + 1 < nops; ++k) {
+  for (int k = 0; k < nops; ++k) {
     float* r = sco + nco * k;
     const double dr = r[0], di = r[1], inv = 1.0 / (dr * dr + di * di);
     const double nr = cr * dr - ci * di, ni = cr * di + ci * dr;
@@ -282,12 +286,7 @@ __device__ bool scale_complex_records(float* sco, int nops, int nco) {
     r[4] = (float)(cr * cr + ci * ci);
     r[5] = r[6] = r[7] = 0.f;
   }
-  float* r = sco + nco * (nops - 1);
-  for (int j = 0; j < 4; ++j) {
-    const double xr = r[2 * j], xi = r[2 * j + 1];
-    r[2 * j] = (float)(cr * xr - ci * xi);
-    r[2 * j + 1] = (float)(cr * xi + ci * xr);
-  }
+  *corr = make_float2((float)cr, (float)(FWD ? ci : -ci));
   return true;
 }
 
@@ -296,12 +295,13 @@ __device__ bool scale_complex_records(float* sco, int nops, int nco) {
 // records as they are, when a factor is small (|c| < 2^-10) or their product
 // would leave the normal range (< 2^-60); the pass then runs every gate in
 // full form.  FWD: records become (M01 / M00, M10 / M11, gf, 0), else
-// (M10 / M00, M01 / M11, gf, 0); the last op's record is multiplied by C.
+// (M10 / M00, M01 / M11, gf, 0); *corr = (C, 0).  Ratios and product in FP64,
+// rounded once (as above).
 template <bool FWD>
-__device__ bool scale_real_records(float* sco, int nops, int nco) {
-  if (nops < 2 || nco != 4) return false;
-  double cacc = 1.0;  // ratios and product in FP64, rounded once (as above)
-  for (int k = 0; k + 1 < nops; ++k) {
+__device__ bool scale_real_records(float* sco, int nops, int nco, float2* corr) {
+  if (nops < 1 || nco != 4) return false;
+  double cacc = 1.0;
+  for (int k = 0; k < nops; ++k) {
     const float* r = sco + 4 * k;
     const float cc = r[0];
     if (!(fabsf(cc) >= 0x1p-10f) || r[3] != cc) return false;
@@ -309,7 +309,7 @@ __device__ bool scale_real_records(float* sco, int nops, int nco) {
     if (!(fabs(cacc) >= 0x1p-60)) return false;
   }
   cacc = 1.0;
-  for (int k = 0; k + 1 < nops; ++k) {
+  for (int k = 0; k < nops; ++k) {
     float* r = sco + 4 * k;
     const double m00 = r[0], m01 = r[1], m10 = r[2], m11 = r[3];
     cacc *= m00;
@@ -318,8 +318,7 @@ __device__ bool scale_real_records(float* sco, int nops, int nco) {
     r[2] = (float)(cacc * cacc);
     r[3] = 0.f;
   }
-  float* r = sco + 4 * (nops - 1);
-  for (int j = 0; j < 4; ++j) r[j] = (float)(r[j] * cacc);
+  *corr = make_float2((float)cacc, 0.f);
   return true;
 }
 
@@ -328,20 +327,22 @@ __device__ bool scale_real_records(float* sco, int nops, int nco) {
 // pass stages the same number of coefficients (nco) and has the same
 // gradient count and generator kinds, so the op's index and coefficient
 // block follow from the round's presence mask without per-op lookups.
-template <int NS, int RB, int KIND, int I, bool COMP>
-__device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, int pat, int kscaled,
-                                        bool fixed,
-                                        float2* v0, float2* v1, const float* sco, float* acc) {
+// SC, the pass's form: 0 full matrices, 1 scaled (single-qubit kinds 0 and
+// 1), 2 scaled -i butterflies (kind 3: constant SX, additions only), -1 the
+// runtime flag sc_rt chooses between 1 and 0 (complex kind 0: a round loop
+// per form spilled registers there, the branch measured faster).
+template <int NS, int RB, int KIND, int I, bool COMP, int SC>
+__device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, int pat,
+                                        int sc_rt, float2* v0, float2* v1, const float* sco, float* acc) {
   using R = float;
   if (KIND == 2 && I + 1 >= RB) return;
   if (!((rmask >> I) & 1u)) return;
   const int k = k0 + __popc(rmask & ((1u << I) - 1u));
   const R* mc = sco + k * nco;
-  if (KIND == 3) {
-    // constant -i butterflies (SX) without gradients: additions only in
-    // scaled form, the last op (or every op, if the records did not scale)
-    // in full form
-    if (k < kscaled) {
+  if constexpr (KIND == 3) {
+    // constant SX without gradients: -i butterflies, or the full matrices
+    // when the records did not scale
+    if constexpr (SC == 2) {
       if (NS == 1) ap1tc<RB, I, true>(v0, mc);
       else bw1tc<RB, I, false, true>(v0, v1, mc, 0, 0, 0, acc);
     } else {
@@ -350,20 +351,17 @@ __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np,
     }
     return;
   }
-  if (KIND == 1 && k < kscaled) {  // scaled form: every op before the last when the pass allows it
+  if constexpr (SC == 1 && KIND == 1) {
     if (NS == 1) ap1t<RB, I>(v0, mc);
     else bw1t<RB, I, COMP>(v0, v1, mc, np, ck, acc);
     return;
   }
-  if (KIND == 0 && k < kscaled) {
-    if (fixed) {
-      if (NS == 1) ap1tc<RB, I, true>(v0, mc);
-      else bw1tc<RB, I, false, true>(v0, v1, mc, 0, 0, 0, acc);
-    } else {
+  if constexpr ((SC == 1 || SC == -1) && KIND == 0) {
+    if (SC == 1 || sc_rt) {
       if (NS == 1) ap1tc<RB, I>(v0, mc);
       else bw1tc<RB, I, COMP>(v0, v1, mc, np, gk, ck, acc);
+      return;
     }
-    return;
   }
   constexpr int I2 = (KIND == 2 && I + 1 < RB) ? I : 0;
   if (NS == 1) {
@@ -486,40 +484,36 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   // tile's copy as soon as every thread holds its last-round elements
   const bool dstore = P.store && !P.scatter;
   const bool early = NS == 2 && nst == 1 && dstore && RB == 4;
-  // single-qubit passes: switch the records to the scaled form (ops below
-  // kscaled)
-  // (KIND 3: constant -i butterflies, scaled only when every record is -i)
-  __shared__ int s_kscaled, s_fixed;
-  if (KIND == 1 || KIND == 0 || KIND == 3) {
+  // single-qubit passes: switch the records to the scaled form when every
+  // gate allows it (kind 3: when every raw record is d (I - i X), M01 = M10 =
+  // -i M00, M11 = M00); s_corr is the factor the held amplitudes take after
+  // the pass's last gate
+  __shared__ int s_sc;
+  __shared__ float2 s_corr;
+  if (KIND != 2) {
     __syncthreads();  // the records are staged
     if (threadIdx.x == 0) {
-      bool ok, fx;
+      float2 corr = make_float2(1.f, 0.f);
+      int sc = 0;
       if (KIND == 3) {
-        // the raw records must be d (I - i X) (M01 = M10 = -i M00, M11 =
-        // M00) before they are rewritten; otherwise every op runs in full form
-        fx = op_np == 0 && op_ck == 0;
+        bool fx = op_np == 0 && op_ck == 0;
         for (int k = 0; fx && k < P.nops; ++k) {
           const float* r = sco + op_nco * k;
           fx = r[6] == r[0] && r[7] == r[1] && r[2] == r[1] && r[3] == -r[0] && r[4] == r[1] && r[5] == -r[0];
         }
-        ok = fx && scale_complex_records<NS == 1>(sco, P.nops, op_nco);
+        if (fx && scale_complex_records<NS == 1>(sco, P.nops, op_nco, &corr)) sc = 2;
+      } else if (KIND == 1) {
+        if (scale_real_records<NS == 1>(sco, P.nops, op_nco, &corr)) sc = 1;
       } else {
-        ok = KIND == 1 ? scale_real_records<NS == 1>(sco, P.nops, op_nco)
-                       : scale_complex_records<NS == 1>(sco, P.nops, op_nco);
-        // constant complex gates whose scaled records are all -i: additions only
-        fx = KIND == 0 && ok && op_np == 0 && op_ck == 0;
-        for (int k = 0; fx && k + 1 < P.nops; ++k) {
-          const float* r = sco + op_nco * k;
-          fx = r[0] == 0.f && r[1] == -1.f && r[2] == 0.f && r[3] == -1.f;
-        }
+        if (scale_complex_records<NS == 1>(sco, P.nops, op_nco, &corr)) sc = 1;
       }
-      s_fixed = fx ? 1 : 0;
-      s_kscaled = ok ? P.nops - 1 : 0;
+      s_sc = sc;
+      s_corr = corr;
     }
   }
   __syncthreads();
-  const int kscaled = (KIND == 1 || KIND == 0 || KIND == 3) ? s_kscaled : 0;
-  const bool kfixed = KIND == 0 && s_fixed != 0;
+  const int pass_sc = KIND != 2 ? s_sc : 0;
+  const float2 corr = s_corr;
 
   unsigned pending = 0, phase = 0;
   auto issue = [&](long long f, int s) {  // thread 0
@@ -566,6 +560,9 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
     const int kb = tile_base(f);
     if (threadIdx.x == 0 && f + (long long)nst * cps < tps) prefetch(f + (long long)nst * cps);
 
+    // the round loop, compiled once per form of the pass
+    auto rounds = [&](auto form) {
+      constexpr int SC = decltype(form)::value;
 #pragma unroll 1
     for (int r = 0; r < P.nrounds; ++r) {
       const int lo = P.rlo[r];
@@ -656,16 +653,33 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
           __syncthreads();
           if (threadIdx.x == 0 && f + cps < tps) issue(f + cps, 0);
         }
-        tma_bit<NS, RB, KIND, 0, COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1, sco, acc);
+        tma_bit<NS, RB, KIND, 0, COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1, sco, acc);
         if (RB > 1)
-          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1,
-                                                       sco, acc);
+          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
+                                                           sco, acc);
         if (RB > 2)
-          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1,
-                                                       sco, acc);
+          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
+                                                           sco, acc);
         if (RB > 3)
-          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, kscaled, kfixed, v0, v1,
-                                                       sco, acc);
+          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
+                                                           sco, acc);
+        if ((SC > 0 || (SC < 0 && pass_sc)) && last) {
+          // the pass's gates are all applied: restore the product of the
+          // scaled form's factors (folded into the phase below where there
+          // is one)
+          if (!(NS == 1 && PRE >= 2 && fpost_ok)) {
+#pragma unroll
+            for (int a = 0; a < (1 << RB); ++a) {
+              if (KIND == 1) {
+                v0[a] = rmul<R>(corr.x, v0[a]);
+                if constexpr (NS == 2) v1[a] = rmul<R>(corr.x, v1[a]);
+              } else {
+                v0[a] = cmul<R>(corr, v0[a]);
+                if constexpr (NS == 2) v1[a] = cmul<R>(corr, v1[a]);
+              }
+            }
+          }
+        }
         if (NS == 1 && PRE >= 2 && fpost_ok && last) {
           // group g = tid holds local indices g | a << 8 of a contiguous pass:
           // z = z0 ^ z(a << 8) with the compile-time pattern a ^ (a << 1)
@@ -674,7 +688,8 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
           constexpr int semask = ((1 << nse) - 1) << zlo;
           const int z0 = ztrans32(kb | li, n, PRE == 2 ? Z_RINGXOR : Z_IDENT);
           const int z0se = (z0 >> zlo) & ((1 << nse) - 1);
-          const C p0 = diag_phase32<R>(fpost_tabs, P.post_tb, z0 & ~semask);
+          C p0 = diag_phase32<R>(fpost_tabs, P.post_tb, z0 & ~semask);
+          if (SC > 0 || (SC < 0 && pass_sc)) p0 = cmul<R>(p0, corr);
           const C* ratio = reinterpret_cast<const C*>(fph + ((sizeof(FwdPhaseMeta) + 15) & ~(size_t)15));
 #pragma unroll
           for (int a = 0; a < (1 << RB); ++a) {
@@ -769,6 +784,12 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
       }
       __syncthreads();
     }
+
+    };
+    if (KIND == 0) rounds(std::integral_constant<int, -1>{});
+    else if (KIND == 3 && pass_sc == 2) rounds(std::integral_constant<int, KIND == 3 ? 2 : 0>{});
+    else if (KIND == 1 && pass_sc == 1) rounds(std::integral_constant<int, KIND == 1 ? 1 : 0>{});
+    else rounds(std::integral_constant<int, 0>{});
 
     if (P.store && P.scatter) {
       // backward scatter through the CNOT ring's inverse map f^-1, in 16-byte
