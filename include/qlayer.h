@@ -115,8 +115,11 @@ typedef struct {
    * there instead of its uncomputed copy.  -1 = automatic (on for states of
    * 1 GiB or more), 0 = off. */
   int32_t ckpt_every;
-  /* 0 = automatic; 1 = whole circuit per sample in shared memory (n <= 13 for
-   * QC_C64 and n <= 12 for QC_C128); 2 = layer-by-layer HBM passes. */
+  /* 0 = automatic (the shared-memory path for n <= 10 with QC_C64 and n <= 8
+   * with QC_C128 at batch <= 128, where the layer path is launch-bound; the
+   * layer path otherwise); 1 = whole circuit per sample in shared memory
+   * (n <= 13 for QC_C64 and n <= 12 for QC_C128); 2 = layer-by-layer HBM
+   * passes. */
   int32_t path;
   /* Layer path: 1 (default) fuses what the planner can fuse (leading
    * single-qubit layers into the product-state init, <Z> into the last

@@ -554,6 +554,15 @@ bool smem_fits(const qc_circuit* c) {
   const int lim = c->dtype == QC_C64 ? 13 : 12;
   return c->n <= lim;
 }
+// The automatic choice: the whole-circuit shared-memory kernel (one CTA per
+// sample, one gate sweep and barrier per gate) wins only where the layer
+// path is launch-bound: measured on HEA circuits, 0.8-1.0x the layer path's
+// time for n <= 10 (complex64) / n <= 8 (complex128) at batch <= 64, slower
+// above (n = 12, batch 256: 1.5x complex64, 1.6x complex128; n = 13, 1.8x).
+bool smem_auto(const qc_circuit* c, int batch) {
+  const int lim = c->dtype == QC_C64 ? 10 : 8;
+  return c->n <= lim && batch <= 128;
+}
 
 void add_job(Plan& P, int kind, int source, long long part_off, long long nblk, int nvals,
              long long bps, const std::vector<OutMap>& outs) {
@@ -729,7 +738,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
 
   bool smem = false;
   if (c->opt.path == 1) smem = true;
-  else if (c->opt.path == 0) smem = smem_fits(c);
+  else if (c->opt.path == 0) smem = smem_auto(c, batch);
   p.smem = smem;
 
   size_t off = 0;

@@ -439,11 +439,19 @@ def test_backward_diagonal_layers_ride_in_the_next_tile_pass(q):
     assert "pre=1" not in plain
 
 
-def test_small_circuits_use_shared_memory_path(q):
-    for name in ("hea4", "hea12", "hea12_c128"):
+def test_automatic_path_takes_shared_memory_only_where_launch_bound(q):
+    """The whole-circuit shared-memory kernel for small states (hea4, and
+    n <= 10 / n <= 8 at batch <= 128), the layer path above (hea12 in both
+    precisions measured 1.5-1.6x faster on it)."""
+    expect = {"hea4": True, "hea12": False, "hea12_c128": False}
+    for name, smem in expect.items():
         cfg = W.WORKLOADS[name]
         desc, _ = _plan(q, cfg["n"], cfg["layers"](), dtype=cfg["dtype"], batch=cfg["batch"], path=0)
-        assert "path=smem" in desc.splitlines()[0]
+        assert ("path=smem" in desc.splitlines()[0]) == smem, (name, desc.splitlines()[0])
+    for n, dtype, B, smem in [(10, "c64", 64, True), (10, "c64", 256, False), (11, "c64", 1, False),
+                              (8, "c128", 128, True), (9, "c128", 4, False)]:
+        desc, _ = _plan(q, n, W.serving_circuit(n), dtype=dtype, batch=B, path=0)
+        assert ("path=smem" in desc.splitlines()[0]) == smem, (n, dtype, B)
 
 
 def test_forward_plan_ends_in_psi_out(q):
