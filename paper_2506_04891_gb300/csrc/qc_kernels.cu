@@ -708,13 +708,18 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
 // Reductions of per-CTA partials (fixed order, float64)
 // ---------------------------------------------------------------------------
 // rows: job j has batch * nvals rows starting at row0[j]; V[row] = sum of the
-// sample's CTAs' partials for that value.
+// sample's CTAs' partials for that value.  One warp per row (a row sums at
+// most a few dozen partials: one CTA per row left most of 10^5 CTAs idle on
+// batches of hundreds of samples).
 #if QC_INST_R != 8
 static __global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restrict__ jobs,
                                                    const long long* __restrict__ row0, int njobs,
-                                                   long long rowbase, const double* __restrict__ part,
-                                                   double* __restrict__ V) {
-  const long long row = rowbase + blockIdx.x;
+                                                   long long rowbase, long long nrows,
+                                                   const double* __restrict__ part, double* __restrict__ V) {
+  const long long rl = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (rl >= nrows) return;
+  const int lane = threadIdx.x & 31;
+  const long long row = rowbase + rl;
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {  // last job with row0 <= row
     int mid = (lo + hi + 1) >> 1;
@@ -725,29 +730,24 @@ static __global__ void __launch_bounds__(kThreads) k_red1(const RedJob* __restri
   const int bsm = (int)(r / J.nvals), v = (int)(r % J.nvals);
   const double* p = part + J.part_off + (long long)v * J.nblk + (long long)bsm * J.blk_per_sample;
   double s = 0;
-  for (int i = threadIdx.x; i < J.blk_per_sample; i += kThreads) s += p[i];
-  __shared__ double red[kWarps];
+  for (int i = lane; i < J.blk_per_sample; i += 32) s += p[i];
   s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tsum = 0;
-    for (int w = 0; w < kWarps; ++w) tsum += red[w];
-    V[row] = tsum;
-  }
+  if (lane == 0) V[row] = s;
 }
 #endif
 
-// one thread per output of a job group: combine values into gradients
-// (added to d_theta / d_x, which the caller zeroes first).
+// one warp per output of a job group: combine values into gradients, the
+// lanes over the batch (added to d_theta / d_x, which the caller zeroes
+// first; a group's outputs write distinct entries).
 #if QC_INST_R != 8
 static __global__ void k_finalize(const RedJob* __restrict__ jobs, const long long* __restrict__ row0,
                            const int* __restrict__ out0, int njobs, int outbase, int nout,
                            const RedOut* __restrict__ outs, int batch, int n_in,
                            const double* __restrict__ V, double* __restrict__ d_theta,
                            double* __restrict__ d_x) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (t >= nout) return;
+  const int lane = threadIdx.x & 31;
   const int o = outbase + t;
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
@@ -758,7 +758,7 @@ static __global__ void k_finalize(const RedJob* __restrict__ jobs, const long lo
   const RedOut ro = outs[o];
   const double* v = V + row0[lo];
   double tot = 0;
-  for (int b = 0; b < batch; ++b) {
+  for (int b = lane; b < batch; b += 32) {
     const double* vb = v + (long long)b * J.nvals;
     const double g = J.kind == RK_DIRECT ? ro.scale * vb[ro.val]
                                          : ro.scale * (vb[0] - 2.0 * vb[1 + ro.val]);
@@ -768,7 +768,10 @@ static __global__ void k_finalize(const RedJob* __restrict__ jobs, const long lo
       tot += g;
     }
   }
-  if (J.source == QC_SRC_THETA && d_theta) d_theta[ro.pidx] += tot;
+  if (J.source == QC_SRC_THETA) {
+    tot = warp_sum(tot);
+    if (lane == 0 && d_theta) d_theta[ro.pidx] += tot;
+  }
 }
 #endif
 
@@ -1290,11 +1293,13 @@ cudaError_t launch_reduce(const RedJob* jobs, const long long* row0, const int* 
                           const RedOut* outs, int batch, int n_in, const double* part, double* V,
                           double* d_theta, double* d_x, cudaStream_t st) {
   if (njobs == 0) return cudaSuccess;
-  k_red1<<<(unsigned)nrows, kThreads, 0, st>>>(jobs, row0, njobs, rowbase, part, V);
+  k_red1<<<(unsigned)((nrows + kWarps - 1) / kWarps), kThreads, 0, st>>>(jobs, row0, njobs, rowbase, nrows,
+                                                                        part, V);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_finalize<<<(nout + 127) / 128, 128, 0, st>>>(jobs, row0, out0, njobs, outbase, nout, outs, batch,
-                                                 n_in, V, d_theta, d_x);
+  // four warps (outputs) per block
+  k_finalize<<<(nout + 3) / 4, 128, 0, st>>>(jobs, row0, out0, njobs, outbase, nout, outs, batch, n_in, V,
+                                             d_theta, d_x);
   return cudaGetLastError();
 }
 #endif
