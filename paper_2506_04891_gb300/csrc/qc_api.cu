@@ -886,6 +886,25 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
             }
           }
         }
+        if (fuse && Li.cls == LC_DIAG && Li.zmode == Z_IDENT && i >= 1 && LI[i - 1].cls == LC_RING && need[i - 1]) {
+          // the diagonal layer undone (and differentiated) in the next
+          // backward ring pass, before its permutation, when that pass is
+          // tiled with at least one element per thread per half tile
+          Step r = ring_step(2);
+          if (!r.rp.whole && r.rp.t - 1 >= 8) {
+            r.rp.pre = 1;
+            r.rp.pre_grad = (Li.diff && Li.nparams > 0) ? 1 : 0;
+            r.rp.pre_tb = Li.tb;
+            r.rp.pre_coef = Li.coef_off;
+            r.rp.pre_bstride = Li.coef_bstride;
+            g.steps.push_back(r);
+            g.lo = i - 1;
+            g.pre_layer = i;
+            i = g.lo - 1;
+            bgroups.push_back(std::move(g));
+            continue;
+          }
+        }
         if (Li.cls == LC_ROT1 || Li.cls == LC_DENSE2) {
           tile_group(i, g);
         } else if (Li.cls == LC_RING) {
@@ -1134,6 +1153,16 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
             outs.push_back(OutMap{0, diag_zbit(D, n, j), D.offset + D.pstride * j, D.gscale});
           add_job(p, RK_MARGINAL, D.source, part_off, nblk, n + 1, st.cps, outs);
           part_off += nblk * (n + 1);
+        } else if (st.type == ST_RING && st.rp.pre && st.rp.pre_grad) {
+          // the fused diagonal's marginals [W, M_0 .. M_{n-1}] per ring CTA
+          const LayerInfo& D = LI[g.pre_layer];
+          const long long bps = 1LL << (n - st.rp.t), nblk = (long long)batch * bps;
+          st.part_off = part_off;
+          std::vector<OutMap> outs;
+          for (int j = 0; j < D.nparams; ++j)
+            outs.push_back(OutMap{0, diag_zbit(D, n, j), D.offset + D.pstride * j, D.gscale});
+          add_job(p, RK_MARGINAL, D.source, part_off, nblk, n + 1, bps, outs);
+          part_off += nblk * (n + 1);
         } else if (st.type == ST_DIAG && Li.diff && Li.nparams > 0) {
           const long long nblk = diag_grid(st.dp, batch);
           st.part_off = part_off;
@@ -1321,7 +1350,7 @@ qc_status run_steps(qc_circuit* c, Plan& p, const std::vector<Step>& steps, int 
         // with lambda formed from psi in the same launch only psi is read
         ProfScope ps(s.ns == 2 ? PC_RING_B : PC_RING_F, s.laminit ? 3 * S : passb, st);
         e = launch_ring<R>(s.rp, s.ns, batch, buf(s.s0), buf(s.d0), s.laminit ? nullptr : buf(s.s1),
-                           buf(s.d1), s.laminit ? gez : nullptr, st);
+                           buf(s.d1), s.laminit ? gez : nullptr, coef, part + s.part_off, st);
         break;
       }
       case ST_LAMINIT: {
@@ -1857,8 +1886,8 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
                  st.dp.xcomp, st.dp.zmode, st.dp.cb, st.s0, st.d0);
         o += line;
       } else if (st.type == ST_RING) {
-        snprintf(line, sizeof line, "%s layer=%d RING ns=%d whole=%d t=%d src=%d dst=%d\n", tag, st.layer, st.ns,
-                 st.rp.whole, st.rp.t, st.s0, st.d0);
+        snprintf(line, sizeof line, "%s layer=%d RING ns=%d whole=%d t=%d pre=%d src=%d dst=%d\n", tag, st.layer,
+                 st.ns, st.rp.whole, st.rp.t, st.rp.pre, st.s0, st.d0);
         o += line;
       } else if (st.type == ST_PRODINIT) {
         snprintf(line, sizeof line, "%s layer=%d PRODINIT dst=%d\n", tag, st.layer, st.d0);

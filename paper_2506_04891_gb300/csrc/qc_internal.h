@@ -203,6 +203,12 @@ struct RingPass {
   int n;
   int t;             // CTA covers 2^t amplitudes (two halves of 2^(t-1))
   int whole;         // 1: whole state per CTA (n <= t)
+  // backward, tiled (not whole), 2^(t-1) >= kThreads: a diagonal layer with
+  // the identity z map undone on psi and lambda before the permutation, and
+  // (pre_grad) its bit marginals [W, M_0 .. M_{n-1}] per CTA written to
+  // part[v * grid + block]
+  int pre, pre_grad, pre_tb;
+  long long pre_coef, pre_bstride;
 };
 
 // Reduction of per-CTA partials into parameter gradients.

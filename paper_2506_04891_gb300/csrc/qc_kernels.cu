@@ -573,11 +573,100 @@ __global__ void __launch_bounds__(kThreads) k_laminit(int n, int cb, const doubl
 template <class R, int NS>
 __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>* src0, cx<R>* dst0,
                                                    const cx<R>* src1, cx<R>* dst1,
-                                                   const double* __restrict__ gez) {
+                                                   const double* __restrict__ gez, const R* __restrict__ coef,
+                                                   double* __restrict__ part) {
   using C = cx<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* S = reinterpret_cast<C*>(smraw);
   const int n = P.n;
+  if constexpr (NS == 2) {
+    if (P.pre && !gez && !P.whole) {
+      // backward: undo the diagonal layer that follows the ring in the
+      // forward (its phase by the tile's own index: z = k), then the ring.
+      // Thread tid holds tile elements e = tid + kThreads j: index bits 0..7
+      // are tid's, bits 8 .. t-2 and the top bit (n - 1) come from j, the
+      // rest from the tile.  w = Im(conj(lambda) psi) is unchanged by the
+      // phase, so the marginals are summed from the loaded values.
+      const int t = P.t, H = 1 << (t - 1);
+      const int fb = n - t;
+      const int b = (int)(blockIdx.x >> fb);
+      const long long f = blockIdx.x & ((1LL << fb) - 1);
+      const long long sb = (long long)b << n;
+      const long long tb = f << (t - 1);
+      const long long ib = tb ^ (tb >> 1);
+      const long long A = ib & ~(long long)(H - 1);
+      const long long Bk = A ^ (3LL << (n - 2));
+      const int il = (int)(ib & (H - 1));
+      const long long topbit = 1LL << (n - 1);
+      const R* tabs = coef + P.pre_coef + (long long)b * P.pre_bstride;
+      C* S1 = S + 2 * H;
+      const int nj = (2 * H) / kThreads, jb = t - 9;  // jl bits 8 .. t-2 are j bits 0 .. jb-1
+      R W = 0, T = 0, Aj[4] = {0, 0, 0, 0};
+      for (int j = 0; j < nj; ++j) {
+        const int e = threadIdx.x + j * kThreads;
+        const int top = e >> (t - 1), jl = e & (H - 1);
+        const long long k = tb + jl + (top ? topbit : 0);
+        const C x = src0[sb + k], l = src1[sb + k];
+        const C ph = diag_phase<R>(tabs, P.pre_tb, k);
+        S[e] = cmulc<R>(ph, x);
+        S1[e] = cmulc<R>(ph, l);
+        if (P.pre_grad) {
+          const R w = im_cdot<R>(l, x);
+          W += w;
+          if (top) T += w;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < jb && ((j >> q) & 1)) Aj[q] += w;
+        }
+      }
+      __syncthreads();
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const C* Ss = s2 ? S1 : S;
+        C* dst = s2 ? dst1 : dst0;
+        for (int e = 2 * threadIdx.x; e < 2 * H; e += 2 * kThreads) {
+          const int u = e >> (t - 1), yl = e & (H - 1);
+          const int jl = gray_inv(yl ^ il);
+          const int top = u ^ (jl & 1);
+          store_pair<R>(dst + sb + (u ? Bk : A) + yl, Ss[top * H + jl], Ss[(top ^ 1) * H + (jl ^ 1)]);
+        }
+      }
+      if (P.pre_grad) {
+        // per warp: W, the masked sums for lane bits 0..4, the j-bit sums and
+        // the top-bit sum in the state's precision (each over 32 lanes);
+        // across warps in FP64
+        __shared__ R red[11][kWarps];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        R vals[11];
+        vals[0] = warp_sum_r<R>(W);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) vals[1 + q] = warp_sum_r<R>(((lane >> q) & 1) ? W : (R)0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vals[6 + q] = q < jb ? warp_sum_r<R>(Aj[q]) : (R)0;
+        vals[10] = warp_sum_r<R>(T);
+        if (lane == 0)
+          for (int v = 0; v < 11; ++v) red[v][warp] = vals[v];
+        __syncthreads();
+        const long long nblk = gridDim.x;
+        for (int v = threadIdx.x; v <= n; v += kThreads) {
+          // v = 0: W; v = 1 + p: M_p, the sum of w over elements with index bit p
+          const int p = v - 1;
+          double sum = 0;
+          for (int w2 = 0; w2 < kWarps; ++w2) {
+            double x;
+            if (v == 0 || (p >= t - 1 && p < n - 1)) x = red[0][w2];
+            else if (p < 5) x = red[1 + p][w2];
+            else if (p < 8) x = ((w2 >> (p - 5)) & 1) ? red[0][w2] : 0.0;
+            else if (p < t - 1) x = red[6 + (p - 8)][w2];
+            else x = red[10][w2];
+            sum += x;
+          }
+          if (p >= t - 1 && p < n - 1 && !((tb >> p) & 1)) sum = 0;
+          part[(long long)v * nblk + blockIdx.x] = sum;
+        }
+      }
+      return;
+    }
+  }
   if (NS == 2 && gez) {
     __shared__ double Sg[kMaxQubits];
     const int b = P.whole ? (int)blockIdx.x : (int)(blockIdx.x >> (n - P.t));
@@ -1220,13 +1309,14 @@ cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, 
 #if QC_INST_R != 8
 size_t ring_smem_bytes(const RingPass& P, int rsize) {
   size_t amps = P.whole ? ((size_t)1 << P.n) : ((size_t)1 << P.t);
-  return amps * 2 * rsize;
+  return amps * 2 * rsize * (P.pre && !P.whole ? 2 : 1);  // both states with a fused diagonal
 }
 #endif
 
 template <class R>
 cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, void* d0,
-                        const void* s1, void* d1, const double* gez, cudaStream_t st) {
+                        const void* s1, void* d1, const double* gez, const void* coef, double* part,
+                        cudaStream_t st) {
   size_t smem = ring_smem_bytes(P, sizeof(R));
   long long grid = P.whole ? batch : ((long long)batch << (P.n - P.t));
   if (ns == 1) {
@@ -1234,13 +1324,13 @@ cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, vo
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const cx<R>*)s0, (cx<R>*)d0, nullptr, nullptr,
-                                                 nullptr);
+                                                 nullptr, (const R*)coef, part);
   } else {
     auto kern = k_ring<R, 2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, kThreads, smem, st>>>(P, (const cx<R>*)s0, (cx<R>*)d0, (const cx<R>*)s1,
-                                                 (cx<R>*)d1, gez);
+                                                 (cx<R>*)d1, gez, (const R*)coef, part);
   }
   return cudaGetLastError();
 }
@@ -1396,7 +1486,7 @@ cudaError_t launch_smem(const SmemLayer* prog, int nl, int n, int batch, int bwd
   template cudaError_t launch_diag<R>(const DiagPass&, int, int, const void*, const void*, void*,  \
                                       const void*, void*, double*, cudaStream_t);                  \
   template cudaError_t launch_ring<R>(const RingPass&, int, int, const void*, void*, const void*,  \
-                                      void*, const double*, cudaStream_t);                         \
+                                      void*, const double*, const void*, double*, cudaStream_t);   \
   template cudaError_t launch_expect<R>(int, int, int, const void*, double*, double*,              \
                                         cudaStream_t);                                             \
   template cudaError_t preload_expect<R>(int);                                                     \

@@ -69,7 +69,8 @@ cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, 
                         void* d0, const void* s1, void* d1, double* part, cudaStream_t st);
 template <class R>
 cudaError_t launch_ring(const RingPass& P, int ns, int batch, const void* s0, void* d0,
-                        const void* s1, void* d1, const double* gez, cudaStream_t st);
+                        const void* s1, void* d1, const double* gez, const void* coef, double* part,
+                        cudaStream_t st);
 template <class R>
 cudaError_t launch_expect(int n, int cb, int batch, const void* psi, double* part, double* ez,
                           cudaStream_t st);

@@ -439,6 +439,19 @@ def test_backward_diagonal_layers_ride_in_the_next_tile_pass(q):
     assert "pre=1" not in plain
 
 
+def test_backward_diagonal_before_a_ring_rides_in_the_ring_pass(q):
+    """HEA blocks [RZ, RY, RZ, CNOT ring]: in the backward the first RZ of a
+    block is undone (and differentiated) in the tiled ring pass that follows
+    it, so no standalone diagonal pass is left; with fusion off it is one."""
+    layers = W.serving_circuit(24)
+    desc, _ = _plan(q, 24, layers, batch=2, path=2)
+    bwd = [l for l in desc.splitlines() if l.startswith("B ")]
+    assert not any(" DIAG " in l for l in bwd)
+    assert sum(" RING " in l and "pre=1" in l for l in bwd) == 5
+    plain, _ = _plan(q, 24, layers, batch=2, path=2, fuse=0)
+    assert sum(" DIAG " in l for l in plain.splitlines() if l.startswith("B ")) >= 6
+
+
 def test_automatic_path_takes_shared_memory_only_where_launch_bound(q):
     """The whole-circuit shared-memory kernel for small states (hea4, and
     n <= 10 / n <= 8 at batch <= 128), the layer path above (hea12 in both
