@@ -888,10 +888,12 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         }
         if (fuse && Li.cls == LC_DIAG && Li.zmode == Z_IDENT && i >= 1 && LI[i - 1].cls == LC_RING && need[i - 1]) {
           // the diagonal layer undone (and differentiated) in the next
-          // backward ring pass, before its permutation, when that pass is
-          // tiled with at least one element per thread per half tile
+          // backward ring pass, before its permutation, when its tile (the
+          // whole state for a whole-state pass) has at least 2^10 amplitudes
+          // (the kernel's loads come in steps of four per thread)
           Step r = ring_step(2);
-          if (!r.rp.whole && r.rp.t - 1 >= 8) {
+          const int rt = r.rp.whole ? n : r.rp.t;
+          if (rt >= 10 && rt <= 13) {
             r.rp.pre = 1;
             r.rp.pre_grad = (Li.diff && Li.nparams > 0) ? 1 : 0;
             r.rp.pre_tb = Li.tb;
@@ -1156,7 +1158,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         } else if (st.type == ST_RING && st.rp.pre && st.rp.pre_grad) {
           // the fused diagonal's marginals [W, M_0 .. M_{n-1}] per ring CTA
           const LayerInfo& D = LI[g.pre_layer];
-          const long long bps = 1LL << (n - st.rp.t), nblk = (long long)batch * bps;
+          const long long bps = st.rp.whole ? 1 : 1LL << (n - st.rp.t), nblk = (long long)batch * bps;
           st.part_off = part_off;
           std::vector<OutMap> outs;
           for (int j = 0; j < D.nparams; ++j)

@@ -203,8 +203,9 @@ struct RingPass {
   int n;
   int t;             // CTA covers 2^t amplitudes (two halves of 2^(t-1))
   int whole;         // 1: whole state per CTA (n <= t)
-  // backward, tiled (not whole), 2^(t-1) >= kThreads: a diagonal layer with
-  // the identity z map undone on psi and lambda before the permutation, and
+  // backward, a tile (or whole state) of 2^10 .. 2^13 amplitudes: a diagonal
+  // layer with the identity z map undone on psi and lambda before the
+  // permutation, and
   // (pre_grad) its bit marginals [W, M_0 .. M_{n-1}] per CTA written to
   // part[v * grid + block]
   int pre, pre_grad, pre_tb;

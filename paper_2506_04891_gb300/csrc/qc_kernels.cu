@@ -580,14 +580,15 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
   C* S = reinterpret_cast<C*>(smraw);
   const int n = P.n;
   if constexpr (NS == 2) {
-    if (P.pre && !gez && !P.whole) {
+    if (P.pre && !gez) {
       // backward: undo the diagonal layer that follows the ring in the
       // forward (its phase by the tile's own index: z = k), then the ring.
       // Thread tid holds tile elements e = tid + kThreads j: index bits 0..7
       // are tid's, bits 8 .. t-2 and the top bit (n - 1) come from j, the
       // rest from the tile.  w = Im(conj(lambda) psi) is unchanged by the
       // phase, so the marginals are summed from the loaded values.
-      const int t = P.t, H = 1 << (t - 1);
+      // (a whole-state CTA is the tile t = n: no tile bits, bit n - 1 the top)
+      const int t = P.whole ? n : P.t, H = 1 << (t - 1);
       const int fb = n - t;
       const int b = (int)(blockIdx.x >> fb);
       const long long f = blockIdx.x & ((1LL << fb) - 1);
@@ -602,25 +603,47 @@ __global__ void __launch_bounds__(kThreads) k_ring(const RingPass P, const cx<R>
       C* S1 = S + 2 * H;
       const int nj = (2 * H) / kThreads, jb = t - 9;  // jl bits 8 .. t-2 are j bits 0 .. jb-1
       R W = 0, T = 0, Aj[4] = {0, 0, 0, 0};
-      for (int j = 0; j < nj; ++j) {
-        const int e = threadIdx.x + j * kThreads;
-        const int top = e >> (t - 1), jl = e & (H - 1);
-        const long long k = tb + jl + (top ? topbit : 0);
-        const C x = src0[sb + k], l = src1[sb + k];
-        const C ph = diag_phase<R>(tabs, P.pre_tb, k);
-        S[e] = cmulc<R>(ph, x);
-        S1[e] = cmulc<R>(ph, l);
-        if (P.pre_grad) {
-          const R w = im_cdot<R>(l, x);
-          W += w;
-          if (top) T += w;
+      // four steps' loads (both states and the phase-table entries) before
+      // their smem writes, so each thread has eight amplitude loads in flight
+#pragma unroll 1
+      for (int j0 = 0; j0 < nj; j0 += 4) {
+        C xs[4], ls[4], ph[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (q < jb && ((j >> q) & 1)) Aj[q] += w;
+        for (int u = 0; u < 4; ++u) {
+          const int e = threadIdx.x + (j0 + u) * kThreads;
+          if (j0 + u >= nj) break;
+          const int top = e >> (t - 1), jl = e & (H - 1);
+          const long long k = tb + jl + (top ? topbit : 0);
+          xs[u] = src0[sb + k];
+          ls[u] = src1[sb + k];
+          ph[u] = diag_phase<R>(tabs, P.pre_tb, k);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          if (j >= nj) break;
+          const int e = threadIdx.x + j * kThreads;
+          S[e] = cmulc<R>(ph[u], xs[u]);
+          S1[e] = cmulc<R>(ph[u], ls[u]);
+          if (P.pre_grad) {
+            const R w = im_cdot<R>(ls[u], xs[u]);
+            W += w;
+            if ((e >> (t - 1)) & 1) T += w;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (q < jb && ((j >> q) & 1)) Aj[q] += w;
+          }
         }
       }
       __syncthreads();
-      for (int s2 = 0; s2 < 2; ++s2) {
+      if (P.whole) {
+        for (int k = threadIdx.x; k < 2 * H; k += kThreads) {
+          const int y = ring_f(k, n);
+          dst0[sb + k] = S[y];
+          dst1[sb + k] = S1[y];
+        }
+      }
+      for (int s2 = 0; s2 < 2 && !P.whole; ++s2) {
         const C* Ss = s2 ? S1 : S;
         C* dst = s2 ? dst1 : dst0;
         for (int e = 2 * threadIdx.x; e < 2 * H; e += 2 * kThreads) {
@@ -1309,7 +1332,7 @@ cudaError_t launch_diag(const DiagPass& P, int ns, int batch, const void* coef, 
 #if QC_INST_R != 8
 size_t ring_smem_bytes(const RingPass& P, int rsize) {
   size_t amps = P.whole ? ((size_t)1 << P.n) : ((size_t)1 << P.t);
-  return amps * 2 * rsize * (P.pre && !P.whole ? 2 : 1);  // both states with a fused diagonal
+  return amps * 2 * rsize * (P.pre ? 2 : 1);  // both states with a fused diagonal
 }
 #endif
 

@@ -69,6 +69,17 @@ def test_layer_path_multi_tile(name, dtype, n):
     compare(dtype, n, CIRCUITS[name](n), 2, seed=2, path=2)
 
 
+@pytest.mark.parametrize("dtype,n", [("c64", 10), ("c64", 12), ("c128", 11), ("c64", 13)])
+def test_diagonal_undone_in_the_backward_ring_pass(dtype, n):
+    """HEA blocks: the first RZ of a block is undone and differentiated in the
+    backward ring pass (whole-state rings at n = 10..12, tiled at 13)."""
+    from paper_2506_04891_gb300 import qlayer as Q
+    layers = W.hea_circuit(n, 3)
+    d = Q.Circuit(n, layers, dtype=dtype, path=2).describe(3)
+    assert any(l.startswith("B") and " RING " in l and "pre=1" in l for l in d.splitlines()), d
+    compare(dtype, n, layers, 3, seed=16, path=2)
+
+
 @pytest.mark.parametrize("name", sorted(CIRCUITS))
 @pytest.mark.parametrize("n", [2, 3])
 @pytest.mark.parametrize("path", [1, 2])
