@@ -635,6 +635,12 @@ bool tma_pass_ok(const qc_circuit* c, const Step& st) {
   } else if (st.rb != 3 && st.rb != 4) {
     return false;
   }
+  if (P.xload) {
+    // the complemented-load variants (see launch_tma_ns)
+    if (P.gather || P.scatter) return false;
+    if (st.ns == 1 && !(P.kind == 2 && !P.pre && !P.post && (st.rb == 3 || st.rb == 4))) return false;
+    if (st.ns == 2 && !(P.kind == 0 && P.sx && P.pre && st.rb == 4)) return false;
+  }
   if (st.ns == 1) {
     if (P.pre || P.scatter) return false;
     if (P.post && !(st.rb == 4 && P.kind != 2 && fwd_post_contig(P))) return false;
@@ -921,6 +927,22 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         bgroups.push_back(std::move(g));
       }
     }
+    // an X layer (no phase) undone by complemented loads in the next group's
+    // first pass, where that pass runs the TMA variant built for it (the SX
+    // pass with the following diagonal undone in round 0)
+    for (size_t k = 0; fuse && k + 1 < bgroups.size(); ++k) {
+      BGroup& gx = bgroups[k];
+      BGroup& gt = bgroups[k + 1];
+      const LayerInfo& X = LI[gx.hi];
+      if (gx.steps.size() != 1 || gx.steps[0].type != ST_DIAG || X.kind != QC_L_X || X.has_phase) continue;
+      if (gt.steps.empty() || gt.steps.front().type != ST_TILE) continue;
+      Step probe = gt.steps.front();
+      probe.tp.xload = 1;
+      if (!tma_pass_ok(c, probe)) continue;
+      gt.steps.front().tp.xload = 1;
+      gt.hi = gx.hi;
+      bgroups.erase(bgroups.begin() + (long)k);
+    }
     std::set<int> bstarts;
     for (auto& g : bgroups) bstarts.insert(g.hi);
 
@@ -1045,6 +1067,23 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
       }
     }
 
+    // an X layer (no phase) applied by complemented loads in the next group's
+    // first pass, where that pass runs the TMA variant built for it (a brick
+    // layer's first pass)
+    for (size_t k = 0; fuse && k + 1 < fgroups.size(); ++k) {
+      FGroup& gx = fgroups[k];
+      FGroup& gt = fgroups[k + 1];
+      if (gx.steps.size() != 1 || gx.steps[0].type != ST_DIAG) continue;
+      const LayerInfo& X = LI[gx.hi];
+      if (X.kind != QC_L_X || X.has_phase) continue;
+      if (gt.steps.empty() || gt.steps.front().type != ST_TILE) continue;
+      Step probe = gt.steps.front();
+      probe.tp.xload = 1;
+      if (!tma_pass_ok(c, probe)) continue;
+      gt.steps.front().tp.xload = 1;
+      fgroups.erase(fgroups.begin() + (long)k);
+    }
+
     // checkpoints: forward group ends that are also backward group inputs
     std::map<int, int> ck_slot;
     if (ck > 0) {
@@ -1076,7 +1115,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
             st.d0 = to_ck ? B_CKPT + ck_slot[g.hi] : A;
           } else {
             st.s0 = cur;
-            const bool inplace_ok = st.type != ST_RING && !(st.type == ST_TILE && st.tp.gather);
+            const bool inplace_ok = st.type != ST_RING && !(st.type == ST_TILE && (st.tp.gather || st.tp.xload));
             if (last && to_ck) st.d0 = B_CKPT + ck_slot[g.hi];
             else if (inplace_ok && (cur == A || cur == Bb)) st.d0 = cur;
             else if (cur == A || cur == Bb) st.d0 = other(cur);
@@ -1122,7 +1161,7 @@ std::unique_ptr<Plan> build_plan(const qc_circuit* c, int batch) {
         st.s1 = cl;
         const bool lam_here = laminit_fused && gi == 0 && st.type == ST_RING;
         st.laminit = lam_here ? 1 : 0;
-        const bool oop = st.type == ST_RING || (st.type == ST_TILE && st.tp.scatter);
+        const bool oop = st.type == ST_RING || (st.type == ST_TILE && (st.tp.scatter || st.tp.xload));
         st.d0 = (!oop && isrun(sp)) ? sp : (isrun(sp) ? orun(sp) : B_RUN0);
         st.d1 = lam_here ? B_LAM0 : (!oop ? cl : olam(cl));
         if (g.lo == 0 && k + 1 == g.steps.size() && st.type == ST_TILE) st.tp.store = 0;
@@ -1872,10 +1911,10 @@ QC_API qc_status qc_describe_plan(const qc_circuit* cc, int batch, char* buf, si
         // contiguous pass's compile-time element patterns
         const int post = !st.tp.post ? 0
                          : (st.ns == 1 && st.rb == 4 && c->dtype == QC_C64 && fwd_post_contig(st.tp)) ? 2 : 1;
-        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d defer=%d store=%d pre=%d post=%d tma=%d tc=%d src=%d dst=%d",
+        snprintf(line, sizeof line, "%s layer=%d TILE ns=%d t=%d c=%d h0=%d rb=%d cps=%d stages=%d rounds=%d ops=%d slots=%d defer=%d store=%d pre=%d post=%d xl=%d tma=%d tc=%d src=%d dst=%d",
                  tag, st.layer, st.ns, st.tp.t, st.tp.c, st.tp.h0, st.rb, st.cps, st.tp.nstage, st.tp.nrounds, st.tp.nops, st.tp.nslots,
                  st.tp.defer,
-                 st.tp.store, st.tp.pre, post, st.tma, st.tc, st.s0, st.d0);
+                 st.tp.store, st.tp.pre, post, st.tp.xload, st.tma, st.tc, st.s0, st.d0);
         o += line;
         for (int k = 0; k < st.tp.nops; ++k) {
           snprintf(line, sizeof line, " [l=%d%s np=%d%s]", st.tp.ops[k].l, st.tp.ops[k].is2q ? ",2q" : "",

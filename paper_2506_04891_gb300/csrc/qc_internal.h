@@ -108,6 +108,8 @@ struct TilePass {
   int kind;                          // 0: complex 1q, 1: real 1q, 2: two-qubit (uniform per pass)
   int rb;                            // register bits per round the rounds were planned for
   int sx;                            // 1: constant SX layer without companions (TMA: additions-only variant)
+  int xload;                         // 1: an X layer (k -> ~k) fused into the loads: tile element k
+                                     //    is read from index ~k (not with gather or scatter)
   // fused neighbours (forward unless noted)
   int gather;        // 1: load psi[f^-1(k)] (a CNOT ring applied before this pass's gates)
   int scatter;       // 1: store to f^-1(k) (backward: inverse CNOT ring after this pass)

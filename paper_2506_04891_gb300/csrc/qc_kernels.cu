@@ -1270,6 +1270,7 @@ template <class R>
 cudaError_t launch_tile(const TilePass& P, int rb, int ns, int batch, int cps, const void* coef,
                         const void* s0, void* d0, const void* s1, void* d1, double* part,
                         cudaStream_t st) {
+  if (P.xload) return cudaErrorInvalidValue;  // complemented loads: TMA variants only
   if (ns == 1) return launch_tile_fwd<R>(P, rb, batch, cps, coef, s0, d0, s1, d1, part, st);
   return launch_tile_bwd<R>(P, rb, batch, cps, coef, s0, d0, s1, d1, part, st);
 }

@@ -388,7 +388,11 @@ __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np,
 // pass, last round on bits 8..11).
 // COMP: the pass also takes companion gradients (a folded preceding RX / RY
 // layer); without them that code is compiled out.
-template <int NS, int RB, int KIND, int PRE, bool COMP>
+// XL: the pass first undoes (backward) or applies (forward) an X layer on
+// every qubit, k -> ~k: each tile is loaded from the mirrored box and its
+// elements are addressed in reversed order (local index i ^ (T - 1)), which
+// the XOR swizzle and the register bases keep linear.
+template <int NS, int RB, int KIND, int PRE, bool COMP, bool XL = false>
 __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
     k_tile_tma(const __grid_constant__ TilePass P, const __grid_constant__ CUtensorMap tm0,
                const __grid_constant__ CUtensorMap tm1, const float* __restrict__ coef, float2* dst0,
@@ -517,9 +521,16 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   const float2 corr = s_corr;
 
   unsigned pending = 0, phase = 0;
+  // box coordinates of tile f (XL: of the mirrored tile, every index bit
+  // outside the box complemented; the batch bits above them are not)
+  const long long hmask = (1LL << (n - h0 - m)) - 1;
+  auto coord2 = [&](long long f) { return (int)((f & ((1LL << gap) - 1)) ^ (XL ? ((1LL << gap) - 1) : 0)); };
+  auto coord4 = [&](long long f) {
+    return (int)(((long long)b << (n - h0 - m)) | ((f >> gap) ^ (XL ? hmask : 0)));
+  };
   auto issue = [&](long long f, int s) {  // thread 0
-    const int c2 = (int)(f & ((1LL << gap) - 1));
-    const int c4 = (int)(((long long)b << (n - h0 - m)) | (f >> gap));
+    const int c2 = coord2(f);
+    const int c4 = coord4(f);
     const unsigned bar = smem_u32(&bars[s]);
     mbar_expect_tx(bar, (unsigned)(NS * T * sizeof(C)));
     tma_load_5d(smem_u32(buf + (size_t)s * NS * T), &tm0, 0, 0, c2, 0, c4, bar);
@@ -529,8 +540,8 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
   // the tile after the ones in flight, pulled into L2 while this one is
   // processed, so its copy into shared memory does not wait on DRAM
   auto prefetch = [&](long long f) {  // thread 0
-    const int c2 = (int)(f & ((1LL << gap) - 1));
-    const int c4 = (int)(((long long)b << (n - h0 - m)) | (f >> gap));
+    const int c2 = coord2(f);
+    const int c4 = coord4(f);
     tma_prefetch_5d(&tm0, 0, 0, c2, 0, c4);
     if (NS == 2) tma_prefetch_5d(&tm1, 0, 0, c2, 0, c4);
   };
@@ -581,23 +592,24 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
       }
       for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
         const int li = (g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB));
-        const int pb = tma_swz(li);
+        const int pb = tma_swz(XL ? (li ^ (T - 1)) : li);
         C v0[1 << RB], v1[NS == 2 ? (1 << RB) : 1];
         if (lo == 0) {
           // amplitude pairs (bit 0) as 16-byte accesses; the swizzle keeps bit 0
+          // (XL: the pair's elements sit in reversed order at pb ^ 1, pb)
 #pragma unroll
           for (int a = 0; a < (1 << RB); a += 2) {
-            int ad = pb;
+            int ad = XL ? (pb ^ 1) : pb;
 #pragma unroll
             for (int j = 1; j < RB; ++j)
               if (a & (1 << j)) ad ^= basis[j];
             const float4 q = *reinterpret_cast<const float4*>(&S0[ad]);
-            v0[a] = make_float2(q.x, q.y);
-            v0[a + 1] = make_float2(q.z, q.w);
+            v0[a] = XL ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+            v0[a + 1] = XL ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
             if constexpr (NS == 2) {
               const float4 u = *reinterpret_cast<const float4*>(&S1[ad]);
-              v1[a] = make_float2(u.x, u.y);
-              v1[a + 1] = make_float2(u.z, u.w);
+              v1[a] = XL ? make_float2(u.z, u.w) : make_float2(u.x, u.y);
+              v1[a + 1] = XL ? make_float2(u.x, u.y) : make_float2(u.z, u.w);
             }
           }
         } else {
@@ -715,13 +727,14 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
         } else if (lo == 0) {
 #pragma unroll
           for (int a = 0; a < (1 << RB); a += 2) {
-            int ad = pb;
+            int ad = XL ? (pb ^ 1) : pb;
 #pragma unroll
             for (int j = 1; j < RB; ++j)
               if (a & (1 << j)) ad ^= basis[j];
-            *reinterpret_cast<float4*>(&S0[ad]) = make_float4(v0[a].x, v0[a].y, v0[a + 1].x, v0[a + 1].y);
+            const int e0 = XL ? a + 1 : a, e1 = XL ? a : a + 1;
+            *reinterpret_cast<float4*>(&S0[ad]) = make_float4(v0[e0].x, v0[e0].y, v0[e1].x, v0[e1].y);
             if constexpr (NS == 2)
-              *reinterpret_cast<float4*>(&S1[ad]) = make_float4(v1[a].x, v1[a].y, v1[a + 1].x, v1[a + 1].y);
+              *reinterpret_cast<float4*>(&S1[ad]) = make_float4(v1[e0].x, v1[e0].y, v1[e1].x, v1[e1].y);
           }
         } else {
 #pragma unroll

@@ -44,7 +44,7 @@ static cudaError_t make_tile_map(CUtensorMap* tm, const void* base, const TilePa
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int NS, int RB, int KIND, int PRE>
+template <int NS, int RB, int KIND, int PRE, bool XL = false>
 static cudaError_t launch_tma_k(const TilePass& P, int batch, int cps, const void* coef, const void* s0,
                                 void* d0, const void* s1, void* d1, double* part, cudaStream_t st) {
   // companion gradients only occur in backward single-qubit passes
@@ -60,7 +60,7 @@ static cudaError_t launch_tma_k(const TilePass& P, int batch, int cps, const voi
     tm1 = tm0;
   }
   const size_t smem = tma_smem_bytes(P, NS);
-  auto kern = comp ? k_tile_tma<NS, RB, KIND, PRE, kMayComp> : k_tile_tma<NS, RB, KIND, PRE, false>;
+  auto kern = comp ? k_tile_tma<NS, RB, KIND, PRE, kMayComp, XL> : k_tile_tma<NS, RB, KIND, PRE, false, XL>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long grid = (long long)batch * cps;
@@ -75,6 +75,21 @@ template <int NS>
 static cudaError_t launch_tma_ns(const TilePass& P, int rb, int batch, int cps, const void* coef, const void* s0,
                                  void* d0, const void* s1, void* d1, double* part, cudaStream_t st) {
 #define QC_TMA_L(RB_, K_, PRE_) launch_tma_k<NS, RB_, K_, PRE_>(P, batch, cps, coef, s0, d0, s1, d1, part, st)
+#define QC_TMA_X(RB_, K_, PRE_) launch_tma_k<NS, RB_, K_, PRE_, true>(P, batch, cps, coef, s0, d0, s1, d1, part, st)
+  if (P.xload) {
+    // a fused X layer (complemented loads): built for the forward brick pass
+    // and the backward SX pass with its diagonal undone in round 0
+    if constexpr (NS == 1) {
+      if (P.kind == 2 && !P.pre && !P.post) {
+        if (rb == 3) return QC_TMA_X(3, 2, 0);
+        if (rb == 4) return QC_TMA_X(4, 2, 0);
+      }
+    } else {
+      if (P.kind == 0 && P.sx && P.pre && rb == 4)
+        return P.pre_zmode == Z_RINGXOR ? QC_TMA_X(4, 3, 2) : QC_TMA_X(4, 3, 1);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (P.kind == 2) {
     if (P.pre || P.post) return cudaErrorInvalidValue;
     switch (rb) {
@@ -104,6 +119,7 @@ static cudaError_t launch_tma_ns(const TilePass& P, int rb, int batch, int cps, 
   if (rb == 3) return P.kind == 1 ? QC_TMA_L(3, 1, 0) : sx ? QC_TMA_L(3, 3, 0) : QC_TMA_L(3, 0, 0);
   if (rb == 4) return P.kind == 1 ? QC_TMA_L(4, 1, 0) : sx ? QC_TMA_L(4, 3, 0) : QC_TMA_L(4, 0, 0);
 #undef QC_TMA_L
+#undef QC_TMA_X
   return cudaErrorInvalidValue;
 }
 

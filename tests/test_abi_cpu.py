@@ -452,6 +452,20 @@ def test_backward_diagonal_before_a_ring_rides_in_the_ring_pass(q):
     assert sum(" DIAG " in l for l in plain.splitlines() if l.startswith("B ")) >= 6
 
 
+def test_x_layers_ride_in_complemented_loads_out_of_place(q):
+    """ibm20: every X layer of the body is applied (forward, the brick's
+    first pass) and undone (backward, the SX pass) by loading tile k from ~k;
+    such a pass reads another CTA's tile, so it never writes in place."""
+    cfg = W.WORKLOADS["ibm20"]
+    desc, _ = _plan(q, cfg["n"], cfg["layers"](), batch=cfg["batch"], path=2)
+    xl = [l for l in desc.splitlines() if " xl=1 " in l]
+    assert sum(l.startswith("F ") for l in xl) == 7 and sum(l.startswith("B ") for l in xl) == 8
+    for l in xl:
+        d = dict(re.findall(r"(\w+)=(-?\d+)", l.split("[")[0]))
+        assert d["src"] != d["dst"] and d["tma"] == "1", l
+    assert not any(" DIAG " in l and "xcomp=1" in l for l in desc.splitlines())
+
+
 def test_automatic_path_takes_shared_memory_only_where_launch_bound(q):
     """The whole-circuit shared-memory kernel for small states (hea4, and
     n <= 10 / n <= 8 at batch <= 128), the layer path above (hea12 in both
