@@ -120,6 +120,27 @@ __device__ __forceinline__ R warp_sum_r(R v) {
   return v;
 }
 
+// Block sums of nv per-thread values val(v): each warp adds its lanes in R
+// (butterfly) and lane 0 keeps the warp total in wred[v * kWarps + warp]
+// (nv * kWarps entries of R); after a barrier thread v adds the kWarps warp
+// totals in FP64 and calls out(v, total). Only those last additions run on
+// the FP64 pipe, slow on this part (a per-warp FP64 butterfly for every value
+// stalled the end of each pass); the order of the sums is fixed.
+template <class R, class Val, class Out>
+__device__ __forceinline__ void block_sums(R* wred, int nv, Val val, Out out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = 0; v < nv; ++v) {
+    const R s = warp_sum_r<R>(val(v));
+    if (lane == 0) wred[v * kWarps + warp] = s;
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += kThreads) {
+    double s = 0;
+    for (int w = 0; w < kWarps; ++w) s += (double)wred[v * kWarps + w];
+    out(v, s);
+  }
+}
+
 // Ring = CNOT(q->q+1 mod n) for q = 0..n-1.  With bit p = n-1-q:
 //   forward  f(k):   bit p = parity(k >> p) for p <= n-2, bit n-1 = parity(k mod 2^(n-1))
 //   inverse  f^-1(k) = k ^ (k >> 1) ^ (k & 1 ? 3 << (n-2) : 0)

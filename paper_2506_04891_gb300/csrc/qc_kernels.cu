@@ -256,37 +256,33 @@ __global__ void __launch_bounds__(kThreads) k_prodinit(int n, int cb, const R* _
 // ---------------------------------------------------------------------------
 
 // Per thread: u_p = zt_p ? (W - accz_p) : accz_p, with accz_p the per-thread
-// sums over the compile-time j bits; written to sred[(1 + p) * kThreads + tid]
-// (added when `add`), sred[tid] holds W.
+// sums over the compile-time j bits (acc[s] holds z bit acc_lo + s).
 template <int NA, class A>
-__device__ __forceinline__ void marg_write(double* sred, int n, long long zt, A W,
-                                           const A* acc, int acc_lo, bool add) {
-  const int tid = threadIdx.x;
-  double w0 = add ? sred[tid] : 0.0;
-  sred[tid] = w0 + (double)W;
-  for (int p = 0; p < n; ++p) {
-    A a = 0;
-    const int q = p - acc_lo;
+__device__ __forceinline__ A marg_u(int p, long long zt, A W, const A* acc, int acc_lo) {
+  A a = 0;
+  const int q = p - acc_lo;
 #pragma unroll
-    for (int s = 0; s < NA; ++s)
-      if (s == q) a = acc[s];
-    A u = ((zt >> p) & 1) ? (W - a) : a;
-    double old = add ? sred[(1 + p) * kThreads + tid] : 0.0;
-    sred[(1 + p) * kThreads + tid] = old + (double)u;
-  }
+  for (int s = 0; s < NA; ++s)
+    if (s == q) a = acc[s];
+  return ((zt >> p) & 1) ? (W - a) : a;
 }
 
-// Sums sred[v][0..kThreads) for v <= n in a fixed order and writes
-// part[v * nblk + blk].
-__device__ __forceinline__ void marg_flush(const double* sred, int nvals, double* part,
-                                           long long nblk, long long blk) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = warp; v < nvals; v += kWarps) {
-    double s = 0;
-    for (int e = 0; e < kThreads / 32; ++e) s += sred[v * kThreads + lane + 32 * e];
-    s = warp_sum(s);
-    if (lane == 0) part[(long long)v * nblk + blk] = s;
-  }
+// part[v * nblk + blk] = the block's sum of W (v = 0) and of u_p (v = 1 + p)
+// for v < nvals (two: each thread's values are the sums over two sets, a
+// chunk and its mirror); wred holds nvals * kWarps entries of A.
+template <int NA, class A>
+__device__ __forceinline__ void marg_reduce(A* wred, int nvals, double* part, long long nblk,
+                                            long long blk, long long zt, A W, const A* acc,
+                                            bool two, long long zt2, A W2, const A* acc2) {
+  block_sums<A>(
+      wred, nvals,
+      [&](int v) -> A {
+        if (v == 0) return two ? W + W2 : W;
+        A u = marg_u<NA, A>(v - 1, zt, W, acc, 7);
+        if (two) u += marg_u<NA, A>(v - 1, zt2, W2, acc2, 7);
+        return u;
+      },
+      [&](int v, double sum) { part[(long long)v * nblk + blk] = sum; });
 }
 
 // ---------------------------------------------------------------------------
@@ -301,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
                                                    double* __restrict__ part) {
   using C = cx<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* sred = reinterpret_cast<double*>(smraw);
+  R* scol = reinterpret_cast<R*>(smraw);  // [nvals][kWarps] warp totals
   const int n = P.n, cb = P.cb;
   const long long N = 1LL << n;
   const int CH = 1 << cb;
@@ -364,9 +360,8 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
     }
     if (NS == 2) {
       const long long zt = ztrans(base + tid, n, ZM);
-      marg_write<JB + 2, R>(sred, n, active ? zt : 0, W, acc, 7, false);
-      __syncthreads();
-      marg_flush(sred, P.nvals, part, gridDim.x, blockIdx.x);
+      marg_reduce<JB + 2, R>(scol, P.nvals, part, gridDim.x, blockIdx.x, active ? zt : 0, W, acc,
+                             false, 0, (R)0, acc);
     }
   } else {
     // mirror chunk of `ch` is nch-1-ch; a single chunk is its own mirror
@@ -456,10 +451,8 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagPass P, const R* __
       const bool act = tid < lim || (tid < CH && !single);
       const long long zt = base + tid;
       const long long ztm = (mbase + CH - 1) ^ tid;
-      marg_write<JB + 2, R>(sred, n, act ? zt : 0, act ? W : (R)0, acc, 7, false);
-      marg_write<JB + 2, R>(sred, n, act ? ztm : 0, act ? Wm : (R)0, accm, 7, true);
-      __syncthreads();
-      marg_flush(sred, P.nvals, part, gridDim.x, blockIdx.x);
+      marg_reduce<JB + 2, R>(scol, P.nvals, part, gridDim.x, blockIdx.x, act ? zt : 0,
+                             act ? W : (R)0, acc, true, act ? ztm : 0, act ? Wm : (R)0, accm);
     }
   }
 }
@@ -1287,7 +1280,7 @@ template <class R, int NS, int ZM, int XC, int JB>
 static cudaError_t launch_diag_jb(const DiagPass& P, int batch, const void* coef, const void* s0,
                                   void* d0, const void* s1, void* d1, double* part,
                                   cudaStream_t st) {
-  size_t smem = NS == 2 ? (size_t)(P.n + 1) * kThreads * sizeof(double) : 0;
+  size_t smem = NS == 2 ? (size_t)P.nvals * kWarps * sizeof(R) : 0;
   auto kern = k_diag<R, NS, ZM, XC, JB>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -969,61 +969,62 @@ __global__ void __launch_bounds__(kThreads, tile_minb(sizeof(R), NS, KIND, PRE))
     slot = slot + 1 == nst ? 0 : slot + 1;
   }
   cp_async_wait_group<0>();
-  if (NS == 2 && P.defer == 2) {
-    for (int s = 0; s < P.nslots; ++s) {
-      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
-      if (lane == 0) sred[warp * P.nslots + s] += v;
-    }
-  }
-  if (NS == 2 && P.defer == 1) {
+  if constexpr (NS == 2) {
+    // gradient sums over the block: per-warp totals in R, FP64 across warps
+    const long long nblk = gridDim.x;
+    auto slot_out = [&](int v, double sum) { part[(long long)v * nblk + blockIdx.x] = sum; };
+    if (P.defer == 2) {
+      block_sums<R>(reinterpret_cast<R*>(sred), P.nslots,
+                    [&](int v) { return sdef[v * kThreads + threadIdx.x]; }, slot_out);
+    } else if (P.defer == 1) {
+      // rounds' register sums (one per slot), then the companions' columns
+      const int nr = P.nslots - P.ncomp;
+      block_sums<R>(
+          reinterpret_cast<R*>(sred), P.nslots,
+          [&](int v) -> R {
+            if (v >= nr) return sdef[(v - nr) * kThreads + threadIdx.x];
+            R a = 0;
 #pragma unroll
-    for (int r = 0; r < kAR; ++r)
+            for (int r = 0; r < kAR; ++r)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int sl = P.rslot[r][i];
-        if (sl >= 0) {
-          const double v = warp_sum((double)acct[r][i]);
-          if (lane == 0) sred[warp * P.nslots + sl] += v;
-        }
+              for (int i = 0; i < 4; ++i)
+                if (P.rslot[r][i] == v) a = acct[r][i];
+            return a;
+          },
+          slot_out);
+    } else if (P.nslots > 0) {
+      // per-round sums: sred holds every warp's FP64 totals
+      __syncthreads();
+      for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
+        double v = 0;
+        for (int w = 0; w < kWarps; ++w) v += sred[w * P.nslots + s];
+        slot_out(s, v);
       }
-    for (int s = 0; s < P.ncomp; ++s) {
-      const double v = warp_sum((double)sdef[s * kThreads + threadIdx.x]);
-      if (lane == 0) sred[warp * P.nslots + P.nslots - P.ncomp + s] += v;
     }
-  }
-  if (NS == 2 && P.nslots > 0) {
-    __syncthreads();
-    for (int s = threadIdx.x; s < P.nslots; s += kThreads) {
-      double v = 0;
-      for (int w = 0; w < kWarps; ++w) v += sred[w * P.nslots + s];
-      part[(long long)s * gridDim.x + blockIdx.x] = v;
-    }
-  }
-  if (pre_b && P.pre_grad) {
-    // per thread u_p = sum over its elements of w * z_p (see the sweep)
-    const FwdPhaseMeta* pm = reinterpret_cast<const FwdPhaseMeta*>(fph_bpre);
-    const R mW = macc[0], mF = macc[11 * kThreads];
-    const double wsum = warp_sum((double)mW);
-    if (lane == 0) smarg[warp * (n + 1)] = wsum;
-    for (int p = 0; p < n; ++p) {
-      R u;
-      int js = -1;
-      for (int j = 0; j < pm->nse; ++j)
-        if (pm->sepos[j] == p) js = j;
-      if (js >= 0) u = macc[(1 + js) * kThreads];
-      else if (p == flpos0) u = macc[9 * kThreads];
-      else if (p == flpos1) u = macc[10 * kThreads];
-      else if ((fmask >> p) & 1) u = 0;  // lane p's term below
-      else u = ((zT >> p) & 1) ? mW : (R)0;
-      double v = warp_sum((double)u);
-      v += (double)__shfl_sync(0xffffffffu, mF, p);
-      if (lane == 0) smarg[warp * (n + 1) + 1 + p] = v;
-    }
-    __syncthreads();
-    for (int v = threadIdx.x; v <= n; v += kThreads) {
-      double s = 0;
-      for (int w = 0; w < kWarps; ++w) s += smarg[w * (n + 1) + v];
-      part[P.pre_moff + (long long)v * gridDim.x + blockIdx.x] = s;
+    if (pre_b && P.pre_grad) {
+      // u_p = sum over the thread's elements of w * z_p: element bits exactly,
+      // the rest from the thread's total and its tile-independent z bits; the
+      // tile-dependent (warp-uniform) bits were summed per warp into lane p's
+      // mF, which lane p adds to its u_p
+      const FwdPhaseMeta* pm = reinterpret_cast<const FwdPhaseMeta*>(fph_bpre);
+      const R mW = macc[0], mF = macc[11 * kThreads];
+      block_sums<R>(
+          reinterpret_cast<R*>(smarg), n + 1,
+          [&](int v) -> R {
+            if (v == 0) return mW;
+            const int p = v - 1;
+            R u;
+            int js = -1;
+            for (int j = 0; j < pm->nse; ++j)
+              if (pm->sepos[j] == p) js = j;
+            if (js >= 0) u = macc[(1 + js) * kThreads];
+            else if (p == flpos0) u = macc[9 * kThreads];
+            else if (p == flpos1) u = macc[10 * kThreads];
+            else if ((fmask >> p) & 1) u = 0;
+            else u = ((zT >> p) & 1) ? mW : (R)0;
+            return lane == p ? u + mF : u;
+          },
+          [&](int v, double sum) { part[P.pre_moff + (long long)v * nblk + blockIdx.x] = sum; });
     }
   }
 }
