@@ -57,6 +57,40 @@ __device__ __forceinline__ R pauli_grad(int ck, cx<R> w0, cx<R> w1, cx<R> y0, cx
 // gate, so the pair just undone (that layer's output side) gives it.
 // MAYCK = false compiles the companion code out (ck is then ignored): the
 // compiler otherwise evaluates it for every pair and selects the result.
+// Gradient of a single-qubit gate with a generic generator, 2 Re <w|A|y>
+// summed over a thread's pairs, A = M^dagger dM.  M is unitary, so A is
+// anti-Hermitian: A00 = i a0 and A11 = i a1 with a0, a1 real, A10 = -conj(A01),
+// and
+//   2 Re <w|A|y> = 2 Re(A01 D) - 2 a0 Im(w0* y0) - 2 a1 Im(w1* y1),
+//   D = w0* y1 - w1 conj(y0).
+// A thread sums the componentwise products behind Im(w0* y0), Im(w1* y1) and
+// D over its pairs (six packed multiply-adds per pair, where the dense
+// form took two complex matrix-vector products and two inner products) and
+// applies A once per gate.
+template <class R>
+struct GenGrad {
+  cx<R> pa, pb, pc, pd, pe, pf;
+  __device__ __forceinline__ GenGrad() {
+    pa = pb = pc = pd = pe = pf = mk<R>(0, 0);
+  }
+  __device__ __forceinline__ void add(cx<R> w0, cx<R> w1, cx<R> y0, cx<R> y1) {
+    const cx<R> s0 = mk<R>(y0.y, y0.x), s1 = mk<R>(y1.y, y1.x);
+    pa = pfma<R>(w0, y1, pa);  // Re(w0* y1) = pa.x + pa.y
+    pb = pfma<R>(w1, y0, pb);  // Re(w1 conj(y0)) = pb.x + pb.y
+    pc = pfma<R>(w0, s1, pc);  // Im(w0* y1) = pc.x - pc.y
+    pd = pfma<R>(w1, s0, pd);  // -Im(w1 conj(y0)) = pd.x - pd.y
+    pe = pfma<R>(w0, s0, pe);  // Im(w0* y0) = pe.x - pe.y
+    pf = pfma<R>(w1, s1, pf);  // Im(w1* y1) = pf.x - pf.y
+  }
+  // a: the record's A (row-major 2x2 complex: A00, A01, A10, A11)
+  __device__ __forceinline__ R value(const R* a) const {
+    const R a0 = a[1], a01r = a[2], a01i = a[3], a1 = a[7];
+    const R dre = (pa.x + pa.y) - (pb.x + pb.y);
+    const R dim = (pc.x - pc.y) + (pd.x - pd.y);
+    return 2 * (a01r * dre - a01i * dim) - 2 * (a0 * (pe.x - pe.y) + a1 * (pf.x - pf.y));
+  }
+};
+
 template <class R, int RB, int I, bool MAYCK = true>
 __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, int np, int gk, int ck_in,
                                     R* acc) {
@@ -111,14 +145,11 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
     return;
   }
   {
-    C m00, m01, m10, m11, a00, a01, a10, a11;
+    C m00, m01, m10, m11;
     ldc2<R>(m, m00, m01);
     ldc2<R>(m + 4, m10, m11);
-    if (np && gk != 1) {
-      ldc2<R>(m + 8, a00, a01);
-      ldc2<R>(m + 12, a10, a11);
-    }
     R g = 0;
+    GenGrad<R> gg;
 #pragma unroll
     for (int a = 0; a < (1 << RB); ++a)
       if (!(a & (1 << I))) {
@@ -136,7 +167,14 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
           if (gk == 1) {
             // RX: 2 Re <l|(-i/2 X)|p> = Im(l0* p1 + l1* p0)
             g += im_cdot<R>(w0, y1) + im_cdot<R>(w1, y0);
+          } else if constexpr (sizeof(R) == 4) {
+            gg.add(w0, w1, y0, y1);
           } else {
+            // complex128: the dense form (the packed sums' 24 extra live
+            // registers spilled at four register bits)
+            C a00, a01, a10, a11;
+            ldc2<R>(m + 8, a00, a01);
+            ldc2<R>(m + 12, a10, a11);
             C t0 = cfma<R>(a01, y1, cmul<R>(a00, y0));
             C t1 = cfma<R>(a11, y1, cmul<R>(a10, y0));
             g += 2 * (re_cdot<R>(w0, t0) + re_cdot<R>(w1, t1));
@@ -144,7 +182,7 @@ __device__ __forceinline__ void bw1(cx<R>* p, cx<R>* l, const R* m, int real, in
         }
         if (ck) acc[I * 3 + 1] += pauli_grad<R>(ck, w0, w1, y0, y1);
       }
-    if (np) acc[I * 3] += g;
+    if (np) acc[I * 3] += (gk == 1 || sizeof(R) != 4) ? g : gg.value(m + 8);
   }
 }
 

@@ -210,14 +210,11 @@ __device__ __forceinline__ void bw1tc(float2* p, float2* l, const float* m, int 
   using C = float2;
   const int ck = MAYCK && !FIXED ? ck_in : 0;
   const int np = FIXED ? 0 : np_in;
-  C s0 = make_float2(0.f, -1.f), s1 = make_float2(0.f, -1.f), a00, a01, a10, a11;
+  C s0 = make_float2(0.f, -1.f), s1 = make_float2(0.f, -1.f);
   if (!FIXED) ldc2<float>(m, s0, s1);
   const float gf = FIXED ? 1.f : m[4];
-  if (np && gk != 1) {
-    ldc2<float>(m + 8, a00, a01);
-    ldc2<float>(m + 12, a10, a11);
-  }
   float g = 0, h = 0;
+  GenGrad<float> gg;
 #pragma unroll
   for (int a = 0; a < (1 << RB); ++a)
     if (!(a & (1 << I))) {
@@ -234,14 +231,12 @@ __device__ __forceinline__ void bw1tc(float2* p, float2* l, const float* m, int 
         if (gk == 1) {
           g += im_cdot<float>(w0, y1) + im_cdot<float>(w1, y0);
         } else {
-          const C t0 = cfma<float>(a01, y1, cmul<float>(a00, y0));
-          const C t1 = cfma<float>(a11, y1, cmul<float>(a10, y0));
-          g += 2 * (re_cdot<float>(w0, t0) + re_cdot<float>(w1, t1));
+          gg.add(w0, w1, y0, y1);
         }
       }
       if (ck) h += pauli_grad<float>(ck, w0, w1, y0, y1);
     }
-  if (np) acc[I * 3] += gf * g;
+  if (np) acc[I * 3] += gf * (gk == 1 ? g : gg.value(m + 8));
   if (ck) acc[I * 3 + 1] += gf * h;
 }
 

@@ -187,6 +187,20 @@ def test_gradients_reduced_every_round_where_shared_sums_do_not_fit():
     _run_with_env(code, {"QC_TMAX_BWD": "11"})
 
 
+@pytest.mark.parametrize("rb", [3, 4])
+def test_generic_generator_gradient_at_three_and_four_register_bits(rb):
+    """GPI2's gradient (a generator that is no Pauli matrix) is summed from
+    the anti-Hermitian form of A = M^dagger dM; the backward passes of the
+    ionq family run at three and at four register bits (own process: the
+    knob is read once), complex64 on TMA tiles and complex128 on per-thread
+    copies."""
+    code = ("import sys; sys.path.insert(0, '.');"
+            "from tests.test_gpu_parity import compare; from paper_2506_04891_gb300 import workloads as W;"
+            "compare('c64', 14, W.ionq_circuit(14, 2), 2, seed=21, path=2);"
+            "compare('c128', 13, W.ionq_circuit(13, 2), 2, seed=22, path=2)")
+    _run_with_env(code, {"QC_RB_BWD": str(rb)})
+
+
 @pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("dtype,n", [("c64", 9), ("c128", 8)])
 def test_constant_gates_and_rot_both_paths(path, dtype, n):
