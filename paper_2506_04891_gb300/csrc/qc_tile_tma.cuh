@@ -327,13 +327,15 @@ __device__ bool scale_real_records(float* sco, int nops, int nco, float2* corr) 
 // runtime flag sc_rt chooses between 1 and 0 (complex kind 0: a round loop
 // per form spilled registers there, the branch measured faster; for real
 // passes the branch measured 1.6% slower on zz26 than a loop per form).
-template <int NS, int RB, int KIND, int I, bool COMP, int SC>
+// FULL: every register bit of the round carries an op (the presence test and
+// its branch are compiled out).
+template <int NS, int RB, int KIND, int I, bool COMP, int SC, bool FULL = false>
 __device__ __forceinline__ void tma_bit(unsigned rmask, int k0, int nco, int np, int gk, int ck, int pat,
                                         int sc_rt, float2* v0, float2* v1, const float* sco, float* acc) {
   using R = float;
   if (KIND == 2 && I + 1 >= RB) return;
-  if (!((rmask >> I) & 1u)) return;
-  const int k = k0 + __popc(rmask & ((1u << I) - 1u));
+  if (!FULL && !((rmask >> I) & 1u)) return;
+  const int k = FULL ? k0 + I : k0 + __popc(rmask & ((1u << I) - 1u));
   const R* mc = sco + k * nco;
   if constexpr (KIND == 3) {
     // constant SX without gradients: -i butterflies, or the full matrices
@@ -585,6 +587,11 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
         basis[j] = tma_swz(1 << (lo + j));
         eo[j] = elem_off(1 << (lo + j));  // global offset of register bit j (disjoint bits)
       }
+      // the group loop, compiled for rounds whose register bits all carry a
+      // gate (FULL: no presence branch after each gate, whose join had the
+      // compiler move the held amplitudes between registers) and for the rest
+      auto groups = [&](auto full_c) {
+        constexpr bool FULL = decltype(full_c)::value;
       for (int g = threadIdx.x; g < (T >> RB); g += kThreads) {
         const int li = (g & ((1 << lo) - 1)) | ((g >> lo) << (lo + RB));
         const int pb = tma_swz(XL ? (li ^ (T - 1)) : li);
@@ -661,15 +668,15 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
           __syncthreads();
           if (threadIdx.x == 0 && f + cps < tps) issue(f + cps, 0);
         }
-        tma_bit<NS, RB, KIND, 0, COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1, sco, acc);
+        tma_bit<NS, RB, KIND, 0, COMP, SC, FULL>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1, sco, acc);
         if (RB > 1)
-          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 1 ? 1 : 0), COMP, SC, FULL>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
                                                            sco, acc);
         if (RB > 2)
-          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 2 ? 2 : 0), COMP, SC, FULL>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
                                                            sco, acc);
         if (RB > 3)
-          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP, SC>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
+          tma_bit<NS, RB, KIND, (RB > 3 ? 3 : 0), COMP, SC, FULL>(rmask, k0, op_nco, op_np, op_gk, op_ck, op_pat, pass_sc, v0, v1,
                                                            sco, acc);
         if ((SC > 0 || (SC < 0 && pass_sc)) && last) {
           // the pass's gates are all applied: restore the product of the
@@ -742,6 +749,13 @@ __global__ void __launch_bounds__(kThreads, tma_minb(NS, KIND))
             if constexpr (NS == 2) S1[ad] = v1[a];
           }
         }
+      }
+      };
+      if constexpr (KIND != 2) {
+        if (rmask == (1u << RB) - 1u) groups(std::true_type{});
+        else groups(std::false_type{});
+      } else {
+        groups(std::false_type{});
       }
       if (NS == 2) {
         if (P.defer == 1) {
